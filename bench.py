@@ -1,0 +1,360 @@
+"""Benchmark of the ETD2RKds hot path on GB300.
+
+Workload (default): the 2D FitzHugh-Nagumo system with advection on a
+1024 x 1024 grid, [0,100]^2, D = (1, 20), velocity (0.5, 0.5), eps = 0.05,
+a1 = 2, a0 = -0.03, tau = 1e-2, seeded N(0, 0.05^2) data.  One benchmark
+step is one whole solve of 500 ETD2RKds time steps from the seeded initial
+data, with the state resident in HBM; the metric is point-steps/s (grid
+points x time steps, both components advanced) over the timed solves.  L2 is
+flushed (256 MB write) between timed solves.
+
+Printed JSON line (rank 0): metric, value, unit, e2e (same metric through
+adr_solve with pinned host buffers, copies inside the timed region),
+roofline of the dominant kernel, the FP64 oracle timed on the host cores,
+the clocks sampled during the timed region and the max relative error of the
+timed precision against an FP64 GPU solve of the same data.
+
+Under torchrun each rank runs its own replica of the workload (independent
+solves, no collective on the data path): "scaling": "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+PREC = {"fp64": wl.FP64, "fp32": wl.FP32, "tf32x3": wl.TF32X3, "bf16x3": wl.BF16X3}
+DTYPE_NAME = {wl.FP64: "f64", wl.FP32: "f32", wl.TF32X3: "f32 (tf32x3 tensor-core products)",
+              wl.BF16X3: "f32 (bf16x3 tensor-core products)"}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(name: str, precision: int):
+    if name == "fhn1024":
+        return wl.fhn_1024(precision=precision)
+    if name == "bruss256":
+        return wl.brusselator_256(precision=precision)
+    if name == "schnak64":
+        return wl.schnakenberg_64(precision=precision)
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(p, sample_steps: int):
+    """The FP64 oracle (as it stands) timed on the host cores on a bounded
+    sample: `sample_steps` ETD2RKds steps of the same workload."""
+    import oracle
+    from oracle import schemes
+    cores = len(os.sched_getaffinity(0))
+    u0, v0 = wl.initial_data(p)
+    u0, v0 = wl.round_to(u0, p.precision), wl.round_to(v0, p.precision)
+    t0 = time.perf_counter()
+    plan = schemes.make_plan(p)
+    plan_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    schemes.etd2rkds_solve(plan, u0, v0, sample_steps)
+    dt = time.perf_counter() - t0
+    return {"value": p.npoints * sample_steps / dt, "unit": "point-steps/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{sample_steps} ETD2RKds steps of the same {p.name} grid, FP64 numpy "
+                      f"(plan time {plan_s:.1f} s excluded)"}
+
+
+def reference_arm(args):
+    """--impl reference: the FP64 CPU oracle on this workload (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = workload(args.workload, PREC[args.precision])
+    sample = args.ref_sample
+    import oracle
+    from oracle import schemes
+    u0, v0 = wl.initial_data(p)
+    u0, v0 = wl.round_to(u0, p.precision), wl.round_to(v0, p.precision)
+    plan = schemes.make_plan(p)
+    for _ in range(args.warmup):
+        schemes.etd2rkds_solve(plan, u0, v0, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        schemes.etd2rkds_solve(plan, u0, v0, sample)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = p.npoints * sample * args.steps / tot
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": "point-steps/s", "value": value,
+            "unit": "point-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": p.name, "grid": list(p.n[: p.d]), "tau": p.tau,
+                       "time_steps_per_bench_step": sample},
+            "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"each bench step = {sample} ETD2RKds steps of {p.name}"},
+            "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="fhn1024")
+    ap.add_argument("--precision", default="fp32", choices=sorted(PREC))
+    ap.add_argument("--time-steps", type=int, default=None,
+                    help="ETD2RKds steps per bench step (default: the workload's)")
+    ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy solve")
+    ap.add_argument("--cpu-sample", type=int, default=40)
+    ap.add_argument("--ref-sample", type=int, default=20)
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    import paper_2307_10684_gb300 as adr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prec = PREC[args.precision]
+    p = workload(args.workload, prec)
+    nts = args.time_steps or p.nsteps
+    dt = adr.state_dtype(prec)
+    u0n, v0n = wl.initial_data(p)
+    u0 = torch.tensor(wl.round_to(u0n, prec), dtype=dt, device="cuda")
+    v0 = torch.tensor(wl.round_to(v0n, prec), dtype=dt, device="cuda")
+    u = torch.empty_like(u0)
+    v = torch.empty_like(v0)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    plan = adr.Plan(p)
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+
+    # accuracy of this precision against an FP64 GPU solve of the same data
+    max_rel = None
+    if not args.no_check:
+        u.copy_(u0)
+        v.copy_(v0)
+        plan.step(u, v, nts)
+        p64 = p.replace(precision=wl.FP64)
+        ur = u0.double().clone()
+        vr = v0.double().clone()
+        with adr.Plan(p64) as plan64:
+            plan64.step(ur, vr, nts)
+        torch.cuda.synchronize()
+        du, mu = adr.max_abs_diff(u, ur)
+        dv, mv = adr.max_abs_diff(v, vr)
+        max_rel = max(du / mu, dv / mv)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def one_solve():
+        u.copy_(u0)
+        v.copy_(v0)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.step(u, v, nts)
+        e1.record(stream)
+        return e0, e1
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    plan.set_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [one_solve() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stats = plan.stats()
+    plan.set_timing(False)
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(ms)
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    npts = p.npoints
+    value = world * npts * nts * args.steps / (tot_ms / 1e3)
+
+    # end to end through adr_solve with pinned host buffers
+    hu0 = u0.cpu().pin_memory()
+    hv0 = v0.cpu().pin_memory()
+    huT = torch.empty_like(hu0).pin_memory()
+    hvT = torch.empty_like(hv0).pin_memory()
+    plan.solve(hu0, hv0, huT, hvT, nts)  # warm
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.solve(hu0, hv0, huT, hvT, nts)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * npts * nts * args.steps / e2e_s, "unit": "point-steps/s",
+           "h2d_bytes_per_step": int(2 * hu0.numel() * hu0.element_size()),
+           "d2h_bytes_per_step": int(2 * huT.numel() * huT.element_size())}
+
+    # roofline of the dominant kernel class (live CUDA-event timing)
+    peaks, peak_src = load_peaks()
+    kern = {k: d for k, d in stats["kernels"].items() if d["count"] > 0}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    kd = kern[dom]
+    avg_s = kd["ms"] / kd["count"] / 1e3
+    total_kernel_ms = sum(d["ms"] for d in kern.values())
+    if dom == "mode_product_simt":
+        flops = kd["flops"] / kd["count"]
+        if prec == wl.FP64:
+            peak = 1250.0 * 1e9  # nominal FP64 rate of GB300 (GFLOP/s)
+            bound, unit, peak_note = "alu", "TFLOP/s", "nominal FP64 1.25 TFLOP/s"
+        else:
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+            bound, unit = "alu", "TFLOP/s"
+            peak_note = "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+        achieved = flops / avg_s
+        roof = {"bound": bound, "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "peak_source": peak_note, "share_of_kernel_time": kd["ms"] / total_kernel_ms}
+    elif dom == "mode_product_tc":
+        flops = kd["flops"] / kd["count"]
+        ratio = 0.5 if prec == wl.TF32X3 else 1.0  # tf32 dense rate = 1/2 of bf16
+        issue = 3.0 if prec == wl.TF32X3 else 6.0
+        peak = peaks["bf16_tflops"] * 1e12 * ratio
+        achieved = flops / avg_s
+        roof = {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "issued_frac": issue * achieved / peak,
+                "peak_source": f"{peak_src} bf16 x {ratio} (dense {['bf16', 'tf32'][ratio < 1]})",
+                "share_of_kernel_time": kd["ms"] / total_kernel_ms}
+    else:
+        bytes_ = kd["bytes"] / kd["count"]
+        achieved = bytes_ / avg_s
+        peak = peaks["hbm_gbs"] * 1e9
+        roof = {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
+        cpu = cpu_baseline(p, args.cpu_sample)
+
+    if rank == 0:
+        line = {"metric": "point-steps/s", "value": value, "unit": "point-steps/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[prec],
+                "data": "synthetic (seeded SplitMix64 N(0,0.05^2) data)",
+                "config": {"workload": p.name, "grid": list(p.n[: p.d]), "tau": p.tau,
+                           "time_steps_per_bench_step": nts, "precision": args.precision,
+                           "l2": "flushed between timed solves (256 MB write)",
+                           "parallelism": f"replicas x{world}"},
+                "max_rel_err_vs_fp64": max_rel, "plan_ms": plan_ms,
+                "e2e": e2e, "gpu_launches": stats["launches"],
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "kernels": {k: {"count": d["count"], "avg_us": 1e3 * d["ms"] / d["count"]}
+                            for k, d in kern.items()}}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * adr.h - C ABI of the GB300 ETD2RKds time stepper.
+ *
+ * The library advances two-component advection-diffusion-reaction systems
+ *     u_t = K^u u + g^u(u, v),   v_t = K^v v + g^v(u, v)
+ * (Caliari & Cassini, arXiv:2307.10684, Sec. 1, Eq. 1-2) on a box grid of
+ * n_1 x ... x n_d points (d = 2 or 3) with homogeneous Neumann boundaries,
+ * using the directional split exponential integrator ETD2RKds
+ * (Sec. 3, Eq. 11).  K^c = A_d^c (+) ... (+) A_1^c is a Kronecker sum
+ * (Eq. 3) of tridiagonal second-order centred finite-difference matrices
+ * (Sec. 4, opening text).  Each step is four Tucker operators (Eq. 5, Eq.
+ * 10b) with the small dense matrices phi_1(tau A_mu^c), phi_2(tau A_mu^c)
+ * plus two Kronecker-sum actions (Eq. 6) and the pointwise reactions.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * State layout: a state tensor is a dense array of n_1 * ... * n_d values
+ *   with x_1 fastest (C array [n_d]...[n_2][n_1]); this is the column-major
+ *   vec() ordering of Sec. 2.  Element type: double for ADR_FP64, float for
+ *   every other precision.
+ * Grid: vertex-centred, x_i = lo + i (hi - lo)/(n - 1), i = 0..n-1.
+ *   Neumann rows mirror a ghost value across the boundary (u_{-1} = u_1).
+ * Pointers: "device" means memory the GPU of the plan can address (cudaMalloc
+ *   or managed); "host or device" arguments are classified with
+ *   cudaPointerGetAttributes.
+ * Streams: every call is enqueued on the plan's CUDA stream (the one given
+ *   to adr_plan_create, 0 = legacy default stream) and is asynchronous with
+ *   respect to the host unless it says otherwise.
+ * Errors: every call returns an adr_status; no exception crosses the ABI.
+ *   On ADR_EINVAL nothing was enqueued and user buffers are untouched.
+ *   adr_last_error() gives a human-readable message for the calling thread.
+ * Ownership: the caller owns state buffers; a plan owns its matrices and
+ *   workspace, which adr_plan_destroy frees.
+ * Threads: a plan may be used from one host thread at a time.
+ */
+#ifndef ADR_H
+#define ADR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ADR_OK = 0,
+  ADR_EINVAL = 1,        /* invalid argument (problem, pointer, size)      */
+  ADR_ENOMEM = 2,        /* device allocation failed                       */
+  ADR_ECUDA = 3,         /* a CUDA runtime call failed                     */
+  ADR_EUNSUPPORTED = 4,  /* valid but not implemented for this shape/prec. */
+  ADR_ETIMEOUT = 5,      /* a bounded device wait gave up                  */
+  ADR_ENUMERIC = 6,      /* non-finite value detected                      */
+  ADR_EBUSY = 7          /* resource busy (admission refused)              */
+} adr_status;
+
+/* Reaction models g^u, g^v and the meaning of adr_problem.params[]:
+ *  ADR_SCHNAKENBERG (Sec. 4.1, Eq. 12): params {gamma, a, b}
+ *     g^u = gamma (a - u + u^2 v),  g^v = gamma (b - u^2 v)
+ *  ADR_FHN, FitzHugh-Nagumo with linear recovery: params {eps, a1, a0}
+ *     g^u = u - u^3 - v,            g^v = eps (u - a1 v - a0)
+ *  ADR_BRUSSELATOR (Sec. 4.6, Eq. 17): params {a, b}
+ *     g^u = a - (b + 1) u + u^2 v,  g^v = b u - u^2 v
+ *  ADR_NO_REACTION: g^u = g^v = 0 (linear advection-diffusion). */
+typedef enum {
+  ADR_SCHNAKENBERG = 0,
+  ADR_FHN = 1,
+  ADR_BRUSSELATOR = 2,
+  ADR_NO_REACTION = 3
+} adr_model;
+
+/* Arithmetic of the mode products (the Tucker operators).
+ *  ADR_FP64   : double state, double SIMT products.
+ *  ADR_FP32   : float state, float SIMT products (FP32 FMA).
+ *  ADR_TF32X3 : float state, tensor-core products with operands split into
+ *               a TF32 high and low part (3 MMAs, FP32 accumulation).
+ *  ADR_BF16X3 : float state, tensor-core products with operands split into
+ *               three BF16 parts (6 MMAs, FP32 accumulation).
+ * Matrix functions are always evaluated in FP64 on the GPU. */
+typedef enum {
+  ADR_FP64 = 0,
+  ADR_FP32 = 1,
+  ADR_TF32X3 = 2,
+  ADR_BF16X3 = 3
+} adr_precision;
+
+/* One problem.  Direction mu = 0 is x_1 (the contiguous axis). */
+typedef struct {
+  int32_t d;            /* 2 or 3                                           */
+  int32_t model;        /* adr_model                                        */
+  int32_t precision;    /* adr_precision                                    */
+  int32_t flags;        /* reserved, must be 0                              */
+  int64_t n[3];         /* grid points per direction, 3 <= n[mu] <= 4096    */
+  double lo[3], hi[3];  /* domain [lo_mu, hi_mu], hi > lo                   */
+  double diff[2];       /* diffusion delta^u, delta^v (> 0)                 */
+  double adv[2][3];     /* velocity of the term -adv[c] . grad(c)           */
+  double params[8];     /* model constants, see adr_model                   */
+  double tau;           /* constant time step (> 0)                         */
+} adr_problem;
+
+typedef struct adr_plan_s* adr_plan;
+
+/* Create a plan: validates the problem, builds the directional matrices
+ * A_mu^c, evaluates e^(tau A_mu^c), phi_1(tau A_mu^c), phi_2(tau A_mu^c) in
+ * FP64 on the GPU (Pade [13/13] scaling and squaring of the augmented matrix
+ * [[X, I, 0], [0, 0, I], [0, 0, 0]], X = tau A_mu^c; phi_ell is Eq. 9),
+ * converts them to the kernel operand format and allocates the step
+ * workspace.  Synchronises the stream before returning.
+ *   problem : host pointer, read only.
+ *   stream  : cudaStream_t (as void*), 0 for the default stream.
+ *   out     : receives the plan; untouched on failure. */
+adr_status adr_plan_create(const adr_problem* problem, void* stream, adr_plan* out);
+
+/* Free a plan (synchronises its stream first).  NULL is accepted. */
+adr_status adr_plan_destroy(adr_plan plan);
+
+/* Advance (u, v) by nsteps ETD2RKds steps in place (Eq. 11):
+ *   U2 = U + tau (sum_mu U x_mu A_mu^u + G^u(U,V)) x_mu phi_1(tau A_mu^u)
+ *   U+ = U2 + 2^(d-1) tau (G^u(U2,V2) - G^u(U,V)) x_mu phi_2(tau A_mu^u)
+ * and likewise for V.  u, v: device pointers to state tensors (layout
+ * above), distinct, not aliasing plan memory.  nsteps >= 0.  Asynchronous. */
+adr_status adr_step(adr_plan plan, void* u, void* v, int64_t nsteps);
+
+/* Solve from (u0, v0) for nsteps steps into (uT, vT).  Each pointer may be
+ * host or device memory; host inputs are copied to the device, host outputs
+ * copied back, and in that case the call returns after the copy-back has
+ * completed.  With device pointers only it is asynchronous.  u0/v0 may
+ * equal uT/vT. */
+adr_status adr_solve(adr_plan plan, const void* u0, const void* v0, void* uT, void* vT,
+                     int64_t nsteps);
+
+/* Bytes a plan for `problem` would hold: state_bytes = one (u, v) pair in
+ * the run precision; cache_bytes = matrices + workspace.  Host only. */
+adr_status adr_plan_bytes(const adr_problem* problem, size_t* state_bytes, size_t* cache_bytes);
+
+/* Copy one FP64 plan matrix to host memory `out` (n_mu * n_mu doubles,
+ * row-major, out[i * n + j] = M[i][j]).  which: 0 = A_mu^c, 1 = e^(tau A),
+ * 2 = phi_1(tau A), 3 = phi_2(tau A).  component: 0 = u, 1 = v.  mu: 0..d-1.
+ * Synchronous. */
+adr_status adr_plan_matrix(adr_plan plan, int which, int component, int mu, double* out);
+
+/* Counters of a plan since creation (or the last reset). */
+typedef struct {
+  int64_t launches;        /* kernels launched by adr_step / adr_solve     */
+  int64_t steps;           /* ETD2RKds steps enqueued                      */
+  int32_t timing;          /* 1 if per-kernel event timing is on           */
+  int32_t nkernels;        /* entries used in the arrays below             */
+  char    name[16][32];    /* kernel class names                           */
+  int64_t count[16];       /* timed launches per class                     */
+  double  ms[16];          /* summed CUDA-event time per class (ms)        */
+  double  flops[16];       /* algorithmic flops per class (summed)         */
+  double  bytes[16];       /* algorithmic bytes per class (summed)         */
+} adr_stats;
+
+/* Turn per-kernel CUDA-event timing on (1) or off (0); clears counters. */
+adr_status adr_plan_set_timing(adr_plan plan, int enable);
+/* Fetch counters; synchronises the plan's stream when timing is on. */
+adr_status adr_plan_stats(adr_plan plan, adr_stats* out);
+
+/* Error reduction (FP64 on the GPU): out[0] = max_i |x_i - ref_i|,
+ * out[1] = max_i |ref_i| over `count` elements.  x: device array of float
+ * (x_is_double = 0) or double (1); ref: device array of double.  out: host.
+ * Enqueued on `stream` and synchronised before returning. */
+adr_status adr_max_abs_diff(void* stream, const void* x, int x_is_double, const double* ref,
+                            int64_t count, double out[2]);
+
+/* Short name of a status code (static storage). */
+const char* adr_status_str(adr_status s);
+/* Message describing the last failure on the calling host thread. */
+const char* adr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADR_H */

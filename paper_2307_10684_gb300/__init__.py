@@ -1,0 +1,167 @@
+"""Python binding of libadr_gb300 (the C ABI declared in include/adr.h).
+
+Argument marshalling only: every step of the ETD2RKds path runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  The
+binding raises if the compiled library is missing; there is no fallback.
+
+Usage::
+
+    import paper_2307_10684_gb300 as adr
+    plan = adr.Plan(problem)          # problem: any object with the adr_problem fields
+    plan.step(u, v, nsteps)           # u, v: contiguous CUDA tensors, updated in place
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+from . import _abi
+from ._abi import (ADR_OK, ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA, ADR_EUNSUPPORTED,  # noqa: F401
+                   ADR_ETIMEOUT, ADR_ENUMERIC, ADR_EBUSY, FP64, FP32, TF32X3, BF16X3,
+                   SCHNAKENBERG, FHN, BRUSSELATOR, NO_REACTION, AdrError, lib, library_path)
+
+__all__ = ["Plan", "AdrError", "lib", "library_path", "plan_bytes", "max_abs_diff",
+           "make_problem", "state_dtype"]
+
+
+def make_problem(p) -> _abi.AdrProblem:
+    """adr_problem from an object with fields d, n, lo, hi, diff, adv, model,
+    params, tau, precision (e.g. workloads.Problem)."""
+    s = _abi.AdrProblem()
+    s.d = int(p.d)
+    s.model = int(p.model)
+    s.precision = int(p.precision)
+    s.flags = 0
+    def at(seq, i, default):
+        return seq[i] if i < min(len(seq), max(int(p.d), 0)) else default
+
+    for m in range(3):
+        s.n[m] = int(at(p.n, m, 1))
+        s.lo[m] = float(at(p.lo, m, 0.0))
+        s.hi[m] = float(at(p.hi, m, 1.0))
+    for c in range(2):
+        s.diff[c] = float(p.diff[c])
+        for m in range(3):
+            s.adv[c][m] = float(at(p.adv[c], m, 0.0))
+    for i in range(8):
+        s.params[i] = float(p.params[i]) if i < len(p.params) else 0.0
+    s.tau = float(p.tau)
+    return s
+
+
+def state_dtype(precision: int):
+    import torch
+    return torch.float64 if precision == FP64 else torch.float32
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """An adr_plan: FP64 matrix functions on the GPU, operands, workspace."""
+
+    def __init__(self, problem, stream=None):
+        self.problem = problem
+        self.precision = int(problem.precision)
+        self.shape = tuple(reversed([int(x) for x in problem.n[: problem.d]]))
+        self._stream = stream
+        self._p = _abi.AdrPlan()
+        self._cprob = make_problem(problem)
+        _abi.check(lib().adr_plan_create(ctypes.byref(self._cprob),
+                                         ctypes.c_void_p(_stream_handle(stream)),
+                                         ctypes.byref(self._p)))
+
+    def close(self):
+        if self._p:
+            lib().adr_plan_destroy(self._p)
+            self._p = _abi.AdrPlan()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check_state(self, x, device: bool):
+        import torch
+        if not isinstance(x, torch.Tensor):
+            raise TypeError("state must be a torch.Tensor")
+        if x.dtype != state_dtype(self.precision):
+            raise TypeError(f"state dtype must be {state_dtype(self.precision)}")
+        if not x.is_contiguous() or x.numel() != _abi.prod(self.shape):
+            raise ValueError(f"state must be contiguous with {_abi.prod(self.shape)} elements")
+        if device and not x.is_cuda:
+            raise ValueError("state must be a CUDA tensor")
+
+    def step(self, u, v, nsteps: int = 1):
+        """adr_step: advance CUDA tensors u, v in place (asynchronous)."""
+        self._check_state(u, True)
+        self._check_state(v, True)
+        _abi.check(lib().adr_step(self._p, ctypes.c_void_p(u.data_ptr()),
+                                  ctypes.c_void_p(v.data_ptr()), ctypes.c_int64(int(nsteps))))
+
+    def solve(self, u0, v0, uT, vT, nsteps: int):
+        """adr_solve: tensors may live on the host (pinned) or the device."""
+        for x in (u0, v0, uT, vT):
+            self._check_state(x, False)
+        _abi.check(lib().adr_solve(self._p, ctypes.c_void_p(u0.data_ptr()),
+                                   ctypes.c_void_p(v0.data_ptr()), ctypes.c_void_p(uT.data_ptr()),
+                                   ctypes.c_void_p(vT.data_ptr()), ctypes.c_int64(int(nsteps))))
+
+    def matrix(self, which: int, component: int, mu: int):
+        """FP64 plan matrix (0 = A, 1 = e^(tau A), 2 = phi_1, 3 = phi_2) as numpy."""
+        import numpy as np
+        n = int(self.problem.n[mu])
+        out = np.empty((n, n), dtype=np.float64)
+        _abi.check(lib().adr_plan_matrix(self._p, int(which), int(component), int(mu),
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def set_timing(self, enable: bool):
+        _abi.check(lib().adr_plan_set_timing(self._p, 1 if enable else 0))
+
+    def stats(self) -> dict:
+        st = _abi.AdrStats()
+        _abi.check(lib().adr_plan_stats(self._p, ctypes.byref(st)))
+        kernels = {}
+        for k in range(st.nkernels):
+            kernels[st.name[k].value.decode()] = {
+                "count": int(st.count[k]), "ms": float(st.ms[k]),
+                "flops": float(st.flops[k]), "bytes": float(st.bytes[k])}
+        return {"launches": int(st.launches), "steps": int(st.steps),
+                "timing": bool(st.timing), "kernels": kernels}
+
+
+def plan_bytes(problem):
+    s = make_problem(problem)
+    sb = ctypes.c_size_t()
+    cb = ctypes.c_size_t()
+    _abi.check(lib().adr_plan_bytes(ctypes.byref(s), ctypes.byref(sb), ctypes.byref(cb)))
+    return int(sb.value), int(cb.value)
+
+
+def max_abs_diff(x, ref, stream=None):
+    """(max |x - ref|, max |ref|) on the GPU in FP64; ref must be float64."""
+    import torch
+    if ref.dtype != torch.float64 or not ref.is_cuda or not x.is_cuda:
+        raise TypeError("x, ref must be CUDA tensors, ref float64")
+    if x.numel() != ref.numel() or not x.is_contiguous() or not ref.is_contiguous():
+        raise ValueError("size / contiguity mismatch")
+    out = (ctypes.c_double * 2)()
+    _abi.check(lib().adr_max_abs_diff(ctypes.c_void_p(_stream_handle(stream)),
+                                      ctypes.c_void_p(x.data_ptr()),
+                                      1 if x.dtype == torch.float64 else 0,
+                                      ctypes.c_void_p(ref.data_ptr()),
+                                      ctypes.c_int64(x.numel()), out))
+    return float(out[0]), float(out[1])

@@ -1,0 +1,87 @@
+"""ctypes declarations mirroring include/adr.h."""
+from __future__ import annotations
+
+import ctypes
+import os
+from functools import reduce
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_PKG, "_build", "libadr_gb300.so")
+
+ADR_OK, ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA, ADR_EUNSUPPORTED, ADR_ETIMEOUT, ADR_ENUMERIC, \
+    ADR_EBUSY = range(8)
+SCHNAKENBERG, FHN, BRUSSELATOR, NO_REACTION = range(4)
+FP64, FP32, TF32X3, BF16X3 = range(4)
+
+c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+class AdrProblem(ctypes.Structure):
+    _fields_ = [("d", c_int32), ("model", c_int32), ("precision", c_int32), ("flags", c_int32),
+                ("n", c_int64 * 3), ("lo", c_double * 3), ("hi", c_double * 3),
+                ("diff", c_double * 2), ("adv", (c_double * 3) * 2), ("params", c_double * 8),
+                ("tau", c_double)]
+
+
+class AdrStats(ctypes.Structure):
+    _fields_ = [("launches", c_int64), ("steps", c_int64), ("timing", c_int32),
+                ("nkernels", c_int32), ("name", (ctypes.c_char * 32) * 16),
+                ("count", c_int64 * 16), ("ms", c_double * 16), ("flops", c_double * 16),
+                ("bytes", c_double * 16)]
+
+
+class AdrPlan(ctypes.c_void_p):
+    pass
+
+
+# name -> (restype, argtypes); every symbol include/adr.h declares
+SIGNATURES = {
+    "adr_plan_create": (c_int32, [ctypes.POINTER(AdrProblem), c_void_p, ctypes.POINTER(AdrPlan)]),
+    "adr_plan_destroy": (c_int32, [AdrPlan]),
+    "adr_step": (c_int32, [AdrPlan, c_void_p, c_void_p, c_int64]),
+    "adr_solve": (c_int32, [AdrPlan, c_void_p, c_void_p, c_void_p, c_void_p, c_int64]),
+    "adr_plan_bytes": (c_int32, [ctypes.POINTER(AdrProblem), ctypes.POINTER(ctypes.c_size_t),
+                                 ctypes.POINTER(ctypes.c_size_t)]),
+    "adr_plan_matrix": (c_int32, [AdrPlan, c_int32, c_int32, c_int32, ctypes.POINTER(c_double)]),
+    "adr_plan_set_timing": (c_int32, [AdrPlan, c_int32]),
+    "adr_plan_stats": (c_int32, [AdrPlan, ctypes.POINTER(AdrStats)]),
+    "adr_max_abs_diff": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int64,
+                                   ctypes.POINTER(c_double)]),
+    "adr_status_str": (ctypes.c_char_p, [c_int32]),
+    "adr_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class AdrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def lib():
+    """The loaded library; raises ImportError if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise ImportError(f"libadr_gb300.so not built ({library_path}); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(library_path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status: int):
+    if status != ADR_OK:
+        L = lib()
+        raise AdrError(status, f"{L.adr_status_str(status).decode()}: "
+                               f"{L.adr_last_error().decode()}")
+
+
+def prod(xs):
+    return reduce(lambda a, b: a * b, xs, 1)

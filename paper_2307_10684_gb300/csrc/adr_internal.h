@@ -1,0 +1,147 @@
+// Internal declarations shared by the translation units of libadr_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/adr.h"
+
+namespace adr {
+
+// Per-thread error message for adr_last_error().
+void set_error(const std::string& msg);
+
+#define ADR_CUDA_TRY(expr)                                                        \
+  do {                                                                            \
+    cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      ::adr::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));       \
+      return ADR_ECUDA;                                                           \
+    }                                                                             \
+  } while (0)
+
+// Tridiagonal directional operator with Neumann rows (interior row i:
+// lo x_{i-1} + di x_i + up x_{i+1}; row 0: di x_0 + b0 x_1; row n-1:
+// bn x_{n-2} + di x_{n-1}).  Row sums are zero, so the kernels evaluate
+// lo (x_{i-1} - x_i) + up (x_{i+1} - x_i), which is the same value with
+// far less cancellation in single precision.
+struct Tridiag {
+  double lo, di, up, b0, bn;
+};
+
+struct ReactionParams {
+  int model;
+  double p[8];
+};
+
+// Stencil + reaction description for one problem, passed by value.
+struct PointwiseArgs {
+  int d;
+  int64_t n[3];
+  int64_t N;
+  Tridiag A[2][3];       // [component][mu]
+  ReactionParams rx;
+};
+
+// Batched GEMM with per-component operand sets.  blockIdx.z = comp * batch
+// + p.  C[p] = alpha * A[p] B[p] (+ beta * base[p]) (+ beta2 * base2[p]),
+// A row-major M x K (lda), B row-major K x N (ldb), C/base/base2 row-major
+// M x N (ldc).  *_bs are batch strides in elements.
+struct GemmArgs {
+  const void* A[2];
+  const void* B[2];
+  void* C[2];
+  const void* base[2];
+  const void* base2[2];
+  int64_t lda, ldb, ldc;
+  int64_t a_bs, b_bs, c_bs;
+  int M, N, K;
+  int batch;   // p range
+  int ncomp;   // 1 or 2
+  double alpha, beta, beta2;
+};
+
+// Kernel launchers (simt.cu).
+template <typename T>
+cudaError_t launch_gemm_simt(const GemmArgs& g, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rhs(const PointwiseArgs& a, const T* u, const T* v, T* wu, T* wv,
+                       cudaStream_t s);
+template <typename T>
+cudaError_t launch_rdiff(const PointwiseArgs& a, const T* u, const T* v, const T* u2,
+                         const T* v2, T* du, T* dv, cudaStream_t s);
+
+// Matrix-function helpers (matfun.cu).
+cudaError_t matfun_phi(int n, const Tridiag& A, double tau, double* E, double* P1, double* P2,
+                       cudaStream_t s);
+cudaError_t launch_build_dense(int n, const Tridiag& A, double scale, double* X, cudaStream_t s);
+cudaError_t launch_convert(const double* src, void* dst, int64_t count, int to_double,
+                           int transpose_n, cudaStream_t s);
+cudaError_t launch_max_abs_diff(const void* x, int x_is_double, const double* ref, int64_t count,
+                                unsigned long long* out2, cudaStream_t s);
+
+
+// Tensor-core operand set of a plan (tc.cu).
+struct TcOperands {
+  int prec;        // ADR_TF32X3 or ADR_BF16X3; 0 when unused
+  void* mats[2][3][2];   // split operand matrices per [c][mu][ell-1]
+  void* work[4];         // tensor-core workspace
+  void* tmaps;           // device copy of tensor maps (opaque)
+  int ready;
+};
+
+}  // namespace adr
+
+enum KernelClass { KC_RHS = 0, KC_RDIFF = 1, KC_MODE_SIMT = 2, KC_MODE_TC = 3, KC_COUNT = 4 };
+
+struct TimedLaunch {
+  int cls;
+  cudaEvent_t e0, e1;
+  double flops, bytes;
+};
+
+struct adr_plan_s {
+  adr_problem prob;
+  cudaStream_t stream;
+  int d;
+  int64_t n[3];
+  int64_t N;
+  int prec;
+  size_t esize;  // bytes per state element
+  adr::PointwiseArgs pw;
+  // FP64 masters [c][mu][which], which: 0 = A, 1 = e^(tau A), 2 = phi_1, 3 = phi_2
+  double* master[2][3][4];
+  // SIMT operands: phi_ell row-major and transposed, in the state type
+  void* op[2][3][2];
+  void* opT[2][3][2];
+  // tensor-core operands
+  adr::TcOperands tc;
+  // workspace
+  void* u2;
+  void* v2;
+  void* bufA[2];
+  void* bufB[2];
+  void* dstate[2];  // device state for adr_solve with host buffers
+  std::vector<void*> allocs;
+  // counters
+  int64_t launches;
+  int64_t steps;
+  bool timing;
+  std::vector<TimedLaunch> timed;
+  std::vector<cudaEvent_t> event_pool;
+  size_t event_next;
+};
+
+
+namespace adr {
+static const char* const kClassNames[KC_COUNT] = {"rhs_stencil_reaction", "reaction_diff",
+                                                  "mode_product_simt", "mode_product_tc"};
+void tc_init(TcOperands* t);
+void tc_free(TcOperands* t);
+cudaError_t tc_prepare(TcOperands* t, int prec, int d, const int64_t n[3],
+                       double* const master[2][3][4], cudaStream_t s);
+cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v);
+}  // namespace adr

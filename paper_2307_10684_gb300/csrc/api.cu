@@ -1,0 +1,502 @@
+// C ABI of the ETD2RKds library: plans, steps, solves and queries.
+//
+// A plan holds, for each component c in {u, v} and direction mu, the FP64
+// matrices A_mu^c, e^(tau A_mu^c), phi_1(tau A_mu^c), phi_2(tau A_mu^c)
+// (computed on the GPU by matfun.cu) plus their operand copies for the step
+// kernels, and the step workspace.  One ETD2RKds step (Sec. 3, Eq. 11) is
+//   W^c  = sum_mu U^c x_mu A_mu^c + G^c(U, V)          (rhs kernel)
+//   U2^c = U^c + tau W^c x_1 phi_1 ... x_d phi_1        (d mode products)
+//   D^c  = G^c(U2, V2) - G^c(U, V)                      (rdiff kernel)
+//   U+^c = U2^c + 2^(d-1) tau D^c x_1 phi_2 ... x_d phi_2
+// with both components handled by each launch.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "adr_internal.h"
+
+namespace adr {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace adr
+
+using namespace adr;
+
+// ---------------------------------------------------------------- helpers
+static adr_status fail(adr_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+static cudaError_t plan_alloc(adr_plan P, void** out, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) return e;
+  P->allocs.push_back(q);
+  *out = q;
+  return cudaSuccess;
+}
+
+static adr_status validate(const adr_problem* p) {
+  if (!p) return fail(ADR_EINVAL, "problem is NULL");
+  if (p->d != 2 && p->d != 3) return fail(ADR_EINVAL, "d must be 2 or 3");
+  if (p->flags != 0) return fail(ADR_EINVAL, "flags must be 0");
+  if (p->model < 0 || p->model > ADR_NO_REACTION) return fail(ADR_EINVAL, "unknown model");
+  if (p->precision < 0 || p->precision > ADR_BF16X3)
+    return fail(ADR_EINVAL, "unknown precision");
+  if (!(p->tau > 0.0) || !isfinite(p->tau)) return fail(ADR_EINVAL, "tau must be finite and > 0");
+  int64_t N = 1;
+  for (int m = 0; m < p->d; ++m) {
+    if (p->n[m] < 3 || p->n[m] > 4096) return fail(ADR_EINVAL, "n[mu] must be in [3, 4096]");
+    if (!(p->hi[m] > p->lo[m]) || !isfinite(p->hi[m]) || !isfinite(p->lo[m]))
+      return fail(ADR_EINVAL, "domain needs lo < hi, finite");
+    N *= p->n[m];
+  }
+  if (N > ((int64_t)1 << 31)) return fail(ADR_EINVAL, "grid too large (N > 2^31)");
+  for (int c = 0; c < 2; ++c) {
+    if (!(p->diff[c] > 0.0) || !isfinite(p->diff[c]))
+      return fail(ADR_EINVAL, "diffusion must be finite and > 0");
+    for (int m = 0; m < p->d; ++m)
+      if (!isfinite(p->adv[c][m])) return fail(ADR_EINVAL, "advection must be finite");
+  }
+  for (int i = 0; i < 8; ++i)
+    if (!isfinite(p->params[i])) return fail(ADR_EINVAL, "params must be finite");
+  return ADR_OK;
+}
+
+// Centred second-order FD coefficients of delta d2/dx2 - alpha d/dx on the
+// vertex grid with mirrored ghost values at both ends (Sec. 4 text).
+static Tridiag fd_coefficients(int64_t n, double lo, double hi, double delta, double alpha) {
+  const double h = (hi - lo) / (double)(n - 1);
+  Tridiag t;
+  t.lo = delta / (h * h) + alpha / (2.0 * h);
+  t.di = -2.0 * delta / (h * h);
+  t.up = delta / (h * h) - alpha / (2.0 * h);
+  t.b0 = 2.0 * delta / (h * h);
+  t.bn = 2.0 * delta / (h * h);
+  return t;
+}
+
+static bool same_operator(const Tridiag& a, const Tridiag& b) {
+  return a.lo == b.lo && a.di == b.di && a.up == b.up && a.b0 == b.b0 && a.bn == b.bn;
+}
+
+static cudaEvent_t pool_event(adr_plan P) {
+  if (P->event_next < P->event_pool.size()) return P->event_pool[P->event_next++];
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  P->event_pool.push_back(e);
+  P->event_next++;
+  return e;
+}
+
+// Launch wrapper: counts launches and, when timing is on, brackets the
+// launch with events on the plan's stream.
+template <typename F>
+static cudaError_t timed_launch(adr_plan P, int cls, double flops, double bytes, F&& fn) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (P->timing) {
+    e0 = pool_event(P);
+    e1 = pool_event(P);
+    if (e0) cudaEventRecord(e0, P->stream);
+  }
+  cudaError_t err = fn();
+  P->launches++;
+  if (P->timing && e0 && e1) {
+    cudaEventRecord(e1, P->stream);
+    P->timed.push_back(TimedLaunch{cls, e0, e1, flops, bytes});
+  }
+  return err;
+}
+
+// ---------------------------------------------------------------- step (SIMT)
+template <typename T>
+static cudaError_t mode_product_simt(adr_plan P, int mu, int ell, void* const in[2], void* const out[2],
+                                     void* const base[2], double alpha) {
+  const int64_t n = P->n[mu];
+  int64_t Q = 1;
+  for (int m = 0; m < mu; ++m) Q *= P->n[m];
+  const int64_t Pb = P->N / (n * Q);
+  GemmArgs g{};
+  g.ncomp = 2;
+  g.alpha = alpha;
+  g.beta = 1.0;
+  for (int c = 0; c < 2; ++c) {
+    g.C[c] = out[c];
+    g.base[c] = base ? base[c] : nullptr;
+    g.base2[c] = nullptr;
+  }
+  if (mu == 0) {  // Y[p][i] = sum_j X[p][j] Phi[i][j]  ->  Y = X Phi^T
+    for (int c = 0; c < 2; ++c) {
+      g.A[c] = in[c];
+      g.B[c] = P->opT[c][mu][ell - 1];
+    }
+    g.M = (int)Pb;
+    g.N = (int)n;
+    g.K = (int)n;
+    g.lda = n;
+    g.ldb = n;
+    g.ldc = n;
+    g.batch = 1;
+  } else {  // Y[p] = Phi X[p], X[p] an n x Q row-major slab
+    for (int c = 0; c < 2; ++c) {
+      g.A[c] = P->op[c][mu][ell - 1];
+      g.B[c] = in[c];
+    }
+    g.M = (int)n;
+    g.N = (int)Q;
+    g.K = (int)n;
+    g.lda = n;
+    g.ldb = Q;
+    g.ldc = Q;
+    g.a_bs = 0;
+    g.b_bs = n * Q;
+    g.c_bs = n * Q;
+    g.batch = (int)Pb;
+  }
+  const double flops = 2.0 * 2.0 * (double)n * (double)P->N;
+  const double bytes = (double)sizeof(T) * 2.0 * (2.0 * P->N + (base ? P->N : 0) + n * n);
+  return timed_launch(P, KC_MODE_SIMT, flops, bytes,
+                      [&] { return launch_gemm_simt<T>(g, P->stream); });
+}
+
+template <typename T>
+static cudaError_t tucker_simt(adr_plan P, int ell, void* const in[2], void* const out[2],
+                               void* const base[2], double alpha) {
+  // in -> bufB -> bufA -> ... -> out, last product with the AXPY epilogue
+  void* cur[2] = {in[0], in[1]};
+  for (int mu = 0; mu < P->d; ++mu) {
+    const bool last = (mu == P->d - 1);
+    void* dst[2];
+    if (last) {
+      dst[0] = out[0];
+      dst[1] = out[1];
+    } else {
+      void* const* pick = (cur[0] == P->bufA[0]) ? P->bufB : P->bufA;
+      dst[0] = pick[0];
+      dst[1] = pick[1];
+    }
+    cudaError_t e = mode_product_simt<T>(P, mu, ell, cur, dst, last ? base : nullptr,
+                                         last ? alpha : 1.0);
+    if (e != cudaSuccess) return e;
+    cur[0] = dst[0];
+    cur[1] = dst[1];
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t step_simt(adr_plan P, T* u, T* v) {
+  const double tau = P->prob.tau;
+  const double N = (double)P->N;
+  cudaError_t e = timed_launch(P, KC_RHS, N * 2.0 * (6.0 * P->d + 10.0), sizeof(T) * N * 4.0, [&] {
+    return launch_rhs<T>(P->pw, u, v, (T*)P->bufA[0], (T*)P->bufA[1], P->stream);
+  });
+  if (e != cudaSuccess) return e;
+  void* uv[2] = {u, v};
+  void* st2[2] = {P->u2, P->v2};
+  e = tucker_simt<T>(P, 1, P->bufA, st2, uv, tau);
+  if (e != cudaSuccess) return e;
+  e = timed_launch(P, KC_RDIFF, N * 2.0 * 12.0, sizeof(T) * N * 6.0, [&] {
+    return launch_rdiff<T>(P->pw, u, v, (const T*)P->u2, (const T*)P->v2, (T*)P->bufA[0],
+                           (T*)P->bufA[1], P->stream);
+  });
+  if (e != cudaSuccess) return e;
+  const double c2 = ldexp(tau, P->d - 1);
+  return tucker_simt<T>(P, 2, P->bufA, uv, st2, c2);
+}
+
+// ---------------------------------------------------------------- plan
+static void plan_free(adr_plan P) {
+  if (!P) return;
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  for (void* q : P->allocs) cudaFree(q);
+  for (cudaEvent_t e : P->event_pool) cudaEventDestroy(e);
+  tc_free(&P->tc);
+  delete P;
+}
+
+extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, adr_plan* out) {
+  if (!out) return fail(ADR_EINVAL, "out is NULL");
+  adr_status st = validate(problem);
+  if (st != ADR_OK) return st;
+  adr_plan P = new adr_plan_s();
+  memset(&P->pw, 0, sizeof(P->pw));
+  memset(P->master, 0, sizeof(P->master));
+  memset(P->op, 0, sizeof(P->op));
+  memset(P->opT, 0, sizeof(P->opT));
+  P->prob = *problem;
+  P->stream = (cudaStream_t)stream;
+  P->d = problem->d;
+  P->N = 1;
+  for (int m = 0; m < 3; ++m) P->n[m] = m < P->d ? problem->n[m] : 1;
+  for (int m = 0; m < P->d; ++m) P->N *= P->n[m];
+  P->prec = problem->precision;
+  P->esize = P->prec == ADR_FP64 ? sizeof(double) : sizeof(float);
+  P->launches = 0;
+  P->steps = 0;
+  P->timing = false;
+  P->event_next = 0;
+  P->u2 = P->v2 = nullptr;
+  P->dstate[0] = P->dstate[1] = nullptr;
+  tc_init(&P->tc);
+
+  PointwiseArgs& pw = P->pw;
+  pw.d = P->d;
+  pw.N = P->N;
+  for (int m = 0; m < 3; ++m) pw.n[m] = P->n[m];
+  pw.rx.model = problem->model;
+  for (int i = 0; i < 8; ++i) pw.rx.p[i] = problem->params[i];
+  for (int c = 0; c < 2; ++c)
+    for (int m = 0; m < P->d; ++m)
+      pw.A[c][m] = fd_coefficients(P->n[m], problem->lo[m], problem->hi[m], problem->diff[c],
+                                   problem->adv[c][m]);
+
+  cudaError_t e = cudaSuccess;
+#define PLAN_TRY(x)                                                            \
+  do {                                                                         \
+    e = (x);                                                                   \
+    if (e != cudaSuccess) {                                                    \
+      set_error(std::string("adr_plan_create: ") + #x + ": " + cudaGetErrorString(e)); \
+      plan_free(P);                                                            \
+      return e == cudaErrorMemoryAllocation ? ADR_ENOMEM : ADR_ECUDA;          \
+    }                                                                          \
+  } while (0)
+
+  // matrices, shared between (c, mu) pairs with identical operators
+  for (int c = 0; c < 2; ++c) {
+    for (int m = 0; m < P->d; ++m) {
+      const int64_t n = P->n[m];
+      bool found = false;
+      for (int c2 = 0; c2 <= c && !found; ++c2)
+        for (int m2 = 0; m2 < P->d && !found; ++m2) {
+          if (c2 == c && m2 >= m) break;
+          if (P->n[m2] == n && same_operator(pw.A[c2][m2], pw.A[c][m])) {
+            for (int w = 0; w < 4; ++w) P->master[c][m][w] = P->master[c2][m2][w];
+            for (int l = 0; l < 2; ++l) {
+              P->op[c][m][l] = P->op[c2][m2][l];
+              P->opT[c][m][l] = P->opT[c2][m2][l];
+            }
+            found = true;
+          }
+        }
+      if (found) continue;
+      const size_t nn = (size_t)n * n;
+      for (int w = 0; w < 4; ++w) PLAN_TRY(plan_alloc(P, (void**)&P->master[c][m][w], nn * 8));
+      PLAN_TRY(launch_build_dense((int)n, pw.A[c][m], 1.0, P->master[c][m][0], P->stream));
+      PLAN_TRY(matfun_phi((int)n, pw.A[c][m], problem->tau, P->master[c][m][1],
+                          P->master[c][m][2], P->master[c][m][3], P->stream));
+      for (int l = 0; l < 2; ++l) {
+        PLAN_TRY(plan_alloc(P, &P->op[c][m][l], nn * P->esize));
+        PLAN_TRY(plan_alloc(P, &P->opT[c][m][l], nn * P->esize));
+        PLAN_TRY(launch_convert(P->master[c][m][2 + l], P->op[c][m][l], (int64_t)nn,
+                                P->prec == ADR_FP64, 0, P->stream));
+        PLAN_TRY(launch_convert(P->master[c][m][2 + l], P->opT[c][m][l], (int64_t)nn,
+                                P->prec == ADR_FP64, (int)n, P->stream));
+      }
+    }
+  }
+  const size_t sb = (size_t)P->N * P->esize;
+  PLAN_TRY(plan_alloc(P, &P->u2, sb));
+  PLAN_TRY(plan_alloc(P, &P->v2, sb));
+  for (int c = 0; c < 2; ++c) {
+    PLAN_TRY(plan_alloc(P, &P->bufA[c], sb));
+    PLAN_TRY(plan_alloc(P, &P->bufB[c], sb));
+  }
+  if (P->prec == ADR_TF32X3 || P->prec == ADR_BF16X3) {
+    e = tc_prepare(&P->tc, P->prec, P->d, P->n, P->master, P->stream);
+    if (e != cudaSuccess) {
+      const bool unsup = (e == cudaErrorNotSupported);
+      set_error(std::string("adr_plan_create: tensor-core operands: ") + cudaGetErrorString(e));
+      plan_free(P);
+      return unsup ? ADR_EUNSUPPORTED : ADR_ECUDA;
+    }
+  }
+  PLAN_TRY(cudaStreamSynchronize(P->stream));
+  PLAN_TRY(cudaGetLastError());
+#undef PLAN_TRY
+  *out = P;
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_plan_destroy(adr_plan plan) {
+  plan_free(plan);
+  return ADR_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static adr_status step_impl(adr_plan P, void* u, void* v, int64_t nsteps) {
+  for (int64_t s = 0; s < nsteps; ++s) {
+    cudaError_t e;
+    if (P->prec == ADR_FP64)
+      e = step_simt<double>(P, (double*)u, (double*)v);
+    else if (P->prec == ADR_FP32)
+      e = step_simt<float>(P, (float*)u, (float*)v);
+    else
+      e = tc_step(&P->tc, P, u, v);
+    if (e != cudaSuccess)
+      return fail(e == cudaErrorNotSupported ? ADR_EUNSUPPORTED : ADR_ECUDA,
+                  std::string("adr_step: ") + cudaGetErrorString(e));
+    P->steps++;
+  }
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_step(adr_plan plan, void* u, void* v, int64_t nsteps) {
+  if (!plan) return fail(ADR_EINVAL, "plan is NULL");
+  if (!u || !v || u == v) return fail(ADR_EINVAL, "u, v must be distinct non-NULL device pointers");
+  if (nsteps < 0) return fail(ADR_EINVAL, "nsteps < 0");
+  if (!is_device_ptr(u) || !is_device_ptr(v))
+    return fail(ADR_EINVAL, "adr_step needs device pointers");
+  return step_impl(plan, u, v, nsteps);
+}
+
+extern "C" adr_status adr_solve(adr_plan plan, const void* u0, const void* v0, void* uT, void* vT,
+                                int64_t nsteps) {
+  if (!plan) return fail(ADR_EINVAL, "plan is NULL");
+  if (!u0 || !v0 || !uT || !vT) return fail(ADR_EINVAL, "NULL state pointer");
+  if (uT == vT) return fail(ADR_EINVAL, "uT and vT must differ");
+  if (nsteps < 0) return fail(ADR_EINVAL, "nsteps < 0");
+  adr_plan P = plan;
+  const size_t sb = (size_t)P->N * P->esize;
+  const bool dev_in = is_device_ptr(u0) && is_device_ptr(v0);
+  const bool dev_out = is_device_ptr(uT) && is_device_ptr(vT);
+  void* wu;
+  void* wv;
+  if (dev_out) {
+    wu = uT;
+    wv = vT;
+  } else {
+    if (!P->dstate[0]) {
+      if (plan_alloc(P, &P->dstate[0], sb) != cudaSuccess ||
+          plan_alloc(P, &P->dstate[1], sb) != cudaSuccess)
+        return fail(ADR_ENOMEM, "adr_solve: device state allocation failed");
+    }
+    wu = P->dstate[0];
+    wv = P->dstate[1];
+  }
+  const cudaMemcpyKind kin = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (wu != u0) ADR_CUDA_TRY(cudaMemcpyAsync(wu, u0, sb, kin, P->stream));
+  if (wv != v0) ADR_CUDA_TRY(cudaMemcpyAsync(wv, v0, sb, kin, P->stream));
+  adr_status st = step_impl(P, wu, wv, nsteps);
+  if (st != ADR_OK) return st;
+  if (!dev_out) {
+    ADR_CUDA_TRY(cudaMemcpyAsync(uT, wu, sb, cudaMemcpyDeviceToHost, P->stream));
+    ADR_CUDA_TRY(cudaMemcpyAsync(vT, wv, sb, cudaMemcpyDeviceToHost, P->stream));
+  }
+  if (!dev_out || !dev_in) ADR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_plan_bytes(const adr_problem* problem, size_t* state_bytes,
+                                     size_t* cache_bytes) {
+  adr_status st = validate(problem);
+  if (st != ADR_OK) return st;
+  const size_t es = problem->precision == ADR_FP64 ? 8 : 4;
+  size_t N = 1, mats = 0;
+  for (int m = 0; m < problem->d; ++m) {
+    N *= (size_t)problem->n[m];
+    const size_t nn = (size_t)problem->n[m] * problem->n[m];
+    mats += 2 * (4 * 8 * nn + 4 * es * nn);
+    if (problem->precision >= ADR_TF32X3) mats += 2 * 2 * 3 * 4 * nn;
+  }
+  if (state_bytes) *state_bytes = 2 * N * es;
+  if (cache_bytes) *cache_bytes = mats + 6 * N * es;
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_plan_matrix(adr_plan plan, int which, int component, int mu, double* out) {
+  if (!plan || !out) return fail(ADR_EINVAL, "NULL argument");
+  if (which < 0 || which > 3 || component < 0 || component > 1 || mu < 0 || mu >= plan->d)
+    return fail(ADR_EINVAL, "matrix index out of range");
+  const int64_t n = plan->n[mu];
+  ADR_CUDA_TRY(cudaMemcpyAsync(out, plan->master[component][mu][which], (size_t)n * n * 8,
+                               cudaMemcpyDeviceToHost, plan->stream));
+  ADR_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_plan_set_timing(adr_plan plan, int enable) {
+  if (!plan) return fail(ADR_EINVAL, "plan is NULL");
+  ADR_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+  plan->timing = enable != 0;
+  plan->timed.clear();
+  plan->event_next = 0;
+  plan->launches = 0;
+  plan->steps = 0;
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_plan_stats(adr_plan plan, adr_stats* out) {
+  if (!plan || !out) return fail(ADR_EINVAL, "NULL argument");
+  memset(out, 0, sizeof(*out));
+  out->launches = plan->launches;
+  out->steps = plan->steps;
+  out->timing = plan->timing ? 1 : 0;
+  out->nkernels = KC_COUNT;
+  for (int k = 0; k < KC_COUNT; ++k) snprintf(out->name[k], 32, "%s", kClassNames[k]);
+  if (plan->timing) {
+    ADR_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+    for (const TimedLaunch& t : plan->timed) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, t.e0, t.e1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      out->count[t.cls]++;
+      out->ms[t.cls] += ms;
+      out->flops[t.cls] += t.flops;
+      out->bytes[t.cls] += t.bytes;
+    }
+  }
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_max_abs_diff(void* stream, const void* x, int x_is_double,
+                                       const double* ref, int64_t count, double out[2]) {
+  if (!x || !ref || !out || count < 0) return fail(ADR_EINVAL, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* d = nullptr;
+  ADR_CUDA_TRY(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+  unsigned long long h[2] = {0, 0};
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(h), s);
+  if (e == cudaSuccess && count > 0) e = launch_max_abs_diff(x, x_is_double, ref, count, d, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(ADR_ECUDA, std::string("adr_max_abs_diff: ") + cudaGetErrorString(e));
+  memcpy(&out[0], &h[0], 8);
+  memcpy(&out[1], &h[1], 8);
+  return ADR_OK;
+}
+
+extern "C" const char* adr_status_str(adr_status s) {
+  switch (s) {
+    case ADR_OK: return "ADR_OK";
+    case ADR_EINVAL: return "ADR_EINVAL";
+    case ADR_ENOMEM: return "ADR_ENOMEM";
+    case ADR_ECUDA: return "ADR_ECUDA";
+    case ADR_EUNSUPPORTED: return "ADR_EUNSUPPORTED";
+    case ADR_ETIMEOUT: return "ADR_ETIMEOUT";
+    case ADR_ENUMERIC: return "ADR_ENUMERIC";
+    case ADR_EBUSY: return "ADR_EBUSY";
+  }
+  return "ADR_UNKNOWN";
+}
+
+extern "C" const char* adr_last_error(void) { return g_last_error.c_str(); }

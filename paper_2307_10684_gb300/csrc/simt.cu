@@ -1,0 +1,254 @@
+// SIMT kernels of the FP64 and FP32 paths: register-blocked batched GEMM
+// for the mu-mode products (Sec. 2, Eq. 5), the stage-1 right-hand side
+// W = sum_mu U x_mu A_mu + G(U, V) (Eq. 6, Eq. 11) and the stage-2 reaction
+// difference D = G(U2, V2) - G(U, V) (Eq. 11).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "adr_internal.h"
+
+namespace adr {
+
+// ---------------------------------------------------------------- reactions
+template <typename T>
+__device__ __forceinline__ void react(const ReactionParams& rx, T u, T v, T& gu, T& gv) {
+  switch (rx.model) {
+    case ADR_SCHNAKENBERG: {
+      const T g = (T)rx.p[0], a = (T)rx.p[1], b = (T)rx.p[2];
+      const T u2v = u * u * v;
+      gu = g * (a - u + u2v);
+      gv = g * (b - u2v);
+    } break;
+    case ADR_FHN: {
+      const T e = (T)rx.p[0], a1 = (T)rx.p[1], a0 = (T)rx.p[2];
+      gu = u - u * u * u - v;
+      gv = e * (u - a1 * v - a0);
+    } break;
+    case ADR_BRUSSELATOR: {
+      const T a = (T)rx.p[0], b = (T)rx.p[1];
+      const T u2v = u * u * v;
+      gu = a - (b + (T)1) * u + u2v;
+      gv = b * u - u2v;
+    } break;
+    default:
+      gu = (T)0;
+      gv = (T)0;
+  }
+}
+
+// One direction of the tridiagonal Kronecker-sum action at one point, in
+// difference form (the rows sum to zero).
+template <typename T>
+__device__ __forceinline__ T stencil_dir(const T* __restrict__ x, int64_t idx, int64_t stride,
+                                         int64_t i, int64_t n, const Tridiag& A) {
+  const T xc = x[idx];
+  if (i == 0) return (T)A.b0 * (x[idx + stride] - xc);
+  if (i == n - 1) return (T)A.bn * (x[idx - stride] - xc);
+  return (T)A.lo * (x[idx - stride] - xc) + (T)A.up * (x[idx + stride] - xc);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) rhs_kernel(PointwiseArgs a, const T* __restrict__ u,
+                                                  const T* __restrict__ v, T* __restrict__ wu,
+                                                  T* __restrict__ wv) {
+  const int64_t n1 = a.n[0], n2 = a.n[1], n3 = a.d == 3 ? a.n[2] : 1;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.N;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i1 = idx % n1;
+    const int64_t r = idx / n1;
+    const int64_t i2 = r % n2;
+    const int64_t i3 = r / n2;
+    T ku = stencil_dir(u, idx, 1, i1, n1, a.A[0][0]) + stencil_dir(u, idx, n1, i2, n2, a.A[0][1]);
+    T kv = stencil_dir(v, idx, 1, i1, n1, a.A[1][0]) + stencil_dir(v, idx, n1, i2, n2, a.A[1][1]);
+    if (a.d == 3) {
+      ku += stencil_dir(u, idx, n1 * n2, i3, n3, a.A[0][2]);
+      kv += stencil_dir(v, idx, n1 * n2, i3, n3, a.A[1][2]);
+    }
+    T gu, gv;
+    react<T>(a.rx, u[idx], v[idx], gu, gv);
+    wu[idx] = ku + gu;
+    wv[idx] = kv + gv;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) rdiff_kernel(PointwiseArgs a, const T* __restrict__ u,
+                                                    const T* __restrict__ v,
+                                                    const T* __restrict__ u2,
+                                                    const T* __restrict__ v2, T* __restrict__ du,
+                                                    T* __restrict__ dv) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.N;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    T g0u, g0v, g2u, g2v;
+    react<T>(a.rx, u[idx], v[idx], g0u, g0v);
+    react<T>(a.rx, u2[idx], v2[idx], g2u, g2v);
+    du[idx] = g2u - g0u;
+    dv[idx] = g2v - g0v;
+  }
+}
+
+static int pointwise_grid(int64_t N) {
+  int64_t b = (N + 255) / 256;
+  const int64_t cap = 152 * 16;
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+template <typename T>
+cudaError_t launch_rhs(const PointwiseArgs& a, const T* u, const T* v, T* wu, T* wv,
+                       cudaStream_t s) {
+  rhs_kernel<T><<<pointwise_grid(a.N), 256, 0, s>>>(a, u, v, wu, wv);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rdiff(const PointwiseArgs& a, const T* u, const T* v, const T* u2, const T* v2,
+                         T* du, T* dv, cudaStream_t s) {
+  rdiff_kernel<T><<<pointwise_grid(a.N), 256, 0, s>>>(a, u, v, u2, v2, du, dv);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_rhs<float>(const PointwiseArgs&, const float*, const float*, float*,
+                                       float*, cudaStream_t);
+template cudaError_t launch_rhs<double>(const PointwiseArgs&, const double*, const double*,
+                                        double*, double*, cudaStream_t);
+template cudaError_t launch_rdiff<float>(const PointwiseArgs&, const float*, const float*,
+                                         const float*, const float*, float*, float*,
+                                         cudaStream_t);
+template cudaError_t launch_rdiff<double>(const PointwiseArgs&, const double*, const double*,
+                                          const double*, const double*, double*, double*,
+                                          cudaStream_t);
+
+// ---------------------------------------------------------------- GEMM
+// Tile configuration: 256 threads as a 16 x 16 grid; each thread owns a
+// TM x TN block of C split into 4-wide groups spread over the tile so that
+// shared-memory reads are conflict free.
+template <typename T>
+struct SimtTile;
+template <>
+struct SimtTile<float> {
+  static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+};
+template <>
+struct SimtTile<double> {
+  static constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs g) {
+  using Cfg = SimtTile<T>;
+  constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, TM = Cfg::TM, TN = Cfg::TN;
+  constexpr int LA = BM * BK / 256;  // A elements loaded per thread (along k)
+  constexpr int LB = BK * BN / 256;  // B elements loaded per thread (along n)
+  constexpr int RS = TM / 4, CS = TN / 4;
+
+  __shared__ __align__(16) T As[2][BK][BM];
+  __shared__ __align__(16) T Bs[2][BK][BN];
+
+  const int z = blockIdx.z;
+  const int comp = z / g.batch;
+  const int p = z - comp * g.batch;
+  const T* __restrict__ A = (const T*)g.A[comp] + (int64_t)p * g.a_bs;
+  const T* __restrict__ B = (const T*)g.B[comp] + (int64_t)p * g.b_bs;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+
+  // load coordinates
+  const int a_row = t / (BK / LA), a_k = (t % (BK / LA)) * LA;
+  const int b_k = t / (BN / LB), b_n = (t % (BN / LB)) * LB;
+
+  T ra[LA], rb[LB];
+  auto load_tiles = [&](int k0) {
+    const int gr = m0 + a_row;
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+      const int gk = k0 + a_k + i;
+      ra[i] = (gr < g.M && gk < g.K) ? A[(int64_t)gr * g.lda + gk] : (T)0;
+    }
+    const int gk = k0 + b_k;
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+      const int gn = n0 + b_n + i;
+      rb[i] = (gk < g.K && gn < g.N) ? B[(int64_t)gk * g.ldb + gn] : (T)0;
+    }
+  };
+  auto store_tiles = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < LA; ++i) As[buf][a_k + i][a_row] = ra[i];
+#pragma unroll
+    for (int i = 0; i < LB; ++i) Bs[buf][b_k][b_n + i] = rb[i];
+  };
+
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = (T)0;
+
+  load_tiles(0);
+  store_tiles(0);
+  __syncthreads();
+
+  const int ktiles = (g.K + BK - 1) / BK;
+  for (int kt = 0; kt < ktiles; ++kt) {
+    const int cur = kt & 1;
+    if (kt + 1 < ktiles) load_tiles((kt + 1) * BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int r = 0; r < RS; ++r)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[r * 4 + i] = As[cur][kk][r * (BM / RS) + ty * 4 + i];
+#pragma unroll
+      for (int c = 0; c < CS; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[c * 4 + j] = Bs[cur][kk][c * (BN / CS) + tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    if (kt + 1 < ktiles) {
+      store_tiles(cur ^ 1);
+    }
+    __syncthreads();
+  }
+
+  // epilogue
+  T* __restrict__ C = (T*)g.C[comp] + (int64_t)p * g.c_bs;
+  const T* __restrict__ base = g.base[comp] ? (const T*)g.base[comp] + (int64_t)p * g.c_bs : nullptr;
+  const T* __restrict__ base2 =
+      g.base2[comp] ? (const T*)g.base2[comp] + (int64_t)p * g.c_bs : nullptr;
+  const T alpha = (T)g.alpha, beta = (T)g.beta, beta2 = (T)g.beta2;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int r = m0 + (i / 4) * (BM / RS) + ty * 4 + (i % 4);
+    if (r >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int c = n0 + (j / 4) * (BN / CS) + tx * 4 + (j % 4);
+      if (c >= g.N) continue;
+      const int64_t o = (int64_t)r * g.ldc + c;
+      T val = alpha * acc[i][j];
+      if (base) val += beta * base[o];
+      if (base2) val += beta2 * base2[o];
+      C[o] = val;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_gemm_simt(const GemmArgs& g, cudaStream_t s) {
+  using Cfg = SimtTile<T>;
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  dim3 grid((g.N + Cfg::BN - 1) / Cfg::BN, (g.M + Cfg::BM - 1) / Cfg::BM, g.batch * g.ncomp);
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+  gemm_simt_kernel<T><<<grid, 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gemm_simt<float>(const GemmArgs&, cudaStream_t);
+template cudaError_t launch_gemm_simt<double>(const GemmArgs&, cudaStream_t);
+
+}  // namespace adr
