@@ -177,7 +177,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="fhn1024")
-    ap.add_argument("--precision", default="fp32", choices=sorted(PREC))
+    ap.add_argument("--precision", default="bf16x3", choices=sorted(PREC))
+    ap.add_argument("--compare", default="fp32",
+                    help="also time this precision on the same workload ('none' to skip)")
     ap.add_argument("--time-steps", type=int, default=None,
                     help="ETD2RKds steps per bench step (default: the workload's)")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy solve")
@@ -331,6 +333,32 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "kernel": dom}
 
+    compare = None
+    if args.compare and args.compare not in ("none", args.precision):
+        cp = PREC[args.compare]
+        pc = workload(args.workload, cp)
+        cdt = adr.state_dtype(cp)
+        cu0 = torch.tensor(wl.round_to(u0n, cp), dtype=cdt, device="cuda")
+        cv0 = torch.tensor(wl.round_to(v0n, cp), dtype=cdt, device="cuda")
+        cu, cv = torch.empty_like(cu0), torch.empty_like(cv0)
+        with adr.Plan(pc) as cplan:
+            cms = []
+            for k in range(1 + max(1, args.steps // 2)):
+                cu.copy_(cu0)
+                cv.copy_(cv0)
+                flush.fill_(1.0)
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                cplan.step(cu, cv, nts)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                if k > 0:
+                    cms.append(a0.elapsed_time(a1))
+        compare = {"precision": args.compare, "ms_per_step": float(np.mean(cms)),
+                   "value": npts * nts / (float(np.mean(cms)) / 1e3),
+                   "speedup_of_headline": (float(np.mean(cms)) / (tot_ms / args.steps))}
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample > 0:
         cpu = cpu_baseline(p, args.cpu_sample)
@@ -348,6 +376,7 @@ def main():
                 "max_rel_err_vs_fp64": max_rel, "plan_ms": plan_ms,
                 "e2e": e2e, "gpu_launches": stats["launches"],
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "same_gpu_comparison": compare,
                 "kernels": {k: {"count": d["count"], "avg_us": 1e3 * d["ms"] / d["count"]}
                             for k, d in kern.items()}}
         print(json.dumps(line), flush=True)

@@ -72,10 +72,13 @@ typedef enum {
 /* Arithmetic of the mode products (the Tucker operators).
  *  ADR_FP64   : double state, double SIMT products.
  *  ADR_FP32   : float state, float SIMT products (FP32 FMA).
- *  ADR_TF32X3 : float state, tensor-core products with operands split into
- *               a TF32 high and low part (3 MMAs, FP32 accumulation).
- *  ADR_BF16X3 : float state, tensor-core products with operands split into
- *               three BF16 parts (6 MMAs, FP32 accumulation).
+ *  ADR_TF32X3 : reserved for TF32 hi+lo tensor-core products; plans return
+ *               ADR_EUNSUPPORTED (the 2^-21 split misses the FP32-class
+ *               accuracy target on fine grids).
+ *  ADR_BF16X3 : float state, tcgen05 tensor-core products with operands
+ *               split into three BF16 parts (6 MMAs, FP32 accumulation);
+ *               needs every n[mu] to be a multiple of 8, else
+ *               ADR_EUNSUPPORTED.
  * Matrix functions are always evaluated in FP64 on the GPU. */
 typedef enum {
   ADR_FP64 = 0,
@@ -124,8 +127,8 @@ adr_status adr_step(adr_plan plan, void* u, void* v, int64_t nsteps);
 /* Solve from (u0, v0) for nsteps steps into (uT, vT).  Each pointer may be
  * host or device memory; host inputs are copied to the device, host outputs
  * copied back, and in that case the call returns after the copy-back has
- * completed.  With device pointers only it is asynchronous.  u0/v0 may
- * equal uT/vT. */
+ * completed (returning ADR_ETIMEOUT if a kernel gave up a bounded wait).
+ * With device pointers only it is asynchronous.  u0/v0 may equal uT/vT. */
 adr_status adr_solve(adr_plan plan, const void* u0, const void* v0, void* uT, void* vT,
                      int64_t nsteps);
 
@@ -145,6 +148,8 @@ typedef struct {
   int64_t steps;           /* ETD2RKds steps enqueued                      */
   int32_t timing;          /* 1 if per-kernel event timing is on           */
   int32_t nkernels;        /* entries used in the arrays below             */
+  int32_t device_error;    /* 0, or the code a bounded device wait left    */
+  int32_t reserved;
   char    name[16][32];    /* kernel class names                           */
   int64_t count[16];       /* timed launches per class                     */
   double  ms[16];          /* summed CUDA-event time per class (ms)        */
@@ -154,7 +159,9 @@ typedef struct {
 
 /* Turn per-kernel CUDA-event timing on (1) or off (0); clears counters. */
 adr_status adr_plan_set_timing(adr_plan plan, int enable);
-/* Fetch counters; synchronises the plan's stream when timing is on. */
+/* Fetch counters; synchronises the plan's stream.  device_error != 0 means
+ * a kernel gave up a bounded wait (its results are invalid); the plan stays
+ * usable and the word is cleared by adr_plan_set_timing. */
 adr_status adr_plan_stats(adr_plan plan, adr_stats* out);
 
 /* Error reduction (FP64 on the GPU): out[0] = max_i |x_i - ref_i|,

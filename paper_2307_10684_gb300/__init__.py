@@ -140,7 +140,8 @@ class Plan:
                 "count": int(st.count[k]), "ms": float(st.ms[k]),
                 "flops": float(st.flops[k]), "bytes": float(st.bytes[k])}
         return {"launches": int(st.launches), "steps": int(st.steps),
-                "timing": bool(st.timing), "kernels": kernels}
+                "timing": bool(st.timing), "device_error": int(st.device_error),
+                "kernels": kernels}
 
 
 def plan_bytes(problem):

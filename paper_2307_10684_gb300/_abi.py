@@ -25,7 +25,8 @@ class AdrProblem(ctypes.Structure):
 
 class AdrStats(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("steps", c_int64), ("timing", c_int32),
-                ("nkernels", c_int32), ("name", (ctypes.c_char * 32) * 16),
+                ("nkernels", c_int32), ("device_error", c_int32), ("reserved", c_int32),
+                ("name", (ctypes.c_char * 32) * 16),
                 ("count", c_int64 * 16), ("ms", c_double * 16), ("flops", c_double * 16),
                 ("bytes", c_double * 16)]
 

@@ -28,23 +28,45 @@ void set_error(const std::string& msg);
 // bn x_{n-2} + di x_{n-1}).  Row sums are zero, so the kernels evaluate
 // lo (x_{i-1} - x_i) + up (x_{i+1} - x_i), which is the same value with
 // far less cancellation in single precision.
-struct Tridiag {
-  double lo, di, up, b0, bn;
+template <typename T>
+struct TridiagT {
+  T lo, di, up, b0, bn;
 };
+using Tridiag = TridiagT<double>;
 
-struct ReactionParams {
+template <typename T>
+struct ReactionT {
   int model;
-  double p[8];
+  T p[8];
 };
 
-// Stencil + reaction description for one problem, passed by value.
-struct PointwiseArgs {
+// Stencil + reaction description for one problem, passed by value.  The
+// coefficients are held in the kernel's arithmetic type so that no kernel
+// converts from double on the (slow) FP64 pipe.
+template <typename T>
+struct PointwiseArgsT {
   int d;
   int64_t n[3];
   int64_t N;
-  Tridiag A[2][3];       // [component][mu]
-  ReactionParams rx;
+  TridiagT<T> A[2][3];  // [component][mu]
+  ReactionT<T> rx;
 };
+using PointwiseArgs = PointwiseArgsT<double>;
+
+template <typename T>
+inline PointwiseArgsT<T> cast_args(const PointwiseArgs& a) {
+  PointwiseArgsT<T> r;
+  r.d = a.d;
+  r.N = a.N;
+  for (int m = 0; m < 3; ++m) r.n[m] = a.n[m];
+  for (int c = 0; c < 2; ++c)
+    for (int m = 0; m < 3; ++m)
+      r.A[c][m] = TridiagT<T>{(T)a.A[c][m].lo, (T)a.A[c][m].di, (T)a.A[c][m].up,
+                              (T)a.A[c][m].b0, (T)a.A[c][m].bn};
+  r.rx.model = a.rx.model;
+  for (int i = 0; i < 8; ++i) r.rx.p[i] = (T)a.rx.p[i];
+  return r;
+}
 
 // Batched GEMM with per-component operand sets.  blockIdx.z = comp * batch
 // + p.  C[p] = alpha * A[p] B[p] (+ beta * base[p]) (+ beta2 * base2[p]),
@@ -68,10 +90,10 @@ struct GemmArgs {
 template <typename T>
 cudaError_t launch_gemm_simt(const GemmArgs& g, cudaStream_t s);
 template <typename T>
-cudaError_t launch_rhs(const PointwiseArgs& a, const T* u, const T* v, T* wu, T* wv,
+cudaError_t launch_rhs(const PointwiseArgsT<T>& a, const T* u, const T* v, T* wu, T* wv,
                        cudaStream_t s);
 template <typename T>
-cudaError_t launch_rdiff(const PointwiseArgs& a, const T* u, const T* v, const T* u2,
+cudaError_t launch_rdiff(const PointwiseArgsT<T>& a, const T* u, const T* v, const T* u2,
                          const T* v2, T* du, T* dv, cudaStream_t s);
 
 // Matrix-function helpers (matfun.cu).
@@ -111,7 +133,8 @@ struct adr_plan_s {
   int64_t N;
   int prec;
   size_t esize;  // bytes per state element
-  adr::PointwiseArgs pw;
+  adr::PointwiseArgs pw;            // FP64 master
+  adr::PointwiseArgsT<float> pwf;   // single-precision copy for FP32-state kernels
   // FP64 masters [c][mu][which], which: 0 = A, 1 = e^(tau A), 2 = phi_1, 3 = phi_2
   double* master[2][3][4];
   // SIMT operands: phi_ell row-major and transposed, in the state type
@@ -144,4 +167,33 @@ void tc_free(TcOperands* t);
 cudaError_t tc_prepare(TcOperands* t, int prec, int d, const int64_t n[3],
                        double* const master[2][3][4], cudaStream_t s);
 cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v);
+int* tc_error_word(TcOperands* t);
+
+inline cudaEvent_t pool_event(adr_plan_s* P) {
+  if (P->event_next < P->event_pool.size()) return P->event_pool[P->event_next++];
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  P->event_pool.push_back(e);
+  P->event_next++;
+  return e;
+}
+
+// Launch wrapper: counts launches and, when timing is on, brackets the
+// launch with events on the plan's stream.
+template <typename F>
+inline cudaError_t timed_kernel(adr_plan_s* P, int cls, double flops, double bytes, F&& fn) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (P->timing) {
+    e0 = pool_event(P);
+    e1 = pool_event(P);
+    if (e0) cudaEventRecord(e0, P->stream);
+  }
+  cudaError_t err = fn();
+  P->launches++;
+  if (P->timing && e0 && e1) {
+    cudaEventRecord(e1, P->stream);
+    P->timed.push_back(TimedLaunch{cls, e0, e1, flops, bytes});
+  }
+  return err;
+}
 }  // namespace adr

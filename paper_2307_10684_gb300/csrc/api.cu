@@ -88,34 +88,6 @@ static bool same_operator(const Tridiag& a, const Tridiag& b) {
   return a.lo == b.lo && a.di == b.di && a.up == b.up && a.b0 == b.b0 && a.bn == b.bn;
 }
 
-static cudaEvent_t pool_event(adr_plan P) {
-  if (P->event_next < P->event_pool.size()) return P->event_pool[P->event_next++];
-  cudaEvent_t e;
-  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-  P->event_pool.push_back(e);
-  P->event_next++;
-  return e;
-}
-
-// Launch wrapper: counts launches and, when timing is on, brackets the
-// launch with events on the plan's stream.
-template <typename F>
-static cudaError_t timed_launch(adr_plan P, int cls, double flops, double bytes, F&& fn) {
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (P->timing) {
-    e0 = pool_event(P);
-    e1 = pool_event(P);
-    if (e0) cudaEventRecord(e0, P->stream);
-  }
-  cudaError_t err = fn();
-  P->launches++;
-  if (P->timing && e0 && e1) {
-    cudaEventRecord(e1, P->stream);
-    P->timed.push_back(TimedLaunch{cls, e0, e1, flops, bytes});
-  }
-  return err;
-}
-
 // ---------------------------------------------------------------- step (SIMT)
 template <typename T>
 static cudaError_t mode_product_simt(adr_plan P, int mu, int ell, void* const in[2], void* const out[2],
@@ -163,7 +135,7 @@ static cudaError_t mode_product_simt(adr_plan P, int mu, int ell, void* const in
   }
   const double flops = 2.0 * 2.0 * (double)n * (double)P->N;
   const double bytes = (double)sizeof(T) * 2.0 * (2.0 * P->N + (base ? P->N : 0) + n * n);
-  return timed_launch(P, KC_MODE_SIMT, flops, bytes,
+  return timed_kernel(P, KC_MODE_SIMT, flops, bytes,
                       [&] { return launch_gemm_simt<T>(g, P->stream); });
 }
 
@@ -193,19 +165,30 @@ static cudaError_t tucker_simt(adr_plan P, int ell, void* const in[2], void* con
 }
 
 template <typename T>
+static const PointwiseArgsT<T>& pw_for(adr_plan P);
+template <>
+const PointwiseArgsT<double>& pw_for<double>(adr_plan P) {
+  return P->pw;
+}
+template <>
+const PointwiseArgsT<float>& pw_for<float>(adr_plan P) {
+  return P->pwf;
+}
+
+template <typename T>
 static cudaError_t step_simt(adr_plan P, T* u, T* v) {
   const double tau = P->prob.tau;
   const double N = (double)P->N;
-  cudaError_t e = timed_launch(P, KC_RHS, N * 2.0 * (6.0 * P->d + 10.0), sizeof(T) * N * 4.0, [&] {
-    return launch_rhs<T>(P->pw, u, v, (T*)P->bufA[0], (T*)P->bufA[1], P->stream);
+  cudaError_t e = timed_kernel(P, KC_RHS, N * 2.0 * (6.0 * P->d + 10.0), sizeof(T) * N * 4.0, [&] {
+    return launch_rhs<T>(pw_for<T>(P), u, v, (T*)P->bufA[0], (T*)P->bufA[1], P->stream);
   });
   if (e != cudaSuccess) return e;
   void* uv[2] = {u, v};
   void* st2[2] = {P->u2, P->v2};
   e = tucker_simt<T>(P, 1, P->bufA, st2, uv, tau);
   if (e != cudaSuccess) return e;
-  e = timed_launch(P, KC_RDIFF, N * 2.0 * 12.0, sizeof(T) * N * 6.0, [&] {
-    return launch_rdiff<T>(P->pw, u, v, (const T*)P->u2, (const T*)P->v2, (T*)P->bufA[0],
+  e = timed_kernel(P, KC_RDIFF, N * 2.0 * 12.0, sizeof(T) * N * 6.0, [&] {
+    return launch_rdiff<T>(pw_for<T>(P), u, v, (const T*)P->u2, (const T*)P->v2, (T*)P->bufA[0],
                            (T*)P->bufA[1], P->stream);
   });
   if (e != cudaSuccess) return e;
@@ -259,6 +242,7 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
       pw.A[c][m] = fd_coefficients(P->n[m], problem->lo[m], problem->hi[m], problem->diff[c],
                                    problem->adv[c][m]);
 
+  P->pwf = cast_args<float>(pw);
   cudaError_t e = cudaSuccess;
 #define PLAN_TRY(x)                                                            \
   do {                                                                         \
@@ -399,7 +383,14 @@ extern "C" adr_status adr_solve(adr_plan plan, const void* u0, const void* v0, v
     ADR_CUDA_TRY(cudaMemcpyAsync(uT, wu, sb, cudaMemcpyDeviceToHost, P->stream));
     ADR_CUDA_TRY(cudaMemcpyAsync(vT, wv, sb, cudaMemcpyDeviceToHost, P->stream));
   }
-  if (!dev_out || !dev_in) ADR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  if (!dev_out || !dev_in) {
+    ADR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    if (int* ew = tc_error_word(&P->tc)) {
+      int h = 0;
+      ADR_CUDA_TRY(cudaMemcpy(&h, ew, sizeof(int), cudaMemcpyDeviceToHost));
+      if (h != 0) return fail(ADR_ETIMEOUT, "adr_solve: a kernel gave up a bounded wait");
+    }
+  }
   return ADR_OK;
 }
 
@@ -435,6 +426,7 @@ extern "C" adr_status adr_plan_set_timing(adr_plan plan, int enable) {
   if (!plan) return fail(ADR_EINVAL, "plan is NULL");
   ADR_CUDA_TRY(cudaStreamSynchronize(plan->stream));
   plan->timing = enable != 0;
+  if (int* ew = tc_error_word(&plan->tc)) ADR_CUDA_TRY(cudaMemset(ew, 0, sizeof(int)));
   plan->timed.clear();
   plan->event_next = 0;
   plan->launches = 0;
@@ -449,6 +441,12 @@ extern "C" adr_status adr_plan_stats(adr_plan plan, adr_stats* out) {
   out->steps = plan->steps;
   out->timing = plan->timing ? 1 : 0;
   out->nkernels = KC_COUNT;
+  ADR_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+  if (int* ew = tc_error_word(&plan->tc)) {
+    int h = 0;
+    ADR_CUDA_TRY(cudaMemcpy(&h, ew, sizeof(int), cudaMemcpyDeviceToHost));
+    out->device_error = h;
+  }
   for (int k = 0; k < KC_COUNT; ++k) snprintf(out->name[k], 32, "%s", kClassNames[k]);
   if (plan->timing) {
     ADR_CUDA_TRY(cudaStreamSynchronize(plan->stream));

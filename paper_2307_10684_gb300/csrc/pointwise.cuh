@@ -1,0 +1,72 @@
+// Pointwise pieces shared by the SIMT and tensor-core step kernels: the
+// reaction terms g^u, g^v and one direction of the tridiagonal Kronecker-sum
+// action (Sec. 2, Eq. 6, with the finite-difference rows of Sec. 4).
+#pragma once
+
+#include <stdint.h>
+
+#include "adr_internal.h"
+
+namespace adr {
+
+template <typename T>
+__device__ __forceinline__ void react(const ReactionT<T>& rx, T u, T v, T& gu, T& gv) {
+  switch (rx.model) {
+    case ADR_SCHNAKENBERG: {
+      const T g = rx.p[0], a = rx.p[1], b = rx.p[2];
+      const T u2v = u * u * v;
+      gu = g * (a - u + u2v);
+      gv = g * (b - u2v);
+    } break;
+    case ADR_FHN: {
+      const T e = rx.p[0], a1 = rx.p[1], a0 = rx.p[2];
+      gu = u - u * u * u - v;
+      gv = e * (u - a1 * v - a0);
+    } break;
+    case ADR_BRUSSELATOR: {
+      const T a = rx.p[0], b = rx.p[1];
+      const T u2v = u * u * v;
+      gu = a - (b + (T)1) * u + u2v;
+      gv = b * u - u2v;
+    } break;
+    default:
+      gu = (T)0;
+      gv = (T)0;
+  }
+}
+
+// One direction of the tridiagonal action at one point, in difference form
+// (the rows sum to zero): interior lo (x_{i-1} - x_i) + up (x_{i+1} - x_i),
+// Neumann rows b0 (x_1 - x_0) and bn (x_{n-2} - x_{n-1}).
+template <typename T>
+__device__ __forceinline__ T stencil_dir(const T* __restrict__ x, int64_t idx, int64_t stride,
+                                         int i, int n, const TridiagT<T>& A) {
+  const T xc = x[idx];
+  if (i == 0) return A.b0 * (x[idx + stride] - xc);
+  if (i == n - 1) return A.bn * (x[idx - stride] - xc);
+  return A.lo * (x[idx - stride] - xc) + A.up * (x[idx + stride] - xc);
+}
+
+// W^c = sum_mu (A_mu^c U^c) + G^c(U, V) at the point with coordinates
+// (i1, i2, i3) and linear index idx; writes both components.
+template <typename T>
+__device__ __forceinline__ void rhs_point(const PointwiseArgsT<T>& a, const T* __restrict__ u,
+                                          const T* __restrict__ v, int64_t idx, int i1, int i2,
+                                          int i3, T& wu, T& wv) {
+  const int n1 = (int)a.n[0], n2 = (int)a.n[1];
+  T ku = stencil_dir(u, idx, 1, i1, n1, a.A[0][0]) +
+         stencil_dir(u, idx, (int64_t)n1, i2, n2, a.A[0][1]);
+  T kv = stencil_dir(v, idx, 1, i1, n1, a.A[1][0]) +
+         stencil_dir(v, idx, (int64_t)n1, i2, n2, a.A[1][1]);
+  if (a.d == 3) {
+    const int n3 = (int)a.n[2];
+    ku += stencil_dir(u, idx, (int64_t)n1 * n2, i3, n3, a.A[0][2]);
+    kv += stencil_dir(v, idx, (int64_t)n1 * n2, i3, n3, a.A[1][2]);
+  }
+  T gu, gv;
+  react<T>(a.rx, u[idx], v[idx], gu, gv);
+  wu = ku + gu;
+  wv = kv + gv;
+}
+
+}  // namespace adr

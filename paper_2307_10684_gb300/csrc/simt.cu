@@ -6,73 +6,26 @@
 #include <stdint.h>
 
 #include "adr_internal.h"
+#include "pointwise.cuh"
 
 namespace adr {
 
-// ---------------------------------------------------------------- reactions
 template <typename T>
-__device__ __forceinline__ void react(const ReactionParams& rx, T u, T v, T& gu, T& gv) {
-  switch (rx.model) {
-    case ADR_SCHNAKENBERG: {
-      const T g = (T)rx.p[0], a = (T)rx.p[1], b = (T)rx.p[2];
-      const T u2v = u * u * v;
-      gu = g * (a - u + u2v);
-      gv = g * (b - u2v);
-    } break;
-    case ADR_FHN: {
-      const T e = (T)rx.p[0], a1 = (T)rx.p[1], a0 = (T)rx.p[2];
-      gu = u - u * u * u - v;
-      gv = e * (u - a1 * v - a0);
-    } break;
-    case ADR_BRUSSELATOR: {
-      const T a = (T)rx.p[0], b = (T)rx.p[1];
-      const T u2v = u * u * v;
-      gu = a - (b + (T)1) * u + u2v;
-      gv = b * u - u2v;
-    } break;
-    default:
-      gu = (T)0;
-      gv = (T)0;
-  }
-}
-
-// One direction of the tridiagonal Kronecker-sum action at one point, in
-// difference form (the rows sum to zero).
-template <typename T>
-__device__ __forceinline__ T stencil_dir(const T* __restrict__ x, int64_t idx, int64_t stride,
-                                         int64_t i, int64_t n, const Tridiag& A) {
-  const T xc = x[idx];
-  if (i == 0) return (T)A.b0 * (x[idx + stride] - xc);
-  if (i == n - 1) return (T)A.bn * (x[idx - stride] - xc);
-  return (T)A.lo * (x[idx - stride] - xc) + (T)A.up * (x[idx + stride] - xc);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) rhs_kernel(PointwiseArgs a, const T* __restrict__ u,
+__global__ void __launch_bounds__(128) rhs_kernel(PointwiseArgsT<T> a, const T* __restrict__ u,
                                                   const T* __restrict__ v, T* __restrict__ wu,
                                                   T* __restrict__ wv) {
-  const int64_t n1 = a.n[0], n2 = a.n[1], n3 = a.d == 3 ? a.n[2] : 1;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.N;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i1 = idx % n1;
-    const int64_t r = idx / n1;
-    const int64_t i2 = r % n2;
-    const int64_t i3 = r / n2;
-    T ku = stencil_dir(u, idx, 1, i1, n1, a.A[0][0]) + stencil_dir(u, idx, n1, i2, n2, a.A[0][1]);
-    T kv = stencil_dir(v, idx, 1, i1, n1, a.A[1][0]) + stencil_dir(v, idx, n1, i2, n2, a.A[1][1]);
-    if (a.d == 3) {
-      ku += stencil_dir(u, idx, n1 * n2, i3, n3, a.A[0][2]);
-      kv += stencil_dir(v, idx, n1 * n2, i3, n3, a.A[1][2]);
-    }
-    T gu, gv;
-    react<T>(a.rx, u[idx], v[idx], gu, gv);
-    wu[idx] = ku + gu;
-    wv[idx] = kv + gv;
-  }
+  const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i1 >= (int)a.n[0]) return;
+  const int i2 = blockIdx.y, i3 = blockIdx.z;
+  const int64_t idx = ((int64_t)i3 * a.n[1] + i2) * a.n[0] + i1;
+  T x, y;
+  rhs_point<T>(a, u, v, idx, i1, i2, i3, x, y);
+  wu[idx] = x;
+  wv[idx] = y;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) rdiff_kernel(PointwiseArgs a, const T* __restrict__ u,
+__global__ void __launch_bounds__(256) rdiff_kernel(PointwiseArgsT<T> a, const T* __restrict__ u,
                                                     const T* __restrict__ v,
                                                     const T* __restrict__ u2,
                                                     const T* __restrict__ v2, T* __restrict__ du,
@@ -94,27 +47,28 @@ static int pointwise_grid(int64_t N) {
 }
 
 template <typename T>
-cudaError_t launch_rhs(const PointwiseArgs& a, const T* u, const T* v, T* wu, T* wv,
+cudaError_t launch_rhs(const PointwiseArgsT<T>& a, const T* u, const T* v, T* wu, T* wv,
                        cudaStream_t s) {
-  rhs_kernel<T><<<pointwise_grid(a.N), 256, 0, s>>>(a, u, v, wu, wv);
+  dim3 grid((unsigned)((a.n[0] + 127) / 128), (unsigned)a.n[1], (unsigned)(a.d == 3 ? a.n[2] : 1));
+  rhs_kernel<T><<<grid, 128, 0, s>>>(a, u, v, wu, wv);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_rdiff(const PointwiseArgs& a, const T* u, const T* v, const T* u2, const T* v2,
+cudaError_t launch_rdiff(const PointwiseArgsT<T>& a, const T* u, const T* v, const T* u2, const T* v2,
                          T* du, T* dv, cudaStream_t s) {
   rdiff_kernel<T><<<pointwise_grid(a.N), 256, 0, s>>>(a, u, v, u2, v2, du, dv);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_rhs<float>(const PointwiseArgs&, const float*, const float*, float*,
+template cudaError_t launch_rhs<float>(const PointwiseArgsT<float>&, const float*, const float*, float*,
                                        float*, cudaStream_t);
-template cudaError_t launch_rhs<double>(const PointwiseArgs&, const double*, const double*,
+template cudaError_t launch_rhs<double>(const PointwiseArgsT<double>&, const double*, const double*,
                                         double*, double*, cudaStream_t);
-template cudaError_t launch_rdiff<float>(const PointwiseArgs&, const float*, const float*,
+template cudaError_t launch_rdiff<float>(const PointwiseArgsT<float>&, const float*, const float*,
                                          const float*, const float*, float*, float*,
                                          cudaStream_t);
-template cudaError_t launch_rdiff<double>(const PointwiseArgs&, const double*, const double*,
+template cudaError_t launch_rdiff<double>(const PointwiseArgsT<double>&, const double*, const double*,
                                           const double*, const double*, double*, double*,
                                           cudaStream_t);
 
@@ -225,15 +179,24 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs g) {
   for (int i = 0; i < TM; ++i) {
     const int r = m0 + (i / 4) * (BM / RS) + ty * 4 + (i % 4);
     if (r >= g.M) continue;
+    // gather the row's epilogue inputs before any store (C may share no
+    // memory with base/base2, but the compiler cannot assume it)
+    T extra[TN];
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int c = n0 + (j / 4) * (BN / CS) + tx * 4 + (j % 4);
-      if (c >= g.N) continue;
       const int64_t o = (int64_t)r * g.ldc + c;
-      T val = alpha * acc[i][j];
-      if (base) val += beta * base[o];
-      if (base2) val += beta2 * base2[o];
-      C[o] = val;
+      T x = (T)0;
+      if (c < g.N) {
+        if (base) x += beta * base[o];
+        if (base2) x += beta2 * base2[o];
+      }
+      extra[j] = x;
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int c = n0 + (j / 4) * (BN / CS) + tx * 4 + (j % 4);
+      if (c < g.N) C[(int64_t)r * g.ldc + c] = alpha * acc[i][j] + extra[j];
     }
   }
 }

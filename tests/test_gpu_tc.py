@@ -1,0 +1,130 @@
+"""Tensor-core (tcgen05, BF16x3 split precision) path vs the FP64 oracle.
+
+Tolerance: the 1e-5 max relative error bound (per component
+||X - X_ref||_inf / ||X_ref||_inf, maximum over u and v).  The BF16x3 split
+carries about 24 significant bits per operand, the same class as FP32.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from oracle import schemes
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def adr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2307_10684_gb300 import build
+    build.build()
+    import paper_2307_10684_gb300 as adr
+    return adr
+
+
+def run(adr, p, u0, v0, nsteps, precision=wl.BF16X3):
+    import torch
+    dt = adr.state_dtype(precision)
+    u = torch.tensor(u0, dtype=dt, device="cuda")
+    v = torch.tensor(v0, dtype=dt, device="cuda")
+    with adr.Plan(p.replace(precision=precision)) as plan:
+        plan.set_timing(True)
+        plan.step(u, v, nsteps)
+        st = plan.stats()
+    assert st["device_error"] == 0
+    return u.double().cpu().numpy(), v.double().cpu().numpy(), st
+
+
+def inputs(p, kind="auto", amp=None):
+    u0, v0 = wl.initial_data(p, kind=kind, amp=amp)
+    return wl.round_to(u0, wl.FP32), wl.round_to(v0, wl.FP32)
+
+
+@pytest.mark.parametrize("n", [(64, 64), (200, 136), (24, 40, 56)])
+def test_linear_stage_one(adr, n):
+    """g = 0: the step is U + tau (K U) x_mu phi_1 (stage 2 adds zero), which
+    isolates the stencil kernel and the stage-1 tensor-core products."""
+    d = len(n)
+    p = wl.Problem(d=d, n=n, lo=(0.0,) * d, hi=(1.0,) * d, diff=(0.02, 0.05),
+                   adv=((0.3,) * d, (-0.2,) * d), model=wl.NO_REACTION, params=(),
+                   tau=1e-2, nsteps=1, seed=21)
+    u0, v0 = inputs(p, kind="uniform", amp=0.5)
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, 1)
+    U, V, st = run(adr, p, u0, v0, 1)
+    assert st["kernels"]["mode_product_tc"]["count"] == 2 * d
+    assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+@pytest.mark.parametrize("n,model", [((200, 136), wl.FHN), ((128, 256), wl.SCHNAKENBERG),
+                                     ((40, 24, 56), wl.BRUSSELATOR), ((8, 16, 8), wl.FHN)])
+def test_ragged_shapes_bf16x3(adr, n, model):
+    d = len(n)
+    params = {wl.SCHNAKENBERG: (200.0, 0.1, 0.9), wl.FHN: (0.05, 2.0, -0.03),
+              wl.BRUSSELATOR: (1.0, 3.0)}[model]
+    p = wl.Problem(d=d, n=n, lo=(0.0,) * d, hi=(1.0,) * d, diff=(0.05, 0.3),
+                   adv=((0.2, -0.1, 0.3)[:d], (-0.2, 0.1, 0.05)[:d]), model=model,
+                   params=params, tau=2e-3, nsteps=10, seed=13)
+    u0, v0 = inputs(p, kind="uniform")
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, p.nsteps)
+    U, V, _ = run(adr, p, u0, v0, p.nsteps)
+    assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+@pytest.mark.parametrize("fuse", ["0", "1"])
+@pytest.mark.parametrize("n", [(72, 200), (24, 40, 56)])
+def test_stage_one_fusion_both_ways(adr, n, fuse, monkeypatch):
+    """The stage-1 combination and reaction difference either fused into the
+    last tensor-core product (pair units) or done by a separate kernel must
+    both match the oracle."""
+    monkeypatch.setenv("ADR_TC_FUSE", fuse)
+    d = len(n)
+    p = wl.Problem(d=d, n=n, lo=(0.0,) * d, hi=(1.0,) * d, diff=(0.05, 0.3),
+                   adv=((0.2, -0.1, 0.3)[:d], (-0.2, 0.1, 0.05)[:d]), model=wl.SCHNAKENBERG,
+                   params=(300.0, 0.1, 0.9), tau=1e-3, nsteps=6, seed=17)
+    u0, v0 = inputs(p, kind="uniform")
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, p.nsteps)
+    U, V, st = run(adr, p, u0, v0, p.nsteps)
+    assert st["kernels"]["reaction_diff"]["count"] == (0 if fuse == "1" else p.nsteps)
+    assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+def test_fhn_1024_full_size_steps(adr):
+    p = wl.fhn_1024(precision=wl.BF16X3)
+    u0, v0 = inputs(p)
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, 3)
+    U, V, _ = run(adr, p, u0, v0, 3)
+    assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+def test_brusselator_256_full_size_step(adr):
+    p = wl.brusselator_256(precision=wl.BF16X3)
+    u0, v0 = inputs(p)
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, 1)
+    U, V, _ = run(adr, p, u0, v0, 1)
+    assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+def test_unsupported_grid_rejected(adr):
+    p = wl.fhn_1024(precision=wl.BF16X3, n=100)  # 100 % 8 != 0
+    with pytest.raises(adr.AdrError) as ei:
+        adr.Plan(p)
+    assert ei.value.status == adr.ADR_EUNSUPPORTED
+
+
+def test_bf16x3_not_less_accurate_than_fp32(adr):
+    """On a 256^2 FHN run of 100 steps the split-precision tensor-core result
+    is at least as close to FP64 as the plain FP32 result (within 2x)."""
+    p = wl.fhn_1024(n=256, nsteps=100)
+    u0, v0 = inputs(p)
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, p.nsteps)
+    Ub, Vb, _ = run(adr, p, u0, v0, p.nsteps, wl.BF16X3)
+    Uf, Vf, _ = run(adr, p, u0, v0, p.nsteps, wl.FP32)
+    eb = oracle.max_rel_err(Ub, Vb, Ur, Vr)
+    ef = oracle.max_rel_err(Uf, Vf, Ur, Vr)
+    assert eb <= TOL and ef <= TOL
+    assert eb <= 2.0 * ef, (eb, ef)
