@@ -171,6 +171,23 @@ adr_status adr_plan_stats(adr_plan plan, adr_stats* out);
 adr_status adr_max_abs_diff(void* stream, const void* x, int x_is_double, const double* ref,
                             int64_t count, double out[2]);
 
+/* Same result as adr_max_abs_diff, but allocates no device memory.  The
+ * paper has no counterpart: this is a service for callers that cannot
+ * allocate at the point where they check a result (a serving loop whose
+ * device-memory budget is fully committed, a host application that owns the
+ * CUDA allocator, code that must avoid cudaFree's implicit synchronisation).
+ * Scratch is a 256 KB device array inside the library image, held by every
+ * GPU that loads the library until the process exits.  Limit: count <=
+ * 67,108,864 (2^26) elements; larger counts return ADR_EINVAL and enqueue
+ * nothing.  The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array, so calls that
+ * overlap on the GPU (different streams, or different host threads) race and
+ * may return each other's results.  Enqueued on `stream`, synchronised before
+ * returning; out: host. */
+adr_status adr_max_abs_diff_noalloc(void* stream, const void* x, int x_is_double,
+                                    const double* ref, int64_t count, double out[2]);
+
 /* Short name of a status code (static storage). */
 const char* adr_status_str(adr_status s);
 /* Message describing the last failure on the calling host thread. */

@@ -48,6 +48,8 @@ SIGNATURES = {
     "adr_plan_stats": (c_int32, [AdrPlan, ctypes.POINTER(AdrStats)]),
     "adr_max_abs_diff": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int64,
                                    ctypes.POINTER(c_double)]),
+    "adr_max_abs_diff_noalloc": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int64,
+                                           ctypes.POINTER(c_double)]),
     "adr_status_str": (ctypes.c_char_p, [c_int32]),
     "adr_last_error": (ctypes.c_char_p, []),
 }
