@@ -156,6 +156,13 @@ struct adr_plan_s {
   std::vector<TimedLaunch> timed;
   std::vector<cudaEvent_t> event_pool;
   size_t event_next;
+  // CUDA graph of kGraphChunk steps for one (u, v) pair, replayed by adr_step
+  int use_graphs;
+  cudaStream_t cap_stream;   // internal stream used only for capture
+  cudaGraphExec_t gexec;
+  void* g_u;
+  void* g_v;
+  int64_t g_launches;        // kernels per replay
 };
 
 

@@ -13,6 +13,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <string>
@@ -202,6 +203,8 @@ static void plan_free(adr_plan P) {
   if (P->stream) cudaStreamSynchronize(P->stream);
   for (void* q : P->allocs) cudaFree(q);
   for (cudaEvent_t e : P->event_pool) cudaEventDestroy(e);
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   tc_free(&P->tc);
   delete P;
 }
@@ -229,6 +232,12 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
   P->event_next = 0;
   P->u2 = P->v2 = nullptr;
   P->dstate[0] = P->dstate[1] = nullptr;
+  P->gexec = nullptr;
+  P->g_u = P->g_v = nullptr;
+  P->g_launches = 0;
+  P->cap_stream = nullptr;
+  P->use_graphs = 1;
+  if (const char* ev = getenv("ADR_GRAPHS")) P->use_graphs = atoi(ev) != 0;
   tc_init(&P->tc);
 
   PointwiseArgs& pw = P->pw;
@@ -303,6 +312,7 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
       return unsup ? ADR_EUNSUPPORTED : ADR_ECUDA;
     }
   }
+  PLAN_TRY(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   PLAN_TRY(cudaStreamSynchronize(P->stream));
   PLAN_TRY(cudaGetLastError());
 #undef PLAN_TRY
@@ -324,7 +334,7 @@ static bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static adr_status step_impl(adr_plan P, void* u, void* v, int64_t nsteps) {
+static cudaError_t step_direct(adr_plan P, void* u, void* v, int64_t nsteps) {
   for (int64_t s = 0; s < nsteps; ++s) {
     cudaError_t e;
     if (P->prec == ADR_FP64)
@@ -333,11 +343,67 @@ static adr_status step_impl(adr_plan P, void* u, void* v, int64_t nsteps) {
       e = step_simt<float>(P, (float*)u, (float*)v);
     else
       e = tc_step(&P->tc, P, u, v);
-    if (e != cudaSuccess)
-      return fail(e == cudaErrorNotSupported ? ADR_EUNSUPPORTED : ADR_ECUDA,
-                  std::string("adr_step: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return e;
     P->steps++;
   }
+  return cudaSuccess;
+}
+
+// Steps per captured graph.  A step is 5-8 launches, so a chunk replays a few
+// hundred kernels per cudaGraphLaunch.
+static constexpr int64_t kGraphChunk = 32;
+
+// Capture kGraphChunk steps on (u, v) into P->gexec.  On any failure graphs
+// are switched off for this plan and the caller launches directly.
+static void build_graph(adr_plan P, void* u, void* v) {
+  if (P->gexec) {
+    cudaGraphExecDestroy(P->gexec);
+    P->gexec = nullptr;
+  }
+  const int64_t l0 = P->launches, s0 = P->steps;
+  cudaStream_t saved = P->stream;
+  P->stream = P->cap_stream;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = step_direct(P, u, v, kGraphChunk);
+    cudaError_t e2 = cudaStreamEndCapture(P->cap_stream, &g);
+    e = e1 != cudaSuccess ? e1 : e2;
+  }
+  P->stream = saved;
+  P->g_launches = P->launches - l0;
+  P->launches = l0;
+  P->steps = s0;
+  if (e == cudaSuccess && g) e = cudaGraphInstantiate(&P->gexec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    P->gexec = nullptr;
+    P->use_graphs = 0;
+    return;
+  }
+  P->g_u = u;
+  P->g_v = v;
+}
+
+static adr_status step_impl(adr_plan P, void* u, void* v, int64_t nsteps) {
+  int64_t done = 0;
+  if (P->use_graphs && !P->timing && nsteps >= kGraphChunk) {
+    if (!P->gexec || P->g_u != u || P->g_v != v) build_graph(P, u, v);
+    if (P->gexec) {
+      for (; done + kGraphChunk <= nsteps; done += kGraphChunk) {
+        cudaError_t e = cudaGraphLaunch(P->gexec, P->stream);
+        if (e != cudaSuccess)
+          return fail(ADR_ECUDA, std::string("adr_step: cudaGraphLaunch: ") + cudaGetErrorString(e));
+        P->launches += P->g_launches;
+        P->steps += kGraphChunk;
+      }
+    }
+  }
+  cudaError_t e = step_direct(P, u, v, nsteps - done);
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorNotSupported ? ADR_EUNSUPPORTED : ADR_ECUDA,
+                std::string("adr_step: ") + cudaGetErrorString(e));
   return ADR_OK;
 }
 

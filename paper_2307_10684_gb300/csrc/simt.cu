@@ -201,11 +201,56 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs g) {
   }
 }
 
+// Small-problem variant: an 8 x 8 output tile per 64-thread CTA, one output
+// per thread.  Used when the register-blocked kernel would leave most SMs
+// idle (GB300 runs FP64 at about two FMAs per clock per SM, so a 64^3
+// product on a single SM takes tens of microseconds).
+template <typename T>
+__global__ void __launch_bounds__(64) gemm_small_kernel(GemmArgs g) {
+  constexpr int TS = 8;
+  __shared__ T As[TS][TS + 1];
+  __shared__ T Bs[TS][TS + 1];
+  const int z = blockIdx.z;
+  const int comp = z / g.batch;
+  const int p = z - comp * g.batch;
+  const T* __restrict__ A = (const T*)g.A[comp] + (int64_t)p * g.a_bs;
+  const T* __restrict__ B = (const T*)g.B[comp] + (int64_t)p * g.b_bs;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  const int r = blockIdx.y * TS + ty, c = blockIdx.x * TS + tx;
+  T acc = (T)0;
+  for (int k0 = 0; k0 < g.K; k0 += TS) {
+    As[ty][tx] = (r < g.M && k0 + tx < g.K) ? A[(int64_t)r * g.lda + k0 + tx] : (T)0;
+    Bs[ty][tx] = (k0 + ty < g.K && c < g.N) ? B[(int64_t)(k0 + ty) * g.ldb + c] : (T)0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < TS; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
+    __syncthreads();
+  }
+  if (r < g.M && c < g.N) {
+    const int64_t o = (int64_t)r * g.ldc + c;
+    T* __restrict__ C = (T*)g.C[comp] + (int64_t)p * g.c_bs;
+    T x = (T)g.alpha * acc;
+    if (g.base[comp]) x += (T)g.beta * ((const T*)g.base[comp] + (int64_t)p * g.c_bs)[o];
+    if (g.base2[comp]) x += (T)g.beta2 * ((const T*)g.base2[comp] + (int64_t)p * g.c_bs)[o];
+    C[o] = x;
+  }
+}
+
 template <typename T>
 cudaError_t launch_gemm_simt(const GemmArgs& g, cudaStream_t s) {
   using Cfg = SimtTile<T>;
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   dim3 grid((g.N + Cfg::BN - 1) / Cfg::BN, (g.M + Cfg::BM - 1) / Cfg::BM, g.batch * g.ncomp);
+  // FP64 runs ~40x slower per SM than FP32, so FP64 products spread over
+  // small tiles whenever the large tiles leave SMs idle; FP32 only for tiny
+  // problems
+  const int64_t min_ctas = sizeof(T) == 8 ? 152 : 32;
+  if ((int64_t)grid.x * grid.y * grid.z < min_ctas) {
+    dim3 sg((g.N + 7) / 8, (g.M + 7) / 8, g.batch * g.ncomp);
+    if (sg.y > 65535 || sg.z > 65535) return cudaErrorInvalidConfiguration;
+    gemm_small_kernel<T><<<sg, 64, 0, s>>>(g);
+    return cudaGetLastError();
+  }
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
   gemm_simt_kernel<T><<<grid, 256, 0, s>>>(g);
   return cudaGetLastError();

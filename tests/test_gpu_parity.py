@@ -205,3 +205,25 @@ def test_timing_stats(adr):
     assert st["steps"] == 4 and st["launches"] == 4 * 6
     k = st["kernels"]["mode_product_simt"]
     assert k["count"] == 16 and k["ms"] > 0 and k["flops"] == pytest.approx(16 * 4 * 128 * 128 * 128)
+
+
+@pytest.mark.parametrize("precision", [wl.FP64, wl.FP32, wl.BF16X3])
+def test_graph_replay_matches_direct_launches(adr, precision, monkeypatch):
+    """adr_step replays captured CUDA graphs for runs of >= 32 steps; the
+    result must be bitwise identical to launching every kernel directly."""
+    import torch
+    p = wl.fhn_1024(precision=precision, n=64, nsteps=70)
+    u0, v0 = inputs(p, precision)
+    dt = adr.state_dtype(precision)
+    outs = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("ADR_GRAPHS", graphs)
+        u = torch.tensor(u0, dtype=dt, device="cuda")
+        v = torch.tensor(v0, dtype=dt, device="cuda")
+        with adr.Plan(p) as plan:
+            plan.step(u, v, p.nsteps)
+            st = plan.stats()
+        outs.append((u.cpu(), v.cpu(), st))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    assert outs[0][2]["launches"] == outs[1][2]["launches"]
+    assert outs[0][2]["steps"] == outs[1][2]["steps"] == p.nsteps
