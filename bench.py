@@ -190,6 +190,166 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """512 independent 2D solves of uneven sizes advanced together by grouped
+    launches (one bench step = all solves x 100 ETD2RKds steps)."""
+    import torch
+    import paper_2307_10684_gb300 as adr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = PREC[args.precision]
+    probs = wl.batched_512(precision=prec)
+    nts = args.time_steps or probs[0].nsteps
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    plans = [adr.Plan(p) for p in probs]
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    dt = adr.state_dtype(prec)
+    init = []
+    for p in probs:
+        u0, v0 = wl.initial_data(p)
+        init.append((torch.tensor(wl.round_to(u0, prec), dtype=dt, device="cuda"),
+                     torch.tensor(wl.round_to(v0, prec), dtype=dt, device="cuda")))
+    us = [torch.empty_like(a) for a, _ in init]
+    vs = [torch.empty_like(b) for _, b in init]
+    batch = adr.Batch(plans)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    npts = sum(p.npoints for p in probs)
+
+    def one_solve():
+        for (a, b), u, v in zip(init, us, vs):
+            u.copy_(a)
+            v.copy_(b)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.step(us, vs, nts)
+        e1.record(stream)
+        return e0, e1
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+    # accuracy: a sample of solves against FP64 GPU plans of the same data
+    max_rel = None
+    if not args.no_check:
+        max_rel = 0.0
+        sample = list(range(0, len(probs), 32))
+        for i in sample:
+            p64 = probs[i].replace(precision=wl.FP64)
+            ur = init[i][0].double().clone()
+            vr = init[i][1].double().clone()
+            with adr.Plan(p64) as pl:
+                pl.step(ur, vr, nts)
+            du, mu = adr.max_abs_diff(us[i], ur)
+            dv, mv = adr.max_abs_diff(vs[i], vr)
+            max_rel = max(max_rel, du / mu, dv / mv)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    batch.set_timing(False)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [one_solve() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = batch.stats()["launches"]
+    clocks = sampler.stop()
+    tot_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * npts * nts * args.steps / (tot_ms / 1e3)
+    batch.set_timing(True)
+    for _ in range(args.steps):
+        one_solve()
+    torch.cuda.synchronize()
+    stats = batch.stats()
+    batch.set_timing(False)
+    # end to end: pinned host states copied in and out inside the timed region
+    hin = [(a.cpu().pin_memory(), b.cpu().pin_memory()) for a, b in init]
+    hout = [(torch.empty_like(a), torch.empty_like(b)) for a, b in hin]
+    hout = [(a.pin_memory(), b.pin_memory()) for a, b in hout]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for (ha, hb), u, v in zip(hin, us, vs):
+            u.copy_(ha, non_blocking=True)
+            v.copy_(hb, non_blocking=True)
+        batch.step(us, vs, nts)
+        for (oa, ob), u, v in zip(hout, us, vs):
+            oa.copy_(u, non_blocking=True)
+            ob.copy_(v, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    nbytes = sum(a.numel() * a.element_size() * 2 for a, _ in hin)
+    e2e = {"value": world * npts * nts * args.steps / e2e_s, "unit": "point-steps/s",
+           "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes)}
+    peaks, peak_src = load_peaks()
+    kern = {k: d for k, d in stats["kernels"].items() if d["count"] > 0}
+    kd = kern["mode_product_tc"] if "mode_product_tc" in kern else max(kern.values(), key=lambda d: d["ms"])
+    ratio = 0.5 if prec == wl.TF32X3 else 1.0
+    peak = peaks["bf16_tflops"] * 1e12 * ratio
+    achieved = (kd["flops"] / kd["count"]) / (kd["ms"] / kd["count"] / 1e3)
+    roof = {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak, "issued_frac": 6.0 * achieved / peak, "traffic": None,
+            "kernel": "mode_product_tc (grouped over 512 solves)",
+            "peak_source": f"{peak_src} bf16 (dense)",
+            "share_of_kernel_time": kd["ms"] / sum(d["ms"] for d in kern.values())}
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
+        from oracle import schemes
+        cores = len(os.sched_getaffinity(0))
+        sample = [probs[i] for i in range(0, len(probs), 64)]
+        steps = max(1, args.cpu_sample // 8)
+        tot = 0.0
+        pts = 0
+        for p in sample:
+            u0, v0 = wl.initial_data(p)
+            plan = schemes.make_plan(p)
+            t1 = time.perf_counter()
+            schemes.etd2rkds_solve(plan, wl.round_to(u0, prec), wl.round_to(v0, prec), steps)
+            tot += time.perf_counter() - t1
+            pts += p.npoints * steps
+        cpu = {"value": pts / tot, "unit": "point-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{steps} steps of each of {len(sample)} batch solves (every 64th)"}
+    if rank == 0:
+        line = {"metric": "point-steps/s", "value": value, "unit": "point-steps/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": DTYPE_NAME[prec],
+                "data": "synthetic (seeded SplitMix64; 512 solves, seeds 1000+i)",
+                "config": {"workload": "batched 512 2D solves, sides {64..512}, 100 steps",
+                           "points": npts, "time_steps_per_bench_step": nts,
+                           "precision": args.precision, "grouped": batch.grouped,
+                           "l2": "flushed between timed solves (256 MB write)",
+                           "parallelism": f"replicas x{world}"},
+                "max_rel_err_vs_fp64": max_rel, "max_rel_err_sample": "every 32nd solve",
+                "plan_ms": plan_ms, "e2e": e2e, "gpu_launches": launches,
+                "kernel_timing": "second pass of the same solves with CUDA events around "
+                                 "each launch",
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "kernels": {k: {"count": d["count"], "avg_us": 1e3 * d["ms"] / d["count"]}
+                            for k, d in kern.items()}}
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for pl in plans:
+        pl.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -209,6 +369,9 @@ def main():
 
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload == "batch512":
+        run_batch(args)
         return
 
     import torch

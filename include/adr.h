@@ -164,6 +164,33 @@ adr_status adr_plan_set_timing(adr_plan plan, int enable);
  * usable and the word is cleared by adr_plan_set_timing. */
 adr_status adr_plan_stats(adr_plan plan, adr_stats* out);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent solves (SURVEY config "batched") advanced together.  When
+ * every plan is ADR_BF16X3 with the same d, one step of the whole batch is a
+ * fixed set of grouped launches: one stencil launch, one launch per mode
+ * product covering every solve's tiles (a persistent tcgen05 kernel reading
+ * per-solve descriptors), one reaction-difference launch; runs of 16 steps
+ * replay a captured CUDA graph.  Other batches step their plans in turn.
+ * The batch uses the plans' matrices and workspaces: while a batch steps, do
+ * not step its plans on their own.  The plans must outlive the batch. */
+typedef struct adr_batch_s* adr_batch;
+
+/* Build a batch of `count` plans (host array, copied); launches go to
+ * `stream`.  Synchronous. */
+adr_status adr_batch_create(const adr_plan* plans, int count, void* stream, adr_batch* out);
+adr_status adr_batch_destroy(adr_batch batch);
+/* Advance solve i's device state (u[i], v[i]) by nsteps steps, all solves in
+ * lock-step; u and v are host arrays of `count` device pointers.  The first
+ * call with a new set of pointers uploads the per-solve descriptors
+ * (synchronous); later calls are asynchronous. */
+adr_status adr_batch_step(adr_batch batch, void* const* u, void* const* v, int64_t nsteps);
+/* Timing and counters of the batch's launches (as for plans). */
+adr_status adr_batch_set_timing(adr_batch batch, int enable);
+adr_status adr_batch_stats(adr_batch batch, adr_stats* out);
+/* 1 when the batch runs grouped tensor-core launches, 0 when it steps its
+ * plans in turn. */
+int adr_batch_is_grouped(adr_batch batch);
+
 /* Error reduction (FP64 on the GPU): out[0] = max_i |x_i - ref_i|,
  * out[1] = max_i |ref_i| over `count` elements.  x: device array of float
  * (x_is_double = 0) or double (1); ref: device array of double.  out: host.

@@ -21,7 +21,7 @@ from ._abi import (ADR_OK, ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA, ADR_EUNSUPPORTED, 
                    ADR_ETIMEOUT, ADR_ENUMERIC, ADR_EBUSY, FP64, FP32, TF32X3, BF16X3,
                    SCHNAKENBERG, FHN, BRUSSELATOR, NO_REACTION, AdrError, lib, library_path)
 
-__all__ = ["Plan", "AdrError", "lib", "library_path", "plan_bytes", "max_abs_diff",
+__all__ = ["Plan", "Batch", "AdrError", "lib", "library_path", "plan_bytes", "max_abs_diff",
            "make_problem", "state_dtype"]
 
 
@@ -134,14 +134,69 @@ class Plan:
     def stats(self) -> dict:
         st = _abi.AdrStats()
         _abi.check(lib().adr_plan_stats(self._p, ctypes.byref(st)))
-        kernels = {}
-        for k in range(st.nkernels):
-            kernels[st.name[k].value.decode()] = {
-                "count": int(st.count[k]), "ms": float(st.ms[k]),
-                "flops": float(st.flops[k]), "bytes": float(st.bytes[k])}
-        return {"launches": int(st.launches), "steps": int(st.steps),
-                "timing": bool(st.timing), "device_error": int(st.device_error),
-                "kernels": kernels}
+        return _stats_dict(st)
+
+
+def _stats_dict(st) -> dict:
+    kernels = {}
+    for k in range(st.nkernels):
+        kernels[st.name[k].value.decode()] = {
+            "count": int(st.count[k]), "ms": float(st.ms[k]),
+            "flops": float(st.flops[k]), "bytes": float(st.bytes[k])}
+    return {"launches": int(st.launches), "steps": int(st.steps), "timing": bool(st.timing),
+            "device_error": int(st.device_error), "kernels": kernels}
+
+
+class Batch:
+    """An adr_batch over existing plans (kept alive by this object)."""
+
+    def __init__(self, plans, stream=None):
+        self.plans = list(plans)
+        arr = (_abi.AdrPlan * len(self.plans))(*[p._p for p in self.plans])
+        self._b = ctypes.c_void_p()
+        _abi.check(lib().adr_batch_create(arr, len(self.plans),
+                                          ctypes.c_void_p(_stream_handle(stream)),
+                                          ctypes.byref(self._b)))
+
+    @property
+    def grouped(self) -> bool:
+        return bool(lib().adr_batch_is_grouped(self._b))
+
+    def step(self, us, vs, nsteps: int = 1):
+        """Advance every solve i's CUDA tensors (us[i], vs[i]) in place."""
+        if len(us) != len(self.plans) or len(vs) != len(self.plans):
+            raise ValueError("one (u, v) pair per plan")
+        for p, u, v in zip(self.plans, us, vs):
+            p._check_state(u, True)
+            p._check_state(v, True)
+        U = (ctypes.c_void_p * len(us))(*[u.data_ptr() for u in us])
+        V = (ctypes.c_void_p * len(vs))(*[v.data_ptr() for v in vs])
+        _abi.check(lib().adr_batch_step(self._b, U, V, ctypes.c_int64(int(nsteps))))
+
+    def set_timing(self, enable: bool):
+        _abi.check(lib().adr_batch_set_timing(self._b, 1 if enable else 0))
+
+    def stats(self) -> dict:
+        st = _abi.AdrStats()
+        _abi.check(lib().adr_batch_stats(self._b, ctypes.byref(st)))
+        return _stats_dict(st)
+
+    def close(self):
+        if self._b:
+            lib().adr_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def plan_bytes(problem):

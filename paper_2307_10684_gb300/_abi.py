@@ -50,6 +50,14 @@ SIGNATURES = {
                                    ctypes.POINTER(c_double)]),
     "adr_max_abs_diff_noalloc": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int64,
                                            ctypes.POINTER(c_double)]),
+    "adr_batch_create": (c_int32, [ctypes.POINTER(AdrPlan), c_int32, c_void_p,
+                                   ctypes.POINTER(c_void_p)]),
+    "adr_batch_destroy": (c_int32, [c_void_p]),
+    "adr_batch_step": (c_int32, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                 c_int64]),
+    "adr_batch_set_timing": (c_int32, [c_void_p, c_int32]),
+    "adr_batch_stats": (c_int32, [c_void_p, ctypes.POINTER(AdrStats)]),
+    "adr_batch_is_grouped": (c_int32, [c_void_p]),
     "adr_status_str": (ctypes.c_char_p, [c_int32]),
     "adr_last_error": (ctypes.c_char_p, []),
 }

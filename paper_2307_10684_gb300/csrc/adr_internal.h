@@ -173,6 +173,7 @@ void tc_init(TcOperands* t);
 void tc_free(TcOperands* t);
 cudaError_t tc_prepare(TcOperands* t, int prec, int d, const int64_t n[3],
                        double* const master[2][3][4], cudaStream_t s);
+cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v);
 cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v);
 int* tc_error_word(TcOperands* t);
 

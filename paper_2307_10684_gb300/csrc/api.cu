@@ -388,6 +388,12 @@ static void build_graph(adr_plan P, void* u, void* v) {
 
 static adr_status step_impl(adr_plan P, void* u, void* v, int64_t nsteps) {
   int64_t done = 0;
+  if (nsteps == 0) return ADR_OK;
+  if (P->prec == ADR_TF32X3 || P->prec == ADR_BF16X3) {
+    cudaError_t e = tc_bind(&P->tc, P, u, v);
+    if (e != cudaSuccess)
+      return fail(ADR_ECUDA, std::string("adr_step: binding state buffers: ") + cudaGetErrorString(e));
+  }
   if (P->use_graphs && !P->timing && nsteps >= kGraphChunk) {
     if (!P->gexec || P->g_u != u || P->g_v != v) build_graph(P, u, v);
     if (P->gexec) {

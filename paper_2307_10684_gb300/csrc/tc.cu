@@ -184,9 +184,30 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& b0, __nv_bfloat16
   b2 = __float2bfloat16_rn(r2);
 }
 
-struct TcMaps {
-  CUtensorMap a[2];  // X pieces [3][M][K] per component
-  CUtensorMap b[2];  // Phi pieces [3][N][K] per component
+// ---------------------------------------------------------------- descriptors
+// Everything one unit of the mode-product kernel needs about its solve for
+// one pass.  Lives in device memory; a launch covers one or many solves
+// (a batch), each with its own sizes, tensor maps, outputs and step size.
+struct alignas(128) TcPassDesc {
+  CUtensorMap amap[2];      // X pieces [3][M][K] per component
+  CUtensorMap bmap[2];      // Phi pieces [3][N][K] per component
+  __nv_bfloat16* outp[2];   // [3][N][M] per component (kPieces3, kStage1)
+  float* outf[2];           // FP32 output per component (kStage1, kAxpy)
+  const float* base[2];     // FP32 base per component (kStage1, kAxpy)
+  int M, N, K;
+  int tiles_m, tiles_n;
+  int pair;                 // 1: unit = (u, v) tile pair; 0: unit = one tile of one component
+  int mode;                 // TcMode
+  float alpha;
+  ReactionT<float> rx;
+};
+
+struct TcLaunch {
+  const TcPassDesc* desc;   // [nsolves]
+  const int* ustart;        // [nsolves + 1] prefix sums of units
+  int nsolves;
+  int nunits;
+  int* err;
 };
 
 // Epilogue of one mode-product pass.
@@ -197,52 +218,62 @@ enum TcMode : int {
   kAxpy = 2       // out = base + alpha acc (FP32)
 };
 
-struct TcEpilogue {
-  int mode;
-  int M, N, K;
-  int tiles_m, tiles_n, nunits;
-  int pair;                      // 1: unit = (u, v) tile pair; 0: unit = one tile of one component
-  __nv_bfloat16* outp[2];        // [3][N][M] per component (kPieces3, kStage1)
-  float* outf[2];                // FP32 output per component (kStage1, kStage2)
-  const float* base[2];          // FP32 base per component (kStage1, kStage2)
-  float alpha;
-  ReactionT<float> rx;
-  int* err;
-};
-
 // The six piece pairs (i, j): A piece i times B piece j, smallest first.
 __device__ __constant__ int kPairA[6] = {1, 0, 2, 0, 1, 0};
 __device__ __constant__ int kPairB[6] = {1, 2, 0, 1, 0, 0};
 
-// Components and tile index of unit u.
-__device__ __forceinline__ void unit_comps(const TcEpilogue& e, int u, int& c_lo, int& c_hi,
-                                           int& r) {
-  if (e.pair) {
-    c_lo = 0;
-    c_hi = 2;
-    r = u;
-  } else {
-    const int per = e.tiles_m * e.tiles_n;
-    c_lo = u / per;
-    c_hi = c_lo + 1;
-    r = u - c_lo * per;
-  }
-}
-
 constexpr int kEpiWarps = 8;                  // two warps per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue
 
-// Persistent kernel.  CTA b handles units b, b + gridDim.x, ...; unit ->
-// (m-tile, n-tile) with the n-tile fastest so that CTAs running together
-// share A tiles in L2.  For each unit the MMA warp accumulates the u tile and
-// then the v tile into one of two TMEM slots (4 accumulators of BN columns),
-// so the epilogue of one unit overlaps the MMAs of the next and sees both
-// components of every point.  Epilogue warp w owns TMEM lane quarter w % 4
-// and half (w - 2) / 4 of the columns; it prefetches its FP32 base values
-// two 16-column chunks ahead, starting before the accumulator is ready.
+// Largest s with start[s] <= x (start[0] = 0, start[n] = total > x).
+__device__ __forceinline__ int find_segment(const int* __restrict__ start, int n, int x) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(start + mid) <= x)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+struct Unit {
+  const TcPassDesc* d;
+  int m0, n0, c_lo, c_hi;
+};
+
+template <int BN>
+__device__ __forceinline__ Unit decode_unit(const TcLaunch& L, int u) {
+  Unit w;
+  const int s = find_segment(L.ustart, L.nsolves, u);
+  w.d = L.desc + s;
+  int r = u - __ldg(L.ustart + s);
+  if (w.d->pair) {
+    w.c_lo = 0;
+    w.c_hi = 2;
+  } else {
+    const int per = w.d->tiles_m * w.d->tiles_n;
+    w.c_lo = r / per;
+    w.c_hi = w.c_lo + 1;
+    r -= w.c_lo * per;
+  }
+  w.m0 = (r / w.d->tiles_n) * kBM;
+  w.n0 = (r % w.d->tiles_n) * BN;
+  return w;
+}
+
+// Persistent kernel.  CTA b handles units b, b + gridDim.x, ... of the
+// launch's unit list (all solves' tiles, solve-major, n-tile fastest within
+// a solve so that CTAs running together share A tiles in L2).  For each unit
+// the MMA warp accumulates into one of two TMEM slots of 2 x BN columns, so
+// the epilogue of one unit overlaps the MMAs of the next; pair units put u
+// and v of the same tile in one slot, which the fused stage-1 epilogue needs.
+// Epilogue warp w owns TMEM lane quarter w % 4 and half (w - 2) / 4 of the
+// columns; it prefetches its FP32 base values two 16-column chunks ahead,
+// starting before the accumulator is ready.
 template <int SW, int BN>
-__global__ void __launch_bounds__(kThreads, 1)
-    tc_mode_kernel(const __grid_constant__ TcMaps maps, TcEpilogue e) {
+__global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) {
   using C = TcCfg<SW, BN>;
   static_assert(4 * BN <= 512, "four accumulators must fit in TMEM");
   extern __shared__ uint8_t smem_raw[];
@@ -256,7 +287,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   int* abort_flag = (int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nk = (e.K + C::BK - 1) / C::BK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -283,24 +313,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    for (int c = 0; c < 2; ++c) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.a[c]) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.b[c]) : "memory");
-    }
     uint32_t g = 0;  // k-block counter of this CTA
     bool stop = false;
-    for (int u = blockIdx.x; u < e.nunits && !stop; u += gridDim.x) {
-      int c_lo, c_hi, r;
-      unit_comps(e, u, c_lo, c_hi, r);
-      const int m0 = (r / e.tiles_n) * kBM, n0 = (r % e.tiles_n) * BN;
-      for (int comp = c_lo; comp < c_hi && !stop; ++comp) {
-        const CUtensorMap* ma = &maps.a[comp];
-        const CUtensorMap* mb = &maps.b[comp];
+    for (int u = blockIdx.x; u < L.nunits && !stop; u += gridDim.x) {
+      const Unit w = decode_unit<BN>(L, u);
+      const int nk = (w.d->K + C::BK - 1) / C::BK;
+      for (int comp = w.c_lo; comp < w.c_hi && !stop; ++comp) {
+        const CUtensorMap* ma = &w.d->amap[comp];
+        const CUtensorMap* mb = &w.d->bmap[comp];
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = g % C::STAGES;
           const uint32_t it = g / C::STAGES;
           if (*abort_v || (it > 0 && !mbar_wait(&empty[s], (it - 1) & 1))) {
-            atomicCAS(e.err, 0, kErrTimeoutEmpty);
+            atomicCAS(L.err, 0, kErrTimeoutEmpty);
             *abort_v = 1;
             stop = true;
             break;
@@ -308,10 +333,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint8_t* st = smem + s * C::STAGE;
           mbar_arrive_expect_tx(&full[s], C::STAGE);
           for (int p = 0; p < kPieces; ++p)
-            tma_load_3d(st + p * C::TILE_A, ma, &full[s], kb * C::BK, m0, p);
+            tma_load_3d(st + p * C::TILE_A, ma, &full[s], kb * C::BK, w.m0, p);
           for (int p = 0; p < kPieces; ++p)
-            tma_load_3d(st + kPieces * C::TILE_A + p * C::TILE_B, mb, &full[s], kb * C::BK, n0,
-                        p);
+            tma_load_3d(st + kPieces * C::TILE_A + p * C::TILE_B, mb, &full[s], kb * C::BK,
+                        w.n0, p);
         }
       }
     }
@@ -324,23 +349,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t g = 0;
     int i = 0;  // local unit counter
     bool stop = false;
-    for (int u = blockIdx.x; u < e.nunits && !stop; u += gridDim.x, ++i) {
+    for (int u = blockIdx.x; u < L.nunits && !stop; u += gridDim.x, ++i) {
       const int slot = i & 1;
       const uint32_t use = i >> 1;
       if (use > 0 && !mbar_wait(&acc_empty[slot], (use - 1) & 1)) {
-        atomicCAS(e.err, 0, kErrTimeoutDone);
+        atomicCAS(L.err, 0, kErrTimeoutDone);
         *abort_v = 1;
         break;
       }
       tc_fence_after();
-      int c_lo, c_hi, r;
-      unit_comps(e, u, c_lo, c_hi, r);
-      for (int comp = c_lo; comp < c_hi && !stop; ++comp) {
-        const uint32_t d = tmem + (uint32_t)((slot * 2 + comp - c_lo) * BN);
+      const Unit w = decode_unit<BN>(L, u);
+      const int nk = (w.d->K + C::BK - 1) / C::BK;
+      for (int comp = w.c_lo; comp < w.c_hi && !stop; ++comp) {
+        const uint32_t dt = tmem + (uint32_t)((slot * 2 + comp - w.c_lo) * BN);
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = g % C::STAGES;
           if (!mbar_wait(&full[s], (g / C::STAGES) & 1)) {
-            atomicCAS(e.err, 0, kErrTimeoutFull);
+            atomicCAS(L.err, 0, kErrTimeoutFull);
             *abort_v = 1;
             stop = true;
             break;
@@ -354,14 +379,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int q = 0; q < 6; ++q) {
               const uint64_t ad = kmajor_desc<SW>(sa + kPairA[q] * C::TILE_A + kk * 32);
               const uint64_t bd = kmajor_desc<SW>(sb + kPairB[q] * C::TILE_B + kk * 32);
-              mma_bf16(d, ad, bd, idesc, (kb | kk | q) != 0);
+              mma_bf16(dt, ad, bd, idesc, (kb | kk | q) != 0);
             }
           }
           mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
         }
       }
       if (stop) break;
-      mma_commit(&acc_full[slot]);  // both accumulators of this slot complete
+      mma_commit(&acc_full[slot]);  // the accumulators of this slot are complete
     }
     // every MMA this thread issued has completed once `drain` fires
     mma_commit(drain);
@@ -372,37 +397,40 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int half = (warp - 2) >> 2;         // column half
     constexpr int HC = BN / 2;                // columns per epilogue warp
     constexpr int NCH = HC / 16;              // 16-column chunks
-    const bool fp32_in = e.mode != kPieces3;
     int i = 0;
-    for (int u = blockIdx.x; u < e.nunits; u += gridDim.x, ++i) {
+    for (int u = blockIdx.x; u < L.nunits; u += gridDim.x, ++i) {
       const int slot = i & 1;
-      int c_lo, c_hi, r;
-      unit_comps(e, u, c_lo, c_hi, r);
-      const int nc = c_hi - c_lo;
-      const int m0 = (r / e.tiles_n) * kBM, n0 = (r % e.tiles_n) * BN + half * HC;
-      const int m = m0 + q * 32 + lane;
-      const bool mrow = m < e.M;
-      const int64_t plane = (int64_t)e.N * e.M;
-      auto chunk_cols = [&](int ch) { return min(16, e.N - (n0 + ch * 16)); };
+      const Unit w = decode_unit<BN>(L, u);
+      const TcPassDesc* D = w.d;
+      const int M = D->M, N = D->N, mode = D->mode;
+      const float alpha = D->alpha;
+      const bool fp32_in = mode != kPieces3;
+      const int nc = w.c_hi - w.c_lo;
+      const int n0 = w.n0 + half * HC;
+      const int m = w.m0 + q * 32 + lane;
+      const bool mrow = m < M;
+      const int64_t plane = (int64_t)N * M;
+      const float* bsrc0 = D->base[w.c_lo];
+      const float* bsrc1 = nc == 2 ? D->base[w.c_lo + 1] : nullptr;
+      auto chunk_cols = [&](int ch) { return min(16, N - (n0 + ch * 16)); };
       // base prefetch, two chunks deep: pb[buffer][component slot][column]
       float pb[2][2][16];
       auto prefetch = [&](int ch, int buf) {
         const int jm = chunk_cols(ch);
-        const int64_t o0 = (int64_t)(n0 + ch * 16) * e.M + m;
+        const int64_t o0 = (int64_t)(n0 + ch * 16) * M + m;
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            pb[buf][c][j] = (mrow && c < nc && j < jm)
-                                ? __ldg(e.base[c_lo + c] + o0 + (int64_t)j * e.M)
-                                : 0.f;
+        for (int j = 0; j < 16; ++j) {
+          const bool ok = mrow && j < jm;
+          pb[buf][0][j] = ok ? __ldg(bsrc0 + o0 + (int64_t)j * M) : 0.f;
+          pb[buf][1][j] = (ok && bsrc1) ? __ldg(bsrc1 + o0 + (int64_t)j * M) : 0.f;
+        }
       };
       if (fp32_in) {
         prefetch(0, 0);
         if (NCH > 1) prefetch(1, 1);
       }
       if (!mbar_wait(&acc_full[slot], (i >> 1) & 1)) {
-        if (lane == 0) atomicCAS(e.err, 0, kErrTimeoutDone);
+        if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
         *abort_v = 1;
         break;
       }
@@ -415,40 +443,45 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld16(ta + (uint32_t)(ch * 16), acc[0]);
         if (nc == 2) tmem_ld16(ta + (uint32_t)(BN + ch * 16), acc[1]);
         const int jm = chunk_cols(ch);
-        const int64_t o0 = (int64_t)(n0 + ch * 16) * e.M + m;
+        const int64_t o0 = (int64_t)(n0 + ch * 16) * M + m;
         const int buf = ch & 1;
         if (mrow && jm > 0) {
-          if (e.mode == kStage1) {
+          if (mode == kStage1) {
+            __nv_bfloat16* op0 = D->outp[0];
+            __nv_bfloat16* op1 = D->outp[1];
+            float* of0 = D->outf[0];
+            float* of1 = D->outf[1];
+            const ReactionT<float> rx = D->rx;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               if (j >= jm) break;
-              const int64_t o = o0 + (int64_t)j * e.M;
+              const int64_t o = o0 + (int64_t)j * M;
               const float u0 = pb[buf][0][j], v0 = pb[buf][1][j];
-              const float u2 = u0 + e.alpha * acc[0][j];
-              const float v2 = v0 + e.alpha * acc[1][j];
-              e.outf[0][o] = u2;
-              e.outf[1][o] = v2;
+              const float u2 = u0 + alpha * acc[0][j];
+              const float v2 = v0 + alpha * acc[1][j];
+              of0[o] = u2;
+              of1[o] = v2;
               float g0u, g0v, g2u, g2v;
-              react<float>(e.rx, u0, v0, g0u, g0v);
-              react<float>(e.rx, u2, v2, g2u, g2v);
+              react<float>(rx, u0, v0, g0u, g0v);
+              react<float>(rx, u2, v2, g2u, g2v);
               __nv_bfloat16 b0, b1, b2;
               split3(g2u - g0u, b0, b1, b2);
-              e.outp[0][o] = b0;
-              e.outp[0][plane + o] = b1;
-              e.outp[0][2 * plane + o] = b2;
+              op0[o] = b0;
+              op0[plane + o] = b1;
+              op0[2 * plane + o] = b2;
               split3(g2v - g0v, b0, b1, b2);
-              e.outp[1][o] = b0;
-              e.outp[1][plane + o] = b1;
-              e.outp[1][2 * plane + o] = b2;
+              op1[o] = b0;
+              op1[plane + o] = b1;
+              op1[2 * plane + o] = b2;
             }
           } else {
             auto emit = [&](int c, const float(&a)[16], const float(&bsv)[16]) {
-              if (e.mode == kPieces3) {
-                __nv_bfloat16* op = e.outp[c_lo + c];
+              if (mode == kPieces3) {
+                __nv_bfloat16* op = D->outp[w.c_lo + c];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                   if (j >= jm) break;
-                  const int64_t o = o0 + (int64_t)j * e.M;
+                  const int64_t o = o0 + (int64_t)j * M;
                   __nv_bfloat16 b0, b1, b2;
                   split3(a[j], b0, b1, b2);
                   op[o] = b0;
@@ -456,11 +489,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                   op[2 * plane + o] = b2;
                 }
               } else {
-                float* of = e.outf[c_lo + c];
+                float* of = D->outf[w.c_lo + c];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                   if (j >= jm) break;
-                  of[o0 + (int64_t)j * e.M] = bsv[j] + e.alpha * a[j];
+                  of[o0 + (int64_t)j * M] = bsv[j] + alpha * a[j];
                 }
               }
             };
@@ -485,10 +518,28 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// W^c = K^c U^c + G^c(U, V) as BF16 pieces [3][N] in the natural layout.
-// One thread per (i1, i2) marches kZ consecutive x3 planes and keeps the x3
-// neighbours in registers (2D grids have a single plane).
-constexpr int kZ = 8;
+// ---------------------------------------------------------------- pointwise
+// Per-solve arguments of the pointwise kernels of the tensor-core path; one
+// launch covers one solve or a whole batch.
+struct PwDesc {
+  PointwiseArgsT<float> a;
+  const float* u;
+  const float* v;
+  const float* u2;
+  const float* v2;
+  __nv_bfloat16* wu;   // pieces [3][N] of the u output
+  __nv_bfloat16* wv;
+  int gx, gy;          // stencil blocks of this solve: gx * gy * gz
+};
+
+struct PwLaunch {
+  const PwDesc* desc;
+  const int* bstart;   // [nsolves + 1] prefix sums of this kernel's blocks
+  int nsolves;
+};
+
+constexpr int kZ = 8;             // x3 planes per stencil thread
+constexpr int kRdiffPerBlock = 1024;
 
 __device__ __forceinline__ float zdir(float xm, float xc, float xp, int z, int n3,
                                       const TridiagT<float>& A) {
@@ -497,16 +548,25 @@ __device__ __forceinline__ float zdir(float xm, float xc, float xp, int z, int n
   return A.lo * (xm - xc) + A.up * (xp - xc);
 }
 
-__global__ void __launch_bounds__(128) rhs_pieces_kernel(PointwiseArgsT<float> a,
-                                                         const float* __restrict__ u,
-                                                         const float* __restrict__ v,
-                                                         __nv_bfloat16* __restrict__ wu,
-                                                         __nv_bfloat16* __restrict__ wv) {
+// W^c = K^c U^c + G^c(U, V) as BF16 pieces [3][N] in the natural layout.
+// One thread per (i1, i2) marches kZ consecutive x3 planes and keeps the x3
+// neighbours in registers (2D grids have a single plane).
+__global__ void __launch_bounds__(128) rhs_pieces_kernel(const PwLaunch L) {
+  const int s = find_segment(L.bstart, L.nsolves, blockIdx.x);
+  const PwDesc& D = L.desc[s];
+  const PointwiseArgsT<float>& a = D.a;
+  int lb = blockIdx.x - __ldg(L.bstart + s);
+  const int bx = lb % D.gx;
+  lb /= D.gx;
+  const int i2 = lb % D.gy;
+  const int z0 = (lb / D.gy) * kZ;
   const int n1 = (int)a.n[0], n2 = (int)a.n[1], n3 = a.d == 3 ? (int)a.n[2] : 1;
-  const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = bx * blockDim.x + threadIdx.x;
   if (i1 >= n1) return;
-  const int i2 = blockIdx.y;
-  const int z0 = blockIdx.z * kZ;
+  const float* __restrict__ u = D.u;
+  const float* __restrict__ v = D.v;
+  __nv_bfloat16* __restrict__ wu = D.wu;
+  __nv_bfloat16* __restrict__ wv = D.wv;
   const int64_t P = (int64_t)n1 * n2;
   const int64_t col = (int64_t)i2 * n1 + i1;
   float uc = u[z0 * P + col], vc = v[z0 * P + col];
@@ -539,19 +599,20 @@ __global__ void __launch_bounds__(128) rhs_pieces_kernel(PointwiseArgsT<float> a
 }
 
 // D^c = G^c(U2, V2) - G^c(U, V) written as BF16 pieces [3][N].
-__global__ void __launch_bounds__(256) rdiff_pieces_kernel(PointwiseArgsT<float> a, const float* __restrict__ u,
-                                                           const float* __restrict__ v,
-                                                           const float* __restrict__ u2,
-                                                           const float* __restrict__ v2,
-                                                           __nv_bfloat16* __restrict__ du,
-                                                           __nv_bfloat16* __restrict__ dv) {
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.N;
-       idx += (int64_t)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) rdiff_pieces_kernel(const PwLaunch L) {
+  const int s = find_segment(L.bstart, L.nsolves, blockIdx.x);
+  const PwDesc& D = L.desc[s];
+  const int64_t N = D.a.N;
+  const int64_t base = (int64_t)(blockIdx.x - __ldg(L.bstart + s)) * kRdiffPerBlock;
+#pragma unroll
+  for (int k = 0; k < kRdiffPerBlock / 256; ++k) {
+    const int64_t idx = base + k * 256 + threadIdx.x;
+    if (idx >= N) break;
     float g0u, g0v, g2u, g2v;
-    react<float>(a.rx, u[idx], v[idx], g0u, g0v);
-    react<float>(a.rx, u2[idx], v2[idx], g2u, g2v);
-    split3(g2u - g0u, du[idx], du[a.N + idx], du[2 * a.N + idx]);
-    split3(g2v - g0v, dv[idx], dv[a.N + idx], dv[2 * a.N + idx]);
+    react<float>(D.a.rx, D.u[idx], D.v[idx], g0u, g0v);
+    react<float>(D.a.rx, D.u2[idx], D.v2[idx], g2u, g2v);
+    split3(g2u - g0u, D.wu[idx], D.wu[N + idx], D.wu[2 * N + idx]);
+    split3(g2v - g0v, D.wv[idx], D.wv[N + idx], D.wv[2 * N + idx]);
   }
 }
 
@@ -612,17 +673,18 @@ cudaError_t set_smem_attr() {
                               TcCfg<SW, BN>::SMEM);
 }
 
-cudaError_t launch_variant(int v, dim3 grid, cudaStream_t s, const TcMaps& maps,
-                           const TcEpilogue& ep) {
+cudaError_t launch_tc(int v, int num_sms, cudaStream_t s, const TcLaunch& L) {
+  if (L.nunits <= 0) return cudaSuccess;
+  dim3 grid((unsigned)(L.nunits < num_sms ? L.nunits : num_sms));
   switch (v) {
     case 0:
-      tc_mode_kernel<64, 128><<<grid, kThreads, TcCfg<64, 128>::SMEM, s>>>(maps, ep);
+      tc_mode_kernel<64, 128><<<grid, kThreads, TcCfg<64, 128>::SMEM, s>>>(L);
       break;
     case 1:
-      tc_mode_kernel<128, 128><<<grid, kThreads, TcCfg<128, 128>::SMEM, s>>>(maps, ep);
+      tc_mode_kernel<128, 128><<<grid, kThreads, TcCfg<128, 128>::SMEM, s>>>(L);
       break;
     case 2:
-      tc_mode_kernel<64, 64><<<grid, kThreads, TcCfg<64, 64>::SMEM, s>>>(maps, ep);
+      tc_mode_kernel<64, 64><<<grid, kThreads, TcCfg<64, 64>::SMEM, s>>>(L);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -637,9 +699,18 @@ int grid_for(int64_t total) {
   return (int)b;
 }
 
+// One tensor-core pass of the step sequence.
+struct TcPass {
+  int b;      // piece buffer read (output pieces go to 1 - b)
+  int mu;     // direction
+  int ell;    // 1: phi_1 (stage 1), 2: phi_2 (stage 2)
+  int mode;   // TcMode
+  int pair;
+};
+
 }  // namespace
 
-// Host-side state of the tensor-core path (owned through TcOperands).
+// Host-side state of the tensor-core path of one plan (owned through TcOperands).
 struct TcState {
   int d;
   int64_t n[3];
@@ -653,7 +724,89 @@ struct TcState {
   int num_sms;
   int* err;
   std::vector<void*> allocs;
+  // step sequence: 2d tensor-core passes, the reaction difference after
+  // pass `rdiff_after` (-1 when fused)
+  std::vector<TcPass> passes;
+  int rdiff_after;
+  // descriptors of this plan as a group of one, bound to (bound_u, bound_v)
+  TcPassDesc* d_desc;
+  int* d_ustart;   // [passes][2]
+  PwDesc* d_pw;
+  int* d_bstart;   // rhs {0, blocks}, rdiff {0, blocks}
+  int units[8];
+  int rhs_blocks, rdiff_blocks;
+  void* bound_u;
+  void* bound_v;
 };
+
+static int units_of(const TcState* S, const TcPass& ps, int bn) {
+  const int64_t nmu = S->n[ps.mu];
+  const int64_t M = S->N / nmu;
+  const int tm = (int)((M + kBM - 1) / kBM), tn = (int)((nmu + bn - 1) / bn);
+  return (ps.pair ? 1 : 2) * tm * tn;
+}
+
+static TcPassDesc make_desc(const TcState* S, const adr_plan_s* P, const TcPass& ps, float* u,
+                            float* v) {
+  TcPassDesc D;
+  memset(&D, 0, sizeof(D));
+  const int bn = kVariants[S->variant].bn;
+  const int64_t nmu = S->n[ps.mu];
+  D.M = (int)(S->N / nmu);
+  D.N = (int)nmu;
+  D.K = (int)nmu;
+  D.tiles_m = (D.M + kBM - 1) / kBM;
+  D.tiles_n = (D.N + bn - 1) / bn;
+  D.pair = ps.pair;
+  D.mode = ps.mode;
+  D.rx = P->pwf.rx;
+  float* U2 = (float*)P->u2;
+  float* V2 = (float*)P->v2;
+  const double tau = P->prob.tau;
+  for (int c = 0; c < 2; ++c) {
+    D.amap[c] = S->amap[ps.b][c][ps.mu];
+    D.bmap[c] = S->bmap[c][ps.mu][ps.ell - 1];
+    D.outp[c] = S->buf[1 - ps.b][c];
+  }
+  if (ps.mode != kPieces3) {
+    if (ps.ell == 1) {  // U2 = U + tau T
+      D.outf[0] = U2;
+      D.outf[1] = V2;
+      D.base[0] = u;
+      D.base[1] = v;
+      D.alpha = (float)tau;
+    } else {  // U+ = U2 + 2^(d-1) tau S
+      D.outf[0] = u;
+      D.outf[1] = v;
+      D.base[0] = U2;
+      D.base[1] = V2;
+      D.alpha = (float)ldexp(tau, S->d - 1);
+    }
+  }
+  return D;
+}
+
+static PwDesc make_pw(const TcState* S, const adr_plan_s* P, float* u, float* v) {
+  PwDesc W;
+  memset(&W, 0, sizeof(W));
+  W.a = P->pwf;
+  W.u = u;
+  W.v = v;
+  W.u2 = (const float*)P->u2;
+  W.v2 = (const float*)P->v2;
+  W.wu = S->buf[0][0];
+  W.wv = S->buf[0][1];
+  W.gx = (int)((S->n[0] + 127) / 128);
+  W.gy = (int)S->n[1];
+  return W;
+}
+
+static int rhs_blocks_of(const TcState* S) {
+  return (int)(((S->n[0] + 127) / 128) * S->n[1] * ((S->n[2] + kZ - 1) / kZ));
+}
+static int rdiff_blocks_of(const TcState* S) {
+  return (int)((S->N + kRdiffPerBlock - 1) / kRdiffPerBlock);
+}
 
 void tc_init(TcOperands* t) { memset(t, 0, sizeof(*t)); }
 
@@ -731,106 +884,153 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int d, const int64_t n[3],
         if (e != cudaSuccess) return e;
       }
     }
+  // step sequence (buffers alternate; the reaction difference writes buffer 0)
+  {
+    int b = 0;
+    S->rdiff_after = -1;
+    for (int mu = 0; mu < d; ++mu) {
+      if (mu < d - 1) {
+        S->passes.push_back({b, mu, 1, kPieces3, 0});
+        b ^= 1;
+      } else if (S->fuse) {
+        S->passes.push_back({b, mu, 1, kStage1, 1});
+        b ^= 1;
+      } else {
+        S->passes.push_back({b, mu, 1, kAxpy, 0});
+        S->rdiff_after = (int)S->passes.size() - 1;
+        b = 0;
+      }
+    }
+    for (int mu = 0; mu < d; ++mu) {
+      S->passes.push_back({b, mu, 2, mu < d - 1 ? kPieces3 : kAxpy, 0});
+      b ^= 1;
+    }
+  }
+  const int np = (int)S->passes.size();
+  for (int p = 0; p < np; ++p) S->units[p] = units_of(S, S->passes[p], bn);
+  S->rhs_blocks = rhs_blocks_of(S);
+  S->rdiff_blocks = rdiff_blocks_of(S);
+  e = alloc((void**)&S->d_desc, sizeof(TcPassDesc) * np);
+  if (e != cudaSuccess) return e;
+  e = alloc((void**)&S->d_ustart, sizeof(int) * 2 * np);
+  if (e != cudaSuccess) return e;
+  e = alloc((void**)&S->d_pw, sizeof(PwDesc));
+  if (e != cudaSuccess) return e;
+  e = alloc((void**)&S->d_bstart, sizeof(int) * 4);
+  if (e != cudaSuccess) return e;
+  std::vector<int> us(2 * np);
+  for (int p = 0; p < np; ++p) {
+    us[2 * p] = 0;
+    us[2 * p + 1] = S->units[p];
+  }
+  e = cudaMemcpyAsync(S->d_ustart, us.data(), sizeof(int) * 2 * np, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const int bs[4] = {0, S->rhs_blocks, 0, S->rdiff_blocks};
+  e = cudaMemcpyAsync(S->d_bstart, bs, sizeof(bs), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);  // the host arrays above go out of scope
+  if (e != cudaSuccess) return e;
+  S->bound_u = S->bound_v = nullptr;
   t->ready = 1;
   return cudaSuccess;
 }
 
-// One mu-mode product for both components: buffer b viewed along direction
-// mu times phi_ell; the epilogue writes pieces to buffer 1 - b, the FP32
-// AXPY, or the fused stage-1 combination.
-static cudaError_t tc_mode(adr_plan_s* P, TcState* S, int b, int mu, int ell, int mode, int pair,
-                           float* const outf[2], const float* const base[2], double alpha) {
-  TcMaps maps;
-  TcEpilogue ep{};
-  const int64_t nmu = S->n[mu];
-  ep.M = (int)(S->N / nmu);
-  ep.N = (int)nmu;
-  ep.K = (int)nmu;
-  ep.err = S->err;
-  ep.mode = mode;
-  ep.pair = pair;
-  ep.alpha = (float)alpha;
-  ep.rx = P->pwf.rx;
-  for (int c = 0; c < 2; ++c) {
-    maps.a[c] = S->amap[b][c][mu];
-    maps.b[c] = S->bmap[c][mu][ell - 1];
-    ep.outp[c] = S->buf[1 - b][c];
-    ep.outf[c] = outf ? outf[c] : nullptr;
-    ep.base[c] = base ? base[c] : nullptr;
-  }
-  const int bn = kVariants[S->variant].bn;
-  ep.tiles_m = (ep.M + kBM - 1) / kBM;
-  ep.tiles_n = (ep.N + bn - 1) / bn;
-  ep.nunits = (pair ? 1 : 2) * ep.tiles_m * ep.tiles_n;
-  dim3 grid((unsigned)(ep.nunits < S->num_sms ? ep.nunits : S->num_sms));
-  const double flops = 2.0 * 2.0 * (double)nmu * (double)S->N;
-  // algorithmic bytes: A pieces in, Phi pieces, outputs (+ FP32 base)
-  double bytes = 2.0 * (6.0 * S->N + 6.0 * nmu * nmu);
-  if (mode == kPieces3) bytes += 2.0 * 6.0 * S->N;
-  if (mode == kAxpy) bytes += 2.0 * 8.0 * S->N;
-  if (mode == kStage1) bytes += 2.0 * (8.0 + 6.0) * S->N;
-  return timed_kernel(P, KC_MODE_TC, flops, bytes,
-                      [&] { return launch_variant(S->variant, grid, P->stream, maps, ep); });
-}
-
-cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
+// Point this plan's descriptors at the state buffers (u, v).  Called before
+// stepping (outside any stream capture); a no-op when already bound.
+cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   TcState* S = (TcState*)t->work[0];
   if (!S || !t->ready) return cudaErrorNotSupported;
-  const float* U = (const float*)u;
-  const float* V = (const float*)v;
-  float* U2 = (float*)P->u2;
-  float* V2 = (float*)P->v2;
-  const PointwiseArgsT<float>& pw = P->pwf;
-  const double tau = P->prob.tau;
-  const double N = (double)S->N;
-  const int d = S->d;
-  cudaError_t e = timed_kernel(P, KC_RHS, N * 2.0 * (6.0 * d + 10.0), N * (8.0 + 12.0), [&] {
-    dim3 g((unsigned)((S->n[0] + 127) / 128), (unsigned)S->n[1],
-           (unsigned)((S->n[2] + kZ - 1) / kZ));
-    rhs_pieces_kernel<<<g, 128, 0, P->stream>>>(pw, U, V, S->buf[0][0], S->buf[0][1]);
+  if (S->bound_u == u && S->bound_v == v) return cudaSuccess;
+  const int np = (int)S->passes.size();
+  std::vector<TcPassDesc> hd(np);
+  for (int p = 0; p < np; ++p) hd[p] = make_desc(S, P, S->passes[p], (float*)u, (float*)v);
+  const PwDesc pw = make_pw(S, P, (float*)u, (float*)v);
+  cudaError_t e = cudaMemcpyAsync(S->d_desc, hd.data(), sizeof(TcPassDesc) * np,
+                                  cudaMemcpyHostToDevice, P->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(S->d_pw, &pw, sizeof(pw), cudaMemcpyHostToDevice, P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) return e;
+  S->bound_u = u;
+  S->bound_v = v;
+  return cudaSuccess;
+}
+
+// Launch the kernels of one ETD2RKds step for a group of solves.
+struct GroupStep {
+  int d, variant, num_sms, nsolves;
+  int np, rdiff_after;
+  const TcPassDesc* desc;   // [np][nsolves]
+  const int* ustart;        // [np][nsolves + 1]
+  int units[8];
+  PwLaunch rhs, rdiff;
+  int rhs_blocks, rdiff_blocks;
+  int* err;
+  double flops[8], bytes[8];  // algorithmic work per pass (timing statistics)
+  double pw_n;                // total points (pointwise statistics)
+};
+
+static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
+  const double N = G.pw_n;
+  cudaError_t e = timed_kernel(ctl, KC_RHS, N * 2.0 * (6.0 * G.d + 10.0), N * (8.0 + 12.0), [&] {
+    rhs_pieces_kernel<<<G.rhs_blocks, 128, 0, ctl->stream>>>(G.rhs);
     return cudaGetLastError();
   });
   if (e != cudaSuccess) return e;
-  // stage 1: U2 = U + tau W x_mu phi_1, then D = G(U2, V2) - G(U, V)
-  float* o2[2] = {U2, V2};
-  const float* b1[2] = {U, V};
-  int b = 0;
-  for (int mu = 0; mu < d - 1; ++mu, b ^= 1) {
-    e = tc_mode(P, S, b, mu, 1, kPieces3, 0, nullptr, nullptr, 1.0);
+  for (int p = 0; p < G.np; ++p) {
+    TcLaunch L;
+    L.desc = G.desc + (size_t)p * G.nsolves;
+    L.ustart = G.ustart + (size_t)p * (G.nsolves + 1);
+    L.nsolves = G.nsolves;
+    L.nunits = G.units[p];
+    L.err = G.err;
+    e = timed_kernel(ctl, KC_MODE_TC, G.flops[p], G.bytes[p],
+                     [&] { return launch_tc(G.variant, G.num_sms, ctl->stream, L); });
     if (e != cudaSuccess) return e;
-  }
-  {
-    // fuse the reaction difference into the last product when there are
-    // enough (u, v) tile pairs to fill the GPU, else a separate kernel
-    const int64_t nlast = S->n[d - 1];
-    const int bn = kVariants[S->variant].bn;
-    const int64_t pairs = ((S->N / nlast + kBM - 1) / kBM) * ((nlast + bn - 1) / bn);
-    if (S->fuse == 1 && pairs > 0) {
-      e = tc_mode(P, S, b, d - 1, 1, kStage1, 1, o2, b1, tau);
-      if (e != cudaSuccess) return e;
-      b ^= 1;
-    } else {
-      e = tc_mode(P, S, b, d - 1, 1, kAxpy, 0, o2, b1, tau);
-      if (e != cudaSuccess) return e;
-      b = 0;
-      e = timed_kernel(P, KC_RDIFF, N * 2.0 * 12.0, N * (16.0 + 12.0), [&] {
-        rdiff_pieces_kernel<<<grid_for(S->N), 256, 0, P->stream>>>(pw, U, V, U2, V2, S->buf[0][0],
-                                                                   S->buf[0][1]);
+    if (p == G.rdiff_after) {
+      e = timed_kernel(ctl, KC_RDIFF, N * 2.0 * 12.0, N * (16.0 + 12.0), [&] {
+        rdiff_pieces_kernel<<<G.rdiff_blocks, 256, 0, ctl->stream>>>(G.rdiff);
         return cudaGetLastError();
       });
       if (e != cudaSuccess) return e;
     }
   }
-  // stage 2: U+ = U2 + 2^(d-1) tau D x_mu phi_2
-  float* o1[2] = {(float*)u, (float*)v};
-  const float* b2[2] = {U2, V2};
-  for (int mu = 0; mu < d; ++mu, b ^= 1) {
-    const bool last = mu == d - 1;
-    e = tc_mode(P, S, b, mu, 2, last ? kAxpy : kPieces3, 0, last ? o1 : nullptr,
-                last ? b2 : nullptr, ldexp(tau, d - 1));
-    if (e != cudaSuccess) return e;
-  }
   return cudaSuccess;
+}
+
+static void pass_work(const TcState* S, const TcPass& ps, double& flops, double& bytes) {
+  const double N = (double)S->N, nmu = (double)S->n[ps.mu];
+  flops = 2.0 * 2.0 * nmu * N;
+  bytes = 2.0 * (6.0 * N + 6.0 * nmu * nmu);
+  if (ps.mode == kPieces3) bytes += 2.0 * 6.0 * N;
+  if (ps.mode == kAxpy) bytes += 2.0 * 8.0 * N;
+  if (ps.mode == kStage1) bytes += 2.0 * (8.0 + 6.0) * N;
+}
+
+cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
+  TcState* S = (TcState*)t->work[0];
+  if (!S || !t->ready || S->bound_u != u || S->bound_v != v) return cudaErrorNotSupported;
+  GroupStep G;
+  memset(&G, 0, sizeof(G));
+  G.d = S->d;
+  G.variant = S->variant;
+  G.num_sms = S->num_sms;
+  G.nsolves = 1;
+  G.np = (int)S->passes.size();
+  G.rdiff_after = S->rdiff_after;
+  G.desc = S->d_desc;
+  G.ustart = S->d_ustart;
+  for (int p = 0; p < G.np; ++p) {
+    G.units[p] = S->units[p];
+    pass_work(S, S->passes[p], G.flops[p], G.bytes[p]);
+  }
+  G.rhs = PwLaunch{S->d_pw, S->d_bstart, 1};
+  G.rdiff = PwLaunch{S->d_pw, S->d_bstart + 2, 1};
+  G.rhs_blocks = S->rhs_blocks;
+  G.rdiff_blocks = S->rdiff_blocks;
+  G.err = S->err;
+  G.pw_n = (double)S->N;
+  return group_step(P, G);
 }
 
 int* tc_error_word(TcOperands* t) {
@@ -838,4 +1038,307 @@ int* tc_error_word(TcOperands* t) {
   return S ? S->err : nullptr;
 }
 
+
 }  // namespace adr
+
+// ================================================================ batches
+// Many independent solves advanced together.  When every plan is a BF16x3
+// plan with the same dimension and kernel variant, one step of the whole
+// batch is one grouped launch per kernel: the stencil kernel and the
+// reaction-difference kernel cover every solve's blocks, and each
+// tensor-core pass covers every solve's tiles in one persistent launch
+// (per-solve descriptors and tensor maps in device memory).  Other batches
+// step their plans one after another with each plan's own kernels.
+using namespace adr;
+
+struct adr_batch_s {
+  std::vector<adr_plan> plans;
+  adr_plan_s* ctl;   // stream, launch counters and timing events of the batch
+  int grouped;
+  // grouped descriptors
+  int np, rdiff_after, variant, num_sms, d, nsolves;
+  TcPassDesc* d_desc;   // [np][nsolves]
+  int* d_ustart;        // [np][nsolves + 1]
+  PwDesc* d_pw;         // [nsolves]
+  int* d_bstart;        // rhs [nsolves + 1], then rdiff [nsolves + 1]
+  int* d_err;
+  int units[8];
+  int rhs_blocks, rdiff_blocks;
+  double flops[8], bytes[8], pw_n;
+  std::vector<void*> bound_u, bound_v;
+  // CUDA graph of kBatchChunk steps
+  cudaStream_t cap;
+  cudaGraphExec_t gexec;
+  int64_t g_launches;
+  std::vector<void*> allocs;
+};
+
+static constexpr int64_t kBatchChunk = 16;
+
+static void batch_free(adr_batch B) {
+  if (!B) return;
+  if (B->ctl) {
+    cudaStreamSynchronize(B->ctl->stream);
+    for (cudaEvent_t e : B->ctl->event_pool) cudaEventDestroy(e);
+    delete B->ctl;
+  }
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  for (void* q : B->allocs) cudaFree(q);
+  delete B;
+}
+
+extern "C" adr_status adr_batch_create(const adr_plan* plans, int count, void* stream,
+                                       adr_batch* out) {
+  if (!plans || count < 1 || !out) {
+    set_error("adr_batch_create: need count >= 1 plans and an output pointer");
+    return ADR_EINVAL;
+  }
+  for (int i = 0; i < count; ++i)
+    if (!plans[i]) {
+      set_error("adr_batch_create: NULL plan");
+      return ADR_EINVAL;
+    }
+  adr_batch B = new adr_batch_s();
+  B->plans.assign(plans, plans + count);
+  B->ctl = new adr_plan_s();
+  B->ctl->stream = (cudaStream_t)stream;
+  B->ctl->prec = plans[0]->prec;
+  B->ctl->use_graphs = 1;
+  if (const char* ev = getenv("ADR_GRAPHS")) B->ctl->use_graphs = atoi(ev) != 0;
+  B->nsolves = count;
+  // grouped only if every plan runs the same tensor-core step sequence
+  bool grouped = true;
+  const TcState* S0 = (const TcState*)plans[0]->tc.work[0];
+  for (int i = 0; i < count && grouped; ++i) {
+    const TcState* S = (const TcState*)plans[i]->tc.work[0];
+    grouped = plans[i]->prec == ADR_BF16X3 && S && S0 && S->d == S0->d &&
+              S->variant == S0->variant && S->passes.size() == S0->passes.size() &&
+              S->rdiff_after == S0->rdiff_after;
+    for (size_t p = 0; grouped && p < S->passes.size(); ++p)
+      grouped = S->passes[p].mode == S0->passes[p].mode && S->passes[p].pair == S0->passes[p].pair;
+  }
+  B->grouped = grouped ? 1 : 0;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** q, size_t bytes) -> cudaError_t {
+    cudaError_t r = cudaMalloc(q, bytes < 16 ? 16 : bytes);
+    if (r == cudaSuccess) B->allocs.push_back(*q);
+    return r;
+  };
+  if (B->grouped) {
+    const int S_ = count;
+    B->np = (int)S0->passes.size();
+    B->rdiff_after = S0->rdiff_after;
+    B->variant = S0->variant;
+    B->num_sms = S0->num_sms;
+    B->d = S0->d;
+    const int bn = kVariants[B->variant].bn;
+    std::vector<int> us((size_t)B->np * (S_ + 1)), bs(2 * (size_t)(S_ + 1));
+    B->pw_n = 0;
+    for (int p = 0; p < B->np; ++p) {
+      int acc = 0;
+      B->flops[p] = B->bytes[p] = 0;
+      for (int i = 0; i < S_; ++i) {
+        const TcState* S = (const TcState*)plans[i]->tc.work[0];
+        us[(size_t)p * (S_ + 1) + i] = acc;
+        acc += units_of(S, S->passes[p], bn);
+        double f, b;
+        pass_work(S, S->passes[p], f, b);
+        B->flops[p] += f;
+        B->bytes[p] += b;
+      }
+      us[(size_t)p * (S_ + 1) + S_] = acc;
+      B->units[p] = acc;
+    }
+    int ra = 0, rd = 0;
+    for (int i = 0; i < S_; ++i) {
+      const TcState* S = (const TcState*)plans[i]->tc.work[0];
+      bs[i] = ra;
+      bs[(S_ + 1) + i] = rd;
+      ra += rhs_blocks_of(S);
+      rd += rdiff_blocks_of(S);
+      B->pw_n += (double)S->N;
+    }
+    bs[S_] = ra;
+    bs[(S_ + 1) + S_] = rd;
+    B->rhs_blocks = ra;
+    B->rdiff_blocks = rd;
+    if ((e = alloc((void**)&B->d_desc, sizeof(TcPassDesc) * B->np * S_)) == cudaSuccess &&
+        (e = alloc((void**)&B->d_ustart, sizeof(int) * us.size())) == cudaSuccess &&
+        (e = alloc((void**)&B->d_pw, sizeof(PwDesc) * S_)) == cudaSuccess &&
+        (e = alloc((void**)&B->d_bstart, sizeof(int) * bs.size())) == cudaSuccess &&
+        (e = alloc((void**)&B->d_err, sizeof(int))) == cudaSuccess)
+      e = cudaMemcpy(B->d_ustart, us.data(), sizeof(int) * us.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(B->d_bstart, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(B->d_err, 0, sizeof(int));
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    set_error(std::string("adr_batch_create: ") + cudaGetErrorString(e));
+    batch_free(B);
+    return e == cudaErrorMemoryAllocation ? ADR_ENOMEM : ADR_ECUDA;
+  }
+  *out = B;
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_batch_destroy(adr_batch batch) {
+  batch_free(batch);
+  return ADR_OK;
+}
+
+static cudaError_t batch_bind(adr_batch B, void* const* u, void* const* v) {
+  bool same = B->bound_u.size() == (size_t)B->nsolves;
+  for (int i = 0; same && i < B->nsolves; ++i) same = B->bound_u[i] == u[i] && B->bound_v[i] == v[i];
+  if (same) return cudaSuccess;
+  const int S_ = B->nsolves;
+  std::vector<TcPassDesc> hd((size_t)B->np * S_);
+  std::vector<PwDesc> hp(S_);
+  for (int i = 0; i < S_; ++i) {
+    adr_plan_s* P = B->plans[i];
+    const TcState* S = (const TcState*)P->tc.work[0];
+    for (int p = 0; p < B->np; ++p)
+      hd[(size_t)p * S_ + i] = make_desc(S, P, S->passes[p], (float*)u[i], (float*)v[i]);
+    hp[i] = make_pw(S, P, (float*)u[i], (float*)v[i]);
+  }
+  cudaError_t e = cudaMemcpyAsync(B->d_desc, hd.data(), sizeof(TcPassDesc) * hd.size(),
+                                  cudaMemcpyHostToDevice, B->ctl->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_pw, hp.data(), sizeof(PwDesc) * hp.size(), cudaMemcpyHostToDevice,
+                        B->ctl->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B->ctl->stream);
+  if (e != cudaSuccess) return e;
+  B->bound_u.assign(u, u + S_);
+  B->bound_v.assign(v, v + S_);
+  if (B->gexec) {  // the graph's descriptors now describe new buffers; recapture
+    cudaGraphExecDestroy(B->gexec);
+    B->gexec = nullptr;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t batch_step_direct(adr_batch B, int64_t nsteps) {
+  GroupStep G;
+  memset(&G, 0, sizeof(G));
+  G.d = B->d;
+  G.variant = B->variant;
+  G.num_sms = B->num_sms;
+  G.nsolves = B->nsolves;
+  G.np = B->np;
+  G.rdiff_after = B->rdiff_after;
+  G.desc = B->d_desc;
+  G.ustart = B->d_ustart;
+  for (int p = 0; p < B->np; ++p) {
+    G.units[p] = B->units[p];
+    G.flops[p] = B->flops[p];
+    G.bytes[p] = B->bytes[p];
+  }
+  G.rhs = PwLaunch{B->d_pw, B->d_bstart, B->nsolves};
+  G.rdiff = PwLaunch{B->d_pw, B->d_bstart + (B->nsolves + 1), B->nsolves};
+  G.rhs_blocks = B->rhs_blocks;
+  G.rdiff_blocks = B->rdiff_blocks;
+  G.err = B->d_err;
+  G.pw_n = B->pw_n;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    cudaError_t e = group_step(B->ctl, G);
+    if (e != cudaSuccess) return e;
+    B->ctl->steps++;
+  }
+  return cudaSuccess;
+}
+
+extern "C" adr_status adr_batch_step(adr_batch batch, void* const* u, void* const* v,
+                                     int64_t nsteps) {
+  if (!batch || !u || !v || nsteps < 0) {
+    set_error("adr_batch_step: bad argument");
+    return ADR_EINVAL;
+  }
+  adr_batch B = batch;
+  for (int i = 0; i < B->nsolves; ++i) {
+    if (!u[i] || !v[i] || u[i] == v[i]) {
+      set_error("adr_batch_step: state pointers must be distinct and non-NULL");
+      return ADR_EINVAL;
+    }
+  }
+  if (!B->grouped) {
+    for (int i = 0; i < B->nsolves; ++i) {
+      adr_status st = adr_step(B->plans[i], u[i], v[i], nsteps);
+      if (st != ADR_OK) return st;
+    }
+    return ADR_OK;
+  }
+  if (nsteps == 0) return ADR_OK;
+  cudaError_t e = batch_bind(B, u, v);
+  if (e != cudaSuccess) {
+    set_error(std::string("adr_batch_step: binding: ") + cudaGetErrorString(e));
+    return ADR_ECUDA;
+  }
+  adr_plan_s* ctl = B->ctl;
+  int64_t done = 0;
+  if (ctl->use_graphs && !ctl->timing && nsteps >= kBatchChunk) {
+    if (!B->gexec) {
+      const int64_t l0 = ctl->launches, s0 = ctl->steps;
+      cudaStream_t saved = ctl->stream;
+      ctl->stream = B->cap;
+      cudaGraph_t g = nullptr;
+      cudaError_t ce = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal);
+      if (ce == cudaSuccess) {
+        cudaError_t e1 = batch_step_direct(B, kBatchChunk);
+        cudaError_t e2 = cudaStreamEndCapture(B->cap, &g);
+        ce = e1 != cudaSuccess ? e1 : e2;
+      }
+      ctl->stream = saved;
+      B->g_launches = ctl->launches - l0;
+      ctl->launches = l0;
+      ctl->steps = s0;
+      if (ce == cudaSuccess && g) ce = cudaGraphInstantiate(&B->gexec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (ce != cudaSuccess) {
+        cudaGetLastError();
+        B->gexec = nullptr;
+        ctl->use_graphs = 0;
+      }
+    }
+    if (B->gexec) {
+      for (; done + kBatchChunk <= nsteps; done += kBatchChunk) {
+        e = cudaGraphLaunch(B->gexec, ctl->stream);
+        if (e != cudaSuccess) {
+          set_error(std::string("adr_batch_step: cudaGraphLaunch: ") + cudaGetErrorString(e));
+          return ADR_ECUDA;
+        }
+        ctl->launches += B->g_launches;
+        ctl->steps += kBatchChunk;
+      }
+    }
+  }
+  e = batch_step_direct(B, nsteps - done);
+  if (e != cudaSuccess) {
+    set_error(std::string("adr_batch_step: ") + cudaGetErrorString(e));
+    return ADR_ECUDA;
+  }
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_batch_set_timing(adr_batch batch, int enable) {
+  if (!batch) return ADR_EINVAL;
+  adr_status st = adr_plan_set_timing(batch->ctl, enable);
+  if (st == ADR_OK && batch->d_err) {
+    if (cudaMemset(batch->d_err, 0, sizeof(int)) != cudaSuccess) return ADR_ECUDA;
+  }
+  return st;
+}
+
+extern "C" adr_status adr_batch_stats(adr_batch batch, adr_stats* out) {
+  if (!batch || !out) return ADR_EINVAL;
+  adr_status st = adr_plan_stats(batch->ctl, out);
+  if (st == ADR_OK && batch->d_err) {
+    int h = 0;
+    if (cudaMemcpy(&h, batch->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return ADR_ECUDA;
+    out->device_error = h;
+  }
+  return st;
+}
+
+extern "C" int adr_batch_is_grouped(adr_batch batch) { return batch ? batch->grouped : 0; }

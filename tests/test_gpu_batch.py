@@ -1,0 +1,122 @@
+"""Batched solves (many independent grids of uneven sizes advanced by grouped
+launches): every result must equal the same solve run alone, and match the
+FP64 oracle within the 1e-5 max relative error bound."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from oracle import schemes
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def adr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2307_10684_gb300 import build
+    build.build()
+    import paper_2307_10684_gb300 as adr
+    return adr
+
+
+def mixed_problems(d=2, count=6, precision=wl.BF16X3):
+    sides = (64, 96, 128, 72, 136, 192) if d == 2 else (24, 40, 16, 32, 48, 56)
+    out = []
+    for i in range(count):
+        n = (sides[i % len(sides)], sides[(i + 2) % len(sides)])
+        if d == 3:
+            n = n + (sides[(i + 4) % len(sides)],)
+        if i % 2 == 0:
+            p = wl.Problem(d=d, n=n, lo=(0.0,) * d, hi=(1.0,) * d, diff=(1.0, 5.0 + 3 * i),
+                           adv=((0.0,) * d, (0.0,) * d), model=wl.SCHNAKENBERG,
+                           params=(100.0 + 150 * i, 0.1, 0.9), tau=2e-4, nsteps=20,
+                           precision=precision, seed=1000 + i)
+        else:
+            p = wl.Problem(d=d, n=n, lo=(0.0,) * d, hi=(100.0,) * d, diff=(1.0, 5.0 + 3 * i),
+                           adv=((0.5,) * d, (0.5,) * d), model=wl.FHN, params=(0.05, 2.0, -0.03),
+                           tau=1e-2, nsteps=20, precision=precision, seed=1000 + i)
+        out.append(p)
+    return out
+
+
+def states(adr, probs):
+    import torch
+    us, vs, inits = [], [], []
+    for p in probs:
+        u0, v0 = wl.initial_data(p)
+        u0, v0 = wl.round_to(u0, wl.FP32), wl.round_to(v0, wl.FP32)
+        inits.append((u0, v0))
+        us.append(torch.tensor(u0, dtype=torch.float32, device="cuda"))
+        vs.append(torch.tensor(v0, dtype=torch.float32, device="cuda"))
+    return us, vs, inits
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_batch_equals_alone_and_oracle(adr, d):
+    import torch
+    probs = mixed_problems(d)
+    nsteps = 20
+    plans = [adr.Plan(p) for p in probs]
+    us, vs, inits = states(adr, probs)
+    with adr.Batch(plans) as batch:
+        assert batch.grouped
+        batch.step(us, vs, nsteps)
+        st = batch.stats()
+    torch.cuda.synchronize()
+    assert st["device_error"] == 0
+    for i, (p, plan) in enumerate(zip(probs, plans)):
+        u = torch.tensor(inits[i][0], dtype=torch.float32, device="cuda")
+        v = torch.tensor(inits[i][1], dtype=torch.float32, device="cuda")
+        plan.step(u, v, nsteps)
+        torch.cuda.synchronize()
+        # alone vs in the mix: the same kernels on the same tiles, bit for bit
+        assert torch.equal(u, us[i]) and torch.equal(v, vs[i]), i
+        Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), *inits[i], nsteps)
+        err = oracle.max_rel_err(us[i].double().cpu().numpy(), vs[i].double().cpu().numpy(),
+                                 Ur, Vr)
+        assert err <= TOL, (i, err)
+    for plan in plans:
+        plan.close()
+
+
+def test_batch_graph_replay_matches_direct(adr, monkeypatch):
+    import torch
+    probs = mixed_problems(2, count=4)
+    outs = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("ADR_GRAPHS", graphs)
+        plans = [adr.Plan(p) for p in probs]
+        us, vs, _ = states(adr, probs)
+        with adr.Batch(plans) as batch:
+            batch.step(us, vs, 35)
+            st = batch.stats()
+        torch.cuda.synchronize()
+        outs.append(([u.cpu() for u in us], [v.cpu() for v in vs], st))
+        for plan in plans:
+            plan.close()
+    for a, b in zip(outs[0][0] + outs[0][1], outs[1][0] + outs[1][1]):
+        assert torch.equal(a, b)
+    assert outs[0][2]["launches"] == outs[1][2]["launches"] == 35 * 6
+    assert outs[0][2]["steps"] == 35
+
+
+def test_batch_of_fp32_plans_steps_each(adr):
+    import torch
+    probs = mixed_problems(2, count=3, precision=wl.FP32)
+    plans = [adr.Plan(p) for p in probs]
+    us, vs, inits = states(adr, probs)
+    with adr.Batch(plans) as batch:
+        assert not batch.grouped
+        batch.step(us, vs, 5)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), *inits[i], 5)
+        assert oracle.max_rel_err(us[i].double().cpu().numpy(), vs[i].double().cpu().numpy(),
+                                  Ur, Vr) <= TOL
+    for plan in plans:
+        plan.close()
