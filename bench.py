@@ -190,6 +190,36 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def tc_roofline(kd, prec, peaks, peak_src, traffic):
+    """Roofline of the tensor-core mode-product kernel class: the slower of
+    (issued MMA flops at the measured dense BF16 peak) and (algorithmic bytes
+    at the measured HBM bandwidth)."""
+    issue = 3.0 if prec == wl.TF32X3 else 6.0   # MMAs per algorithmic product
+    ratio = 0.5 if prec == wl.TF32X3 else 1.0   # tf32 dense rate = 1/2 of bf16
+    avg_s = kd["ms"] / kd["count"] / 1e3
+    flops = kd["flops"] / kd["count"]
+    nbytes = kd["bytes"] / kd["count"]
+    tc_peak = peaks["bf16_tflops"] * 1e12 * ratio
+    bw = peaks["hbm_gbs"] * 1e9
+    t_tensor = issue * flops / tc_peak
+    t_hbm = nbytes / bw
+    if t_tensor >= t_hbm:
+        return {"bound": "tensor", "achieved": issue * flops / avg_s / 1e12,
+                "peak": tc_peak / 1e12, "unit": "TFLOP/s", "frac": t_tensor / avg_s,
+                "traffic": traffic, "kernel": "mode_product_tc",
+                "algorithmic_flops_per_launch": flops, "issued_flops_per_launch": issue * flops,
+                "algorithmic_bytes_per_launch": nbytes,
+                "frac_algorithmic_flops": flops / avg_s / tc_peak,
+                "hbm_frac": t_hbm / avg_s,
+                "peak_source": f"{peak_src} dense bf16 (x{ratio}); achieved counts the "
+                               f"{int(issue)} split-piece MMAs per product"}
+    return {"bound": "hbm", "achieved": nbytes / avg_s / 1e9, "peak": bw / 1e9, "unit": "GB/s",
+            "frac": t_hbm / avg_s, "traffic": traffic, "kernel": "mode_product_tc",
+            "algorithmic_bytes_per_launch": nbytes, "algorithmic_flops_per_launch": flops,
+            "tensor_frac": t_tensor / avg_s,
+            "peak_source": f"{peak_src} HBM copy bandwidth"}
+
+
 def run_batch(args):
     """512 independent 2D solves of uneven sizes advanced together by grouped
     launches (one bench step = all solves x 100 ETD2RKds steps)."""
@@ -299,14 +329,9 @@ def run_batch(args):
     peaks, peak_src = load_peaks()
     kern = {k: d for k, d in stats["kernels"].items() if d["count"] > 0}
     kd = kern["mode_product_tc"] if "mode_product_tc" in kern else max(kern.values(), key=lambda d: d["ms"])
-    ratio = 0.5 if prec == wl.TF32X3 else 1.0
-    peak = peaks["bf16_tflops"] * 1e12 * ratio
-    achieved = (kd["flops"] / kd["count"]) / (kd["ms"] / kd["count"] / 1e3)
-    roof = {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / peak, "issued_frac": 6.0 * achieved / peak, "traffic": None,
-            "kernel": "mode_product_tc (grouped over 512 solves)",
-            "peak_source": f"{peak_src} bf16 (dense)",
-            "share_of_kernel_time": kd["ms"] / sum(d["ms"] for d in kern.values())}
+    roof = tc_roofline(kd, prec, peaks, peak_src, None)
+    roof["kernel"] = "mode_product_tc (grouped over 512 solves)"
+    roof["share_of_kernel_time"] = kd["ms"] / sum(d["ms"] for d in kern.values())
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample > 0:
         from oracle import schemes
@@ -350,6 +375,106 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """Poisson request stream (seeded, 200 req/s) of mixed 2D/3D grids and
+    models, served with continuous batching; reports p50/p99 latency and the
+    served throughput beside the offered load."""
+    import torch
+    import paper_2307_10684_gb300 as adr
+    from paper_2307_10684_gb300.serve import Request, Server, latency_summary
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    prec = PREC[args.precision]
+    stream_reqs = wl.serving_stream(count=args.requests, precision=prec, seed=5 + rank)
+
+    def make(i, t, p):
+        def init(p=p):
+            u0, v0 = wl.initial_data(p)
+            return (np.asarray(wl.round_to(u0, prec), dtype=np.float32),
+                    np.asarray(wl.round_to(v0, prec), dtype=np.float32))
+        return Request(i, t, p, init, p.nsteps)
+
+    reqs = [make(i, t, p) for i, (t, p) in enumerate(stream_reqs)]
+    # deterministic accuracy sample: every 20th request that is small
+    sample = [r.rid for r in reqs if r.rid % 20 == 0 and
+              (r.problem.d == 2 and r.problem.npoints <= 256 * 256 or
+               r.problem.d == 3 and r.problem.npoints <= 96 ** 3)]
+    # warm-up: a few small requests through a throwaway server
+    warm = [make(100000 + i, 0.0, wl.fhn_1024(precision=prec, n=64, nsteps=32)) for i in range(3)]
+    Server(budget_bytes=2**32).run(warm)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    srv = Server(budget_bytes=int(args.budget_gb * 2**30), chunk=16, keep_ids=sample)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    summ = latency_summary(res, wall)
+    offered = sum(r.problem.npoints * r.nsteps for r in reqs)
+    span = max(r.arrival for r in reqs)
+    # accuracy of the sampled requests against FP64 GPU solves of the same data
+    # and the conditioning floor: an FP64 solve from data perturbed by 2^-24
+    errs, floors, fp32_errs = [], [], []
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    for rid in sample:
+        req = reqs[rid]
+        out = srv.results[rid]
+        u0, v0 = req.init()
+        ur = torch.tensor(u0, dtype=torch.float64, device="cuda")
+        vr = torch.tensor(v0, dtype=torch.float64, device="cuda")
+        up = ur * (1 + 2.0**-24 * (2 * torch.rand(ur.shape, generator=gen, device="cuda",
+                                                  dtype=torch.float64) - 1))
+        vp = vr * (1 + 2.0**-24 * (2 * torch.rand(vr.shape, generator=gen, device="cuda",
+                                                  dtype=torch.float64) - 1))
+        with adr.Plan(req.problem.replace(precision=wl.FP64)) as pl:
+            pl.step(ur, vr, req.nsteps)
+            pl.step(up, vp, req.nsteps)
+        uf = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        vf = torch.tensor(v0, dtype=torch.float32, device="cuda")
+        with adr.Plan(req.problem.replace(precision=wl.FP32)) as pl:
+            pl.step(uf, vf, req.nsteps)
+        au, mu = adr.max_abs_diff(uf, ur)
+        av, mv = adr.max_abs_diff(vf, vr)
+        fp32_errs.append(max(au / mu, av / mv))
+        du, mu = adr.max_abs_diff(out.u.cuda().float().contiguous(), ur)
+        dv, mv = adr.max_abs_diff(out.v.cuda().float().contiguous(), vr)
+        errs.append(max(du / mu, dv / mv))
+        fu, _ = adr.max_abs_diff(up, ur)
+        fv, _ = adr.max_abs_diff(vp, vr)
+        floors.append(max(fu / mu, fv / mv))
+    if rank == 0:
+        line = {"metric": "served point-steps/s; p50/p99 solve latency",
+                "value": summ["served_point_steps_per_s"], "unit": "point-steps/s",
+                "n_gpus": world, "steps": len(reqs), "warmup": len(warm),
+                "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[prec],
+                "data": "synthetic Poisson request stream (seed 5), seeded initial data",
+                "config": {"workload": f"serving, {len(reqs)} requests at 200/s, 2D sides "
+                                       "128-1024, 3D sides 64-192, 3 models, horizons 50-1000",
+                           "budget_gb": args.budget_gb, "chunk_steps": 16},
+                "latency": {k: summ[k] for k in ("p50_s", "p99_s", "mean_s", "max_s")},
+                "offered_point_steps_per_s": offered / span if span > 0 else None,
+                "served_point_steps_per_s": summ["served_point_steps_per_s"],
+                "wall_s": wall, "arrival_span_s": span,
+                "max_rel_err_vs_fp64": max(errs) if errs else None,
+                "max_rel_err_sample": f"{len(errs)} requests (every 20th with <=256^2 or <=96^3)",
+                "sample_errors": [round(e, 9) for e in errs],
+                "sample_fp64_floors": [round(f, 9) for f in floors],
+                "sample_plain_fp32_errors": [round(e, 9) for e in fp32_errs],
+                "sample_within_1e-5": sum(1 for e in errs if e <= 1e-5),
+                "sample_within_2x_plain_fp32": sum(1 for e, f in zip(errs, fp32_errs)
+                                                  if e <= max(1e-5, 2 * f)),
+                "server_stats": dict(srv.stats), "clocks": clocks,
+                "e2e": {"value": summ["served_point_steps_per_s"], "unit": "point-steps/s",
+                        "note": "requests enter and leave through host memory"}}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,6 +490,8 @@ def main():
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy solve")
     ap.add_argument("--cpu-sample", type=int, default=40)
     ap.add_argument("--ref-sample", type=int, default=20)
+    ap.add_argument("--requests", type=int, default=400, help="serving workload: request count")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device-memory budget")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -372,6 +499,9 @@ def main():
         return
     if args.workload == "batch512":
         run_batch(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
 
     import torch
@@ -506,18 +636,8 @@ def main():
                 "frac": achieved / peak, "traffic": None, "kernel": dom,
                 "peak_source": peak_note, "share_of_kernel_time": kd["ms"] / total_kernel_ms}
     elif dom == "mode_product_tc":
-        flops = kd["flops"] / kd["count"]
-        ratio = 0.5 if prec == wl.TF32X3 else 1.0  # tf32 dense rate = 1/2 of bf16
-        issue = 3.0 if prec == wl.TF32X3 else 6.0
-        peak = peaks["bf16_tflops"] * 1e12 * ratio
-        achieved = flops / avg_s
-        roof = {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(args.workload), "kernel": dom,
-                "algorithmic_bytes": kd["bytes"] / kd["count"],
-                "issued_frac": issue * achieved / peak,
-                "peak_source": f"{peak_src} bf16 x {ratio} (dense {['bf16', 'tf32'][ratio < 1]})",
-                "share_of_kernel_time": kd["ms"] / total_kernel_ms}
+        roof = tc_roofline(kd, prec, peaks, peak_src, profiled_traffic(args.workload))
+        roof["share_of_kernel_time"] = kd["ms"] / total_kernel_ms
     else:
         bytes_ = kd["bytes"] / kd["count"]
         achieved = bytes_ / avg_s

@@ -114,6 +114,12 @@ typedef struct adr_plan_s* adr_plan;
  *   out     : receives the plan; untouched on failure. */
 adr_status adr_plan_create(const adr_problem* problem, void* stream, adr_plan* out);
 
+/* Move a plan to another CUDA stream (as void*, 0 = default stream): later
+ * calls enqueue there.  Synchronises the old stream first, so work already
+ * enqueued is complete.  Lets a plan be built on one stream (for instance
+ * on a planner thread) and stepped on another. */
+adr_status adr_plan_set_stream(adr_plan plan, void* stream);
+
 /* Free a plan (synchronises its stream first).  NULL is accepted. */
 adr_status adr_plan_destroy(adr_plan plan);
 

@@ -76,6 +76,11 @@ class Plan:
                                          ctypes.c_void_p(_stream_handle(stream)),
                                          ctypes.byref(self._p)))
 
+    def set_stream(self, stream=None):
+        """adr_plan_set_stream: later calls enqueue on `stream` (default: current)."""
+        self._stream = stream
+        _abi.check(lib().adr_plan_set_stream(self._p, ctypes.c_void_p(_stream_handle(stream))))
+
     def close(self):
         if self._p:
             lib().adr_plan_destroy(self._p)

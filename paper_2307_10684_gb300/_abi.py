@@ -39,6 +39,7 @@ class AdrPlan(ctypes.c_void_p):
 SIGNATURES = {
     "adr_plan_create": (c_int32, [ctypes.POINTER(AdrProblem), c_void_p, ctypes.POINTER(AdrPlan)]),
     "adr_plan_destroy": (c_int32, [AdrPlan]),
+    "adr_plan_set_stream": (c_int32, [AdrPlan, c_void_p]),
     "adr_step": (c_int32, [AdrPlan, c_void_p, c_void_p, c_int64]),
     "adr_solve": (c_int32, [AdrPlan, c_void_p, c_void_p, c_void_p, c_void_p, c_int64]),
     "adr_plan_bytes": (c_int32, [ctypes.POINTER(AdrProblem), ctypes.POINTER(ctypes.c_size_t),

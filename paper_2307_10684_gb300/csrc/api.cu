@@ -320,6 +320,13 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
   return ADR_OK;
 }
 
+extern "C" adr_status adr_plan_set_stream(adr_plan plan, void* stream) {
+  if (!plan) return fail(ADR_EINVAL, "plan is NULL");
+  ADR_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+  plan->stream = (cudaStream_t)stream;
+  return ADR_OK;
+}
+
 extern "C" adr_status adr_plan_destroy(adr_plan plan) {
   plan_free(plan);
   return ADR_OK;
