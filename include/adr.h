@@ -54,7 +54,8 @@ typedef enum {
   ADR_EBUSY = 7          /* resource busy (admission refused)              */
 } adr_status;
 
-/* Reaction models g^u, g^v and the meaning of adr_problem.params[]:
+/* Reaction models g^u, g^v and the meaning of adr_problem.params[]
+ * (unused entries must be 0):
  *  ADR_SCHNAKENBERG (Sec. 4.1, Eq. 12): params {gamma, a, b}
  *     g^u = gamma (a - u + u^2 v),  g^v = gamma (b - u^2 v)
  *  ADR_FHN, FitzHugh-Nagumo with linear recovery: params {eps, a1, a0}
@@ -66,7 +67,15 @@ typedef enum {
   ADR_SCHNAKENBERG = 0,
   ADR_FHN = 1,
   ADR_BRUSSELATOR = 2,
-  ADR_NO_REACTION = 3
+  ADR_NO_REACTION = 3,
+  ADR_FHN_RHO = 4,   /* FitzHugh-Nagumo as in Sec. 4.2-4.3, Eq. 13-14:
+                        params {rho, a1, a2}: g^u = rho (u - u^3 - v),
+                        g^v = rho a1 (u - a2 v)                             */
+  ADR_DIB = 5        /* morpho-chemical DIB model, Sec. 4.4, Eq. 15: params
+                        {rho, a1u, a2u, a3u, a4u, a1v, a2v, a3v, a4v, a5v}:
+                        g^u = rho (a1u (1 - v) u - a2u u^3 - a3u (v - a4u)),
+                        g^v = rho (a1v (1 + a2v u) (1 - v) (1 - a3v (1 - v))
+                                   - a4v v (1 + a5v u) (1 + a3v v))         */
 } adr_model;
 
 /* Arithmetic of the mode products (the Tucker operators).
@@ -87,17 +96,27 @@ typedef enum {
   ADR_BF16X3 = 3
 } adr_precision;
 
+/* Time-stepping scheme.
+ *  ADR_ETD2RKDS : directional split ETD2RK, Sec. 3, Eq. 11 (the default).
+ *  ADR_LAWSON2B : second-order Lawson scheme in tensor form, Eq. 7: two
+ *                 Tucker operators of e^(tau A_mu) per component and step;
+ *                 no splitting error, so exact to rounding when g = 0. */
+typedef enum {
+  ADR_ETD2RKDS = 0,
+  ADR_LAWSON2B = 1
+} adr_scheme;
+
 /* One problem.  Direction mu = 0 is x_1 (the contiguous axis). */
 typedef struct {
   int32_t d;            /* 2 or 3                                           */
   int32_t model;        /* adr_model                                        */
   int32_t precision;    /* adr_precision                                    */
-  int32_t flags;        /* reserved, must be 0                              */
+  int32_t scheme;       /* adr_scheme                                       */
   int64_t n[3];         /* grid points per direction, 3 <= n[mu] <= 4096    */
   double lo[3], hi[3];  /* domain [lo_mu, hi_mu], hi > lo                   */
   double diff[2];       /* diffusion delta^u, delta^v (> 0)                 */
   double adv[2][3];     /* velocity of the term -adv[c] . grad(c)           */
-  double params[8];     /* model constants, see adr_model                   */
+  double params[16];    /* model constants, see adr_model                   */
   double tau;           /* constant time step (> 0)                         */
 } adr_problem;
 
@@ -220,6 +239,16 @@ adr_status adr_max_abs_diff(void* stream, const void* x, int x_is_double, const 
  * returning; out: host. */
 adr_status adr_max_abs_diff_noalloc(void* stream, const void* x, int x_is_double,
                                     const double* ref, int64_t count, double out[2]);
+
+/* Dynamics indicators of Sec. 4 for the state (u, v) after a step from
+ * (u_prev, v_prev): out[0], out[1] = spatial means <U>, <V> (trapezoid
+ * weights on the vertex grid, divided by the weights' sum, i.e. by |Omega|
+ * in grid units); out[2], out[3] = ||U - U_prev||_F, ||V - V_prev||_F.  All
+ * four pointers are device state tensors of the plan's shape and type; out
+ * is host memory.  Accumulates in FP64 on the GPU into plan-owned scratch;
+ * synchronous. */
+adr_status adr_indicators(adr_plan plan, const void* u_prev, const void* v_prev, const void* u,
+                          const void* v, double out[4]);
 
 /* Short name of a status code (static storage). */
 const char* adr_status_str(adr_status s);

@@ -19,7 +19,9 @@ from typing import Optional
 from . import _abi
 from ._abi import (ADR_OK, ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA, ADR_EUNSUPPORTED,  # noqa: F401
                    ADR_ETIMEOUT, ADR_ENUMERIC, ADR_EBUSY, FP64, FP32, TF32X3, BF16X3,
-                   SCHNAKENBERG, FHN, BRUSSELATOR, NO_REACTION, AdrError, lib, library_path)
+                   SCHNAKENBERG, FHN, BRUSSELATOR, NO_REACTION, FHN_RHO, DIB, ETD2RKDS,
+                   LAWSON2B, AdrError, lib,
+                   library_path)
 
 __all__ = ["Plan", "Batch", "AdrError", "lib", "library_path", "plan_bytes", "max_abs_diff",
            "make_problem", "state_dtype"]
@@ -32,7 +34,7 @@ def make_problem(p) -> _abi.AdrProblem:
     s.d = int(p.d)
     s.model = int(p.model)
     s.precision = int(p.precision)
-    s.flags = 0
+    s.scheme = int(getattr(p, "scheme", 0))
     def at(seq, i, default):
         return seq[i] if i < min(len(seq), max(int(p.d), 0)) else default
 
@@ -44,7 +46,9 @@ def make_problem(p) -> _abi.AdrProblem:
         s.diff[c] = float(p.diff[c])
         for m in range(3):
             s.adv[c][m] = float(at(p.adv[c], m, 0.0))
-    for i in range(8):
+    if len(p.params) > 16:
+        raise ValueError("at most 16 model parameters")
+    for i in range(16):
         s.params[i] = float(p.params[i]) if i < len(p.params) else 0.0
     s.tau = float(p.tau)
     return s
@@ -132,6 +136,17 @@ class Plan:
         _abi.check(lib().adr_plan_matrix(self._p, int(which), int(component), int(mu),
                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
+
+    def indicators(self, u_prev, v_prev, u, v):
+        """adr_indicators: (<U>, <V>, ||U - U_prev||_F, ||V - V_prev||_F)."""
+        for x in (u_prev, v_prev, u, v):
+            self._check_state(x, True)
+        out = (ctypes.c_double * 4)()
+        _abi.check(lib().adr_indicators(self._p, ctypes.c_void_p(u_prev.data_ptr()),
+                                        ctypes.c_void_p(v_prev.data_ptr()),
+                                        ctypes.c_void_p(u.data_ptr()),
+                                        ctypes.c_void_p(v.data_ptr()), out))
+        return tuple(float(x) for x in out)
 
     def set_timing(self, enable: bool):
         _abi.check(lib().adr_plan_set_timing(self._p, 1 if enable else 0))

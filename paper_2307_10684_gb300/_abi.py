@@ -10,16 +10,17 @@ library_path = os.path.join(_PKG, "_build", "libadr_gb300.so")
 
 ADR_OK, ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA, ADR_EUNSUPPORTED, ADR_ETIMEOUT, ADR_ENUMERIC, \
     ADR_EBUSY = range(8)
-SCHNAKENBERG, FHN, BRUSSELATOR, NO_REACTION = range(4)
+SCHNAKENBERG, FHN, BRUSSELATOR, NO_REACTION, FHN_RHO, DIB = range(6)
+ETD2RKDS, LAWSON2B = range(2)
 FP64, FP32, TF32X3, BF16X3 = range(4)
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
 
 class AdrProblem(ctypes.Structure):
-    _fields_ = [("d", c_int32), ("model", c_int32), ("precision", c_int32), ("flags", c_int32),
+    _fields_ = [("d", c_int32), ("model", c_int32), ("precision", c_int32), ("scheme", c_int32),
                 ("n", c_int64 * 3), ("lo", c_double * 3), ("hi", c_double * 3),
-                ("diff", c_double * 2), ("adv", (c_double * 3) * 2), ("params", c_double * 8),
+                ("diff", c_double * 2), ("adv", (c_double * 3) * 2), ("params", c_double * 16),
                 ("tau", c_double)]
 
 
@@ -59,6 +60,8 @@ SIGNATURES = {
     "adr_batch_set_timing": (c_int32, [c_void_p, c_int32]),
     "adr_batch_stats": (c_int32, [c_void_p, ctypes.POINTER(AdrStats)]),
     "adr_batch_is_grouped": (c_int32, [c_void_p]),
+    "adr_indicators": (c_int32, [AdrPlan, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 ctypes.POINTER(c_double)]),
     "adr_status_str": (ctypes.c_char_p, [c_int32]),
     "adr_last_error": (ctypes.c_char_p, []),
 }

@@ -37,7 +37,7 @@ using Tridiag = TridiagT<double>;
 template <typename T>
 struct ReactionT {
   int model;
-  T p[8];
+  T p[16];
 };
 
 // Stencil + reaction description for one problem, passed by value.  The
@@ -64,7 +64,7 @@ inline PointwiseArgsT<T> cast_args(const PointwiseArgs& a) {
       r.A[c][m] = TridiagT<T>{(T)a.A[c][m].lo, (T)a.A[c][m].di, (T)a.A[c][m].up,
                               (T)a.A[c][m].b0, (T)a.A[c][m].bn};
   r.rx.model = a.rx.model;
-  for (int i = 0; i < 8; ++i) r.rx.p[i] = (T)a.rx.p[i];
+  for (int i = 0; i < 16; ++i) r.rx.p[i] = (T)a.rx.p[i];
   return r;
 }
 
@@ -93,6 +93,12 @@ template <typename T>
 cudaError_t launch_rhs(const PointwiseArgsT<T>& a, const T* u, const T* v, T* wu, T* wv,
                        cudaStream_t s);
 template <typename T>
+cudaError_t launch_lawson_pre(const PointwiseArgsT<T>& a, const T* u, const T* v, T scale, T* xu,
+                              T* xv, cudaStream_t s);
+template <typename T>
+cudaError_t launch_lawson_post(const PointwiseArgsT<T>& a, const T* u2, const T* v2, T scale, T* u,
+                               T* v, cudaStream_t s);
+template <typename T>
 cudaError_t launch_rdiff(const PointwiseArgsT<T>& a, const T* u, const T* v, const T* u2,
                          const T* v2, T* du, T* dv, cudaStream_t s);
 
@@ -102,6 +108,9 @@ cudaError_t matfun_phi(int n, const Tridiag& A, double tau, double* E, double* P
 cudaError_t launch_build_dense(int n, const Tridiag& A, double scale, double* X, cudaStream_t s);
 cudaError_t launch_convert(const double* src, void* dst, int64_t count, int to_double,
                            int transpose_n, cudaStream_t s);
+cudaError_t launch_indicators(const PointwiseArgs& a, const void* up, const void* vp,
+                              const void* u, const void* v, int is_double, double* acc,
+                              cudaStream_t s);
 cudaError_t launch_max_abs_diff(const void* x, int x_is_double, const double* ref, int64_t count,
                                 unsigned long long* out2, cudaStream_t s);
 
@@ -117,7 +126,14 @@ struct TcOperands {
 
 }  // namespace adr
 
-enum KernelClass { KC_RHS = 0, KC_RDIFF = 1, KC_MODE_SIMT = 2, KC_MODE_TC = 3, KC_COUNT = 4 };
+enum KernelClass {
+  KC_RHS = 0,
+  KC_RDIFF = 1,
+  KC_MODE_SIMT = 2,
+  KC_MODE_TC = 3,
+  KC_LAWSON_PW = 4,
+  KC_COUNT = 5
+};
 
 struct TimedLaunch {
   int cls;
@@ -132,14 +148,15 @@ struct adr_plan_s {
   int64_t n[3];
   int64_t N;
   int prec;
+  int scheme;    // adr_scheme
   size_t esize;  // bytes per state element
   adr::PointwiseArgs pw;            // FP64 master
   adr::PointwiseArgsT<float> pwf;   // single-precision copy for FP32-state kernels
   // FP64 masters [c][mu][which], which: 0 = A, 1 = e^(tau A), 2 = phi_1, 3 = phi_2
   double* master[2][3][4];
   // SIMT operands: phi_ell row-major and transposed, in the state type
-  void* op[2][3][2];
-  void* opT[2][3][2];
+  void* op[2][3][3];    // [c][mu][ell]: ell 0 = e^(tau A), 1 = phi_1, 2 = phi_2
+  void* opT[2][3][3];
   // tensor-core operands
   adr::TcOperands tc;
   // workspace
@@ -148,6 +165,7 @@ struct adr_plan_s {
   void* bufA[2];
   void* bufB[2];
   void* dstate[2];  // device state for adr_solve with host buffers
+  double* ind;      // 4 accumulators of adr_indicators
   std::vector<void*> allocs;
   // counters
   int64_t launches;
@@ -168,10 +186,11 @@ struct adr_plan_s {
 
 namespace adr {
 static const char* const kClassNames[KC_COUNT] = {"rhs_stencil_reaction", "reaction_diff",
-                                                  "mode_product_simt", "mode_product_tc"};
+                                                  "mode_product_simt", "mode_product_tc",
+                                                  "lawson_pointwise"};
 void tc_init(TcOperands* t);
 void tc_free(TcOperands* t);
-cudaError_t tc_prepare(TcOperands* t, int prec, int d, const int64_t n[3],
+cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t n[3],
                        double* const master[2][3][4], cudaStream_t s);
 cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v);
 cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v);

@@ -48,8 +48,9 @@ static cudaError_t plan_alloc(adr_plan P, void** out, size_t bytes) {
 static adr_status validate(const adr_problem* p) {
   if (!p) return fail(ADR_EINVAL, "problem is NULL");
   if (p->d != 2 && p->d != 3) return fail(ADR_EINVAL, "d must be 2 or 3");
-  if (p->flags != 0) return fail(ADR_EINVAL, "flags must be 0");
-  if (p->model < 0 || p->model > ADR_NO_REACTION) return fail(ADR_EINVAL, "unknown model");
+  if (p->scheme != ADR_ETD2RKDS && p->scheme != ADR_LAWSON2B)
+    return fail(ADR_EINVAL, "unknown scheme");
+  if (p->model < 0 || p->model > ADR_DIB) return fail(ADR_EINVAL, "unknown model");
   if (p->precision < 0 || p->precision > ADR_BF16X3)
     return fail(ADR_EINVAL, "unknown precision");
   if (!(p->tau > 0.0) || !isfinite(p->tau)) return fail(ADR_EINVAL, "tau must be finite and > 0");
@@ -67,7 +68,7 @@ static adr_status validate(const adr_problem* p) {
     for (int m = 0; m < p->d; ++m)
       if (!isfinite(p->adv[c][m])) return fail(ADR_EINVAL, "advection must be finite");
   }
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 16; ++i)
     if (!isfinite(p->params[i])) return fail(ADR_EINVAL, "params must be finite");
   return ADR_OK;
 }
@@ -109,7 +110,7 @@ static cudaError_t mode_product_simt(adr_plan P, int mu, int ell, void* const in
   if (mu == 0) {  // Y[p][i] = sum_j X[p][j] Phi[i][j]  ->  Y = X Phi^T
     for (int c = 0; c < 2; ++c) {
       g.A[c] = in[c];
-      g.B[c] = P->opT[c][mu][ell - 1];
+      g.B[c] = P->opT[c][mu][ell];
     }
     g.M = (int)Pb;
     g.N = (int)n;
@@ -120,7 +121,7 @@ static cudaError_t mode_product_simt(adr_plan P, int mu, int ell, void* const in
     g.batch = 1;
   } else {  // Y[p] = Phi X[p], X[p] an n x Q row-major slab
     for (int c = 0; c < 2; ++c) {
-      g.A[c] = P->op[c][mu][ell - 1];
+      g.A[c] = P->op[c][mu][ell];
       g.B[c] = in[c];
     }
     g.M = (int)n;
@@ -197,6 +198,34 @@ static cudaError_t step_simt(adr_plan P, T* u, T* v) {
   return tucker_simt<T>(P, 2, P->bufA, uv, st2, c2);
 }
 
+// Lawson2b, Eq. 7:  U2 = (U + tau G(U,V)) x_mu e^(tau A_mu),
+//                   U+ = (U + tau/2 G(U,V)) x_mu e^(tau A_mu) + tau/2 G(U2, V2).
+template <typename T>
+static cudaError_t step_lawson_simt(adr_plan P, T* u, T* v) {
+  const T tau = (T)P->prob.tau;
+  const double N = (double)P->N;
+  void* uv[2] = {u, v};
+  void* st2[2] = {P->u2, P->v2};
+  auto pre = [&](T scale) {
+    return timed_kernel(P, KC_LAWSON_PW, N * 2.0 * 12.0, sizeof(T) * N * 4.0, [&] {
+      return launch_lawson_pre<T>(pw_for<T>(P), u, v, scale, (T*)P->bufA[0], (T*)P->bufA[1],
+                                  P->stream);
+    });
+  };
+  cudaError_t e = pre(tau);
+  if (e != cudaSuccess) return e;
+  e = tucker_simt<T>(P, 0, P->bufA, st2, nullptr, 1.0);
+  if (e != cudaSuccess) return e;
+  e = pre(tau / (T)2);
+  if (e != cudaSuccess) return e;
+  e = tucker_simt<T>(P, 0, P->bufA, uv, nullptr, 1.0);
+  if (e != cudaSuccess) return e;
+  return timed_kernel(P, KC_LAWSON_PW, N * 2.0 * 12.0, sizeof(T) * N * 6.0, [&] {
+    return launch_lawson_post<T>(pw_for<T>(P), (const T*)P->u2, (const T*)P->v2, tau / (T)2, u,
+                                 v, P->stream);
+  });
+}
+
 // ---------------------------------------------------------------- plan
 static void plan_free(adr_plan P) {
   if (!P) return;
@@ -225,6 +254,7 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
   for (int m = 0; m < 3; ++m) P->n[m] = m < P->d ? problem->n[m] : 1;
   for (int m = 0; m < P->d; ++m) P->N *= P->n[m];
   P->prec = problem->precision;
+  P->scheme = problem->scheme;
   P->esize = P->prec == ADR_FP64 ? sizeof(double) : sizeof(float);
   P->launches = 0;
   P->steps = 0;
@@ -245,7 +275,7 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
   pw.N = P->N;
   for (int m = 0; m < 3; ++m) pw.n[m] = P->n[m];
   pw.rx.model = problem->model;
-  for (int i = 0; i < 8; ++i) pw.rx.p[i] = problem->params[i];
+  for (int i = 0; i < 16; ++i) pw.rx.p[i] = problem->params[i];
   for (int c = 0; c < 2; ++c)
     for (int m = 0; m < P->d; ++m)
       pw.A[c][m] = fd_coefficients(P->n[m], problem->lo[m], problem->hi[m], problem->diff[c],
@@ -273,7 +303,7 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
           if (c2 == c && m2 >= m) break;
           if (P->n[m2] == n && same_operator(pw.A[c2][m2], pw.A[c][m])) {
             for (int w = 0; w < 4; ++w) P->master[c][m][w] = P->master[c2][m2][w];
-            for (int l = 0; l < 2; ++l) {
+            for (int l = 0; l < 3; ++l) {
               P->op[c][m][l] = P->op[c2][m2][l];
               P->opT[c][m][l] = P->opT[c2][m2][l];
             }
@@ -286,12 +316,13 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
       PLAN_TRY(launch_build_dense((int)n, pw.A[c][m], 1.0, P->master[c][m][0], P->stream));
       PLAN_TRY(matfun_phi((int)n, pw.A[c][m], problem->tau, P->master[c][m][1],
                           P->master[c][m][2], P->master[c][m][3], P->stream));
-      for (int l = 0; l < 2; ++l) {
+      // SIMT operands (FP32/FP64 plans): e^(tau A), phi_1, phi_2 and transposes
+      for (int l = 0; l < 3 && P->prec <= ADR_FP32; ++l) {
         PLAN_TRY(plan_alloc(P, &P->op[c][m][l], nn * P->esize));
         PLAN_TRY(plan_alloc(P, &P->opT[c][m][l], nn * P->esize));
-        PLAN_TRY(launch_convert(P->master[c][m][2 + l], P->op[c][m][l], (int64_t)nn,
+        PLAN_TRY(launch_convert(P->master[c][m][1 + l], P->op[c][m][l], (int64_t)nn,
                                 P->prec == ADR_FP64, 0, P->stream));
-        PLAN_TRY(launch_convert(P->master[c][m][2 + l], P->opT[c][m][l], (int64_t)nn,
+        PLAN_TRY(launch_convert(P->master[c][m][1 + l], P->opT[c][m][l], (int64_t)nn,
                                 P->prec == ADR_FP64, (int)n, P->stream));
       }
     }
@@ -304,7 +335,7 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
     PLAN_TRY(plan_alloc(P, &P->bufB[c], sb));
   }
   if (P->prec == ADR_TF32X3 || P->prec == ADR_BF16X3) {
-    e = tc_prepare(&P->tc, P->prec, P->d, P->n, P->master, P->stream);
+    e = tc_prepare(&P->tc, P->prec, P->scheme, P->d, P->n, P->master, P->stream);
     if (e != cudaSuccess) {
       const bool unsup = (e == cudaErrorNotSupported);
       set_error(std::string("adr_plan_create: tensor-core operands: ") + cudaGetErrorString(e));
@@ -312,6 +343,7 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
       return unsup ? ADR_EUNSUPPORTED : ADR_ECUDA;
     }
   }
+  PLAN_TRY(plan_alloc(P, (void**)&P->ind, 4 * sizeof(double)));
   PLAN_TRY(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   PLAN_TRY(cudaStreamSynchronize(P->stream));
   PLAN_TRY(cudaGetLastError());
@@ -344,10 +376,13 @@ static bool is_device_ptr(const void* p) {
 static cudaError_t step_direct(adr_plan P, void* u, void* v, int64_t nsteps) {
   for (int64_t s = 0; s < nsteps; ++s) {
     cudaError_t e;
+    const bool lawson = P->scheme == ADR_LAWSON2B;
     if (P->prec == ADR_FP64)
-      e = step_simt<double>(P, (double*)u, (double*)v);
+      e = lawson ? step_lawson_simt<double>(P, (double*)u, (double*)v)
+                 : step_simt<double>(P, (double*)u, (double*)v);
     else if (P->prec == ADR_FP32)
-      e = step_simt<float>(P, (float*)u, (float*)v);
+      e = lawson ? step_lawson_simt<float>(P, (float*)u, (float*)v)
+                 : step_simt<float>(P, (float*)u, (float*)v);
     else
       e = tc_step(&P->tc, P, u, v);
     if (e != cudaSuccess) return e;
@@ -541,6 +576,27 @@ extern "C" adr_status adr_plan_stats(adr_plan plan, adr_stats* out) {
       out->bytes[t.cls] += t.bytes;
     }
   }
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_indicators(adr_plan plan, const void* u_prev, const void* v_prev,
+                                     const void* u, const void* v, double out[4]) {
+  if (!plan || !u_prev || !v_prev || !u || !v || !out) return fail(ADR_EINVAL, "NULL argument");
+  if (!is_device_ptr(u_prev) || !is_device_ptr(v_prev) || !is_device_ptr(u) || !is_device_ptr(v))
+    return fail(ADR_EINVAL, "adr_indicators needs device pointers");
+  adr_plan P = plan;
+  double h[4];
+  ADR_CUDA_TRY(cudaMemsetAsync(P->ind, 0, 4 * sizeof(double), P->stream));
+  ADR_CUDA_TRY(launch_indicators(P->pw, u_prev, v_prev, u, v, P->prec == ADR_FP64, P->ind,
+                                 P->stream));
+  ADR_CUDA_TRY(cudaMemcpyAsync(h, P->ind, sizeof(h), cudaMemcpyDeviceToHost, P->stream));
+  ADR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  double wsum = 1.0;
+  for (int m = 0; m < P->d; ++m) wsum *= (double)(P->n[m] - 1);
+  out[0] = h[0] / wsum;
+  out[1] = h[1] / wsum;
+  out[2] = sqrt(h[2]);
+  out[3] = sqrt(h[3]);
   return ADR_OK;
 }
 

@@ -256,11 +256,58 @@ __global__ void max_abs_diff_kernel(const void* __restrict__ x, int x_is_double,
   }
 }
 
+// Weighted sums for the dynamics indicators: acc[0] += w u, acc[1] += w v,
+// acc[2] += (u - up)^2, acc[3] += (v - vp)^2 with trapezoid weights w.
+__global__ void __launch_bounds__(256) indicators_kernel(PointwiseArgs a, const void* __restrict__ up,
+                                                         const void* __restrict__ vp,
+                                                         const void* __restrict__ u,
+                                                         const void* __restrict__ v, int is_double,
+                                                         double* __restrict__ acc) {
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t n1 = a.n[0], n2 = a.n[1], n3 = a.d == 3 ? a.n[2] : 1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i1 = e % n1, r = e / n1, i2 = r % n2, i3 = r / n2;
+    double w = (i1 == 0 || i1 == n1 - 1) ? 0.5 : 1.0;
+    w *= (i2 == 0 || i2 == n2 - 1) ? 0.5 : 1.0;
+    if (a.d == 3) w *= (i3 == 0 || i3 == n3 - 1) ? 0.5 : 1.0;
+    double x, y, xp, yp;
+    if (is_double) {
+      x = ((const double*)u)[e];
+      y = ((const double*)v)[e];
+      xp = ((const double*)up)[e];
+      yp = ((const double*)vp)[e];
+    } else {
+      x = ((const float*)u)[e];
+      y = ((const float*)v)[e];
+      xp = ((const float*)up)[e];
+      yp = ((const float*)vp)[e];
+    }
+    s[0] += w * x;
+    s[1] += w * y;
+    s[2] += (x - xp) * (x - xp);
+    s[3] += (y - yp) * (y - yp);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double t = s[k];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&acc[k], t);
+  }
+}
+
 static int grid_for(int64_t total) {
   int64_t b = (total + 255) / 256;
   if (b < 1) b = 1;
   if (b > 152 * 16) b = 152 * 16;
   return (int)b;
+}
+
+cudaError_t launch_indicators(const PointwiseArgs& a, const void* up, const void* vp,
+                              const void* u, const void* v, int is_double, double* acc,
+                              cudaStream_t s) {
+  indicators_kernel<<<grid_for(a.N), 256, 0, s>>>(a, up, vp, u, v, is_double, acc);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_build_dense(int n, const Tridiag& A, double scale, double* X, cudaStream_t s) {

@@ -29,6 +29,19 @@ __device__ __forceinline__ void react(const ReactionT<T>& rx, T u, T v, T& gu, T
       gu = a - (b + (T)1) * u + u2v;
       gv = b * u - u2v;
     } break;
+    case ADR_FHN_RHO: {
+      const T rho = rx.p[0], a1 = rx.p[1], a2 = rx.p[2];
+      gu = rho * (u - u * u * u - v);
+      gv = rho * a1 * (u - a2 * v);
+    } break;
+    case ADR_DIB: {
+      const T rho = rx.p[0], a1u = rx.p[1], a2u = rx.p[2], a3u = rx.p[3], a4u = rx.p[4];
+      const T a1v = rx.p[5], a2v = rx.p[6], a3v = rx.p[7], a4v = rx.p[8], a5v = rx.p[9];
+      const T one = (T)1;
+      gu = rho * (a1u * (one - v) * u - a2u * u * u * u - a3u * (v - a4u));
+      gv = rho * (a1v * (one + a2v * u) * (one - v) * (one - a3v * (one - v)) -
+                  a4v * v * (one + a5v * u) * (one + a3v * v));
+    } break;
     default:
       gu = (T)0;
       gv = (T)0;

@@ -40,6 +40,36 @@ __global__ void __launch_bounds__(256) rdiff_kernel(PointwiseArgsT<T> a, const T
   }
 }
 
+// Lawson2b (Eq. 7) pointwise stages: x = u + scale G^u(u, v) (both
+// components), and u += scale G^u(u2, v2).
+template <typename T>
+__global__ void __launch_bounds__(256) lawson_pre_kernel(PointwiseArgsT<T> a, const T* __restrict__ u,
+                                                         const T* __restrict__ v, T scale,
+                                                         T* __restrict__ xu, T* __restrict__ xv) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.N;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    T gu, gv;
+    const T uu = u[idx], vv = v[idx];
+    react<T>(a.rx, uu, vv, gu, gv);
+    xu[idx] = uu + scale * gu;
+    xv[idx] = vv + scale * gv;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) lawson_post_kernel(PointwiseArgsT<T> a,
+                                                          const T* __restrict__ u2,
+                                                          const T* __restrict__ v2, T scale,
+                                                          T* __restrict__ u, T* __restrict__ v) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.N;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    T gu, gv;
+    react<T>(a.rx, u2[idx], v2[idx], gu, gv);
+    u[idx] += scale * gu;
+    v[idx] += scale * gv;
+  }
+}
+
 static int pointwise_grid(int64_t N) {
   int64_t b = (N + 255) / 256;
   const int64_t cap = 152 * 16;
@@ -61,6 +91,30 @@ cudaError_t launch_rdiff(const PointwiseArgsT<T>& a, const T* u, const T* v, con
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_lawson_pre(const PointwiseArgsT<T>& a, const T* u, const T* v, T scale, T* xu,
+                              T* xv, cudaStream_t s) {
+  lawson_pre_kernel<T><<<pointwise_grid(a.N), 256, 0, s>>>(a, u, v, scale, xu, xv);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lawson_post(const PointwiseArgsT<T>& a, const T* u2, const T* v2, T scale, T* u,
+                               T* v, cudaStream_t s) {
+  lawson_post_kernel<T><<<pointwise_grid(a.N), 256, 0, s>>>(a, u2, v2, scale, u, v);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_lawson_pre<float>(const PointwiseArgsT<float>&, const float*,
+                                              const float*, float, float*, float*, cudaStream_t);
+template cudaError_t launch_lawson_pre<double>(const PointwiseArgsT<double>&, const double*,
+                                               const double*, double, double*, double*,
+                                               cudaStream_t);
+template cudaError_t launch_lawson_post<float>(const PointwiseArgsT<float>&, const float*,
+                                               const float*, float, float*, float*, cudaStream_t);
+template cudaError_t launch_lawson_post<double>(const PointwiseArgsT<double>&, const double*,
+                                                const double*, double, double*, double*,
+                                                cudaStream_t);
 template cudaError_t launch_rhs<float>(const PointwiseArgsT<float>&, const float*, const float*, float*,
                                        float*, cudaStream_t);
 template cudaError_t launch_rhs<double>(const PointwiseArgsT<double>&, const double*, const double*,

@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const bool ok = mrow && j < jm;
-          pb[buf][0][j] = ok ? __ldg(bsrc0 + o0 + (int64_t)j * M) : 0.f;
+          pb[buf][0][j] = (ok && bsrc0) ? __ldg(bsrc0 + o0 + (int64_t)j * M) : 0.f;
           pb[buf][1][j] = (ok && bsrc1) ? __ldg(bsrc1 + o0 + (int64_t)j * M) : 0.f;
         }
       };
@@ -529,6 +529,7 @@ struct PwDesc {
   const float* v2;
   __nv_bfloat16* wu;   // pieces [3][N] of the u output
   __nv_bfloat16* wv;
+  float tau;
   int gx, gy;          // stencil blocks of this solve: gx * gy * gz
 };
 
@@ -616,6 +617,46 @@ __global__ void __launch_bounds__(256) rdiff_pieces_kernel(const PwLaunch L) {
   }
 }
 
+// Lawson2b (Eq. 7) first pointwise stage: x = u + factor tau G(u, v) as
+// BF16 pieces [3][N] (both components).
+__global__ void __launch_bounds__(256) lawson_pre_pieces_kernel(const PwLaunch L, float factor) {
+  const int s = find_segment(L.bstart, L.nsolves, blockIdx.x);
+  const PwDesc& D = L.desc[s];
+  const int64_t N = D.a.N;
+  const float sc = factor * D.tau;
+  const int64_t base = (int64_t)(blockIdx.x - __ldg(L.bstart + s)) * kRdiffPerBlock;
+#pragma unroll
+  for (int k = 0; k < kRdiffPerBlock / 256; ++k) {
+    const int64_t idx = base + k * 256 + threadIdx.x;
+    if (idx >= N) break;
+    const float uu = D.u[idx], vv = D.v[idx];
+    float gu, gv;
+    react<float>(D.a.rx, uu, vv, gu, gv);
+    split3(uu + sc * gu, D.wu[idx], D.wu[N + idx], D.wu[2 * N + idx]);
+    split3(vv + sc * gv, D.wv[idx], D.wv[N + idx], D.wv[2 * N + idx]);
+  }
+}
+
+// Lawson2b last stage: u += factor tau G(u2, v2) in FP32, in place.
+__global__ void __launch_bounds__(256) lawson_post_kernel(const PwLaunch L, float factor) {
+  const int s = find_segment(L.bstart, L.nsolves, blockIdx.x);
+  const PwDesc& D = L.desc[s];
+  const int64_t N = D.a.N;
+  const float sc = factor * D.tau;
+  float* u = const_cast<float*>(D.u);
+  float* v = const_cast<float*>(D.v);
+  const int64_t base = (int64_t)(blockIdx.x - __ldg(L.bstart + s)) * kRdiffPerBlock;
+#pragma unroll
+  for (int k = 0; k < kRdiffPerBlock / 256; ++k) {
+    const int64_t idx = base + k * 256 + threadIdx.x;
+    if (idx >= N) break;
+    float gu, gv;
+    react<float>(D.a.rx, D.u2[idx], D.v2[idx], gu, gv);
+    u[idx] += sc * gu;
+    v[idx] += sc * gv;
+  }
+}
+
 // Phi (FP64, row-major n x n) -> three BF16 pieces [3][n][n].
 __global__ void split_matrix_kernel(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
                                     int64_t count) {
@@ -700,12 +741,24 @@ int grid_for(int64_t total) {
 }
 
 // One tensor-core pass of the step sequence.
+enum { kOutPieces = 0, kOutStage = 1, kOutState = 2 };   // outputs: pieces, U2/V2, u/v
+enum { kBaseNone = 0, kBaseState = 1, kBaseStage = 2 };  // FP32 base: none, u/v, U2/V2
+enum { kAlphaOne = 0, kAlphaTau = 1, kAlphaTauD = 2 };   // 1, tau, 2^(d-1) tau
 struct TcPass {
   int b;      // piece buffer read (output pieces go to 1 - b)
   int mu;     // direction
-  int ell;    // 1: phi_1 (stage 1), 2: phi_2 (stage 2)
+  int ell;    // matrix: 0 = e^(tau A), 1 = phi_1, 2 = phi_2
   int mode;   // TcMode
   int pair;
+  int out, base, alpha;
+};
+
+// One launch of the step sequence.
+enum { kOpRhs = 0, kOpTc = 1, kOpRdiff = 2, kOpLawsonPre = 3, kOpLawsonPost = 4 };
+struct TcOp {
+  int kind;
+  int pass;       // kOpTc: index into the passes
+  float factor;   // Lawson stages: multiple of tau
 };
 
 }  // namespace
@@ -715,19 +768,19 @@ struct TcState {
   int d;
   int64_t n[3];
   int64_t N;
-  __nv_bfloat16* phi[2][3][2];   // [c][mu][ell-1] -> [3][n][n]
+  __nv_bfloat16* phi[2][3][3];   // [c][mu][ell] -> [3][n][n]; ell 0 = e^(tau A)
   __nv_bfloat16* buf[2][2];      // [b][c] -> [3][N]
   CUtensorMap amap[2][2][3];     // [b][c][mu]: buffer b viewed as [3][N/n_mu][n_mu]
-  CUtensorMap bmap[2][3][2];     // [c][mu][ell-1]
+  CUtensorMap bmap[2][3][3];     // [c][mu][ell]
   int variant;
   int fuse;      // 1: fuse the stage-1 combination into the last stage-1 product
   int num_sms;
   int* err;
   std::vector<void*> allocs;
-  // step sequence: 2d tensor-core passes, the reaction difference after
-  // pass `rdiff_after` (-1 when fused)
+  // step sequence: tensor-core passes and the launches around them
+  int scheme;
   std::vector<TcPass> passes;
-  int rdiff_after;
+  std::vector<TcOp> ops;
   // descriptors of this plan as a group of one, bound to (bound_u, bound_v)
   TcPassDesc* d_desc;
   int* d_ustart;   // [passes][2]
@@ -760,29 +813,18 @@ static TcPassDesc make_desc(const TcState* S, const adr_plan_s* P, const TcPass&
   D.pair = ps.pair;
   D.mode = ps.mode;
   D.rx = P->pwf.rx;
-  float* U2 = (float*)P->u2;
-  float* V2 = (float*)P->v2;
+  float* stage[2] = {(float*)P->u2, (float*)P->v2};
+  float* state[2] = {u, v};
   const double tau = P->prob.tau;
   for (int c = 0; c < 2; ++c) {
     D.amap[c] = S->amap[ps.b][c][ps.mu];
-    D.bmap[c] = S->bmap[c][ps.mu][ps.ell - 1];
+    D.bmap[c] = S->bmap[c][ps.mu][ps.ell];
     D.outp[c] = S->buf[1 - ps.b][c];
+    D.outf[c] = ps.out == kOutStage ? stage[c] : (ps.out == kOutState ? state[c] : nullptr);
+    D.base[c] = ps.base == kBaseStage ? stage[c] : (ps.base == kBaseState ? state[c] : nullptr);
   }
-  if (ps.mode != kPieces3) {
-    if (ps.ell == 1) {  // U2 = U + tau T
-      D.outf[0] = U2;
-      D.outf[1] = V2;
-      D.base[0] = u;
-      D.base[1] = v;
-      D.alpha = (float)tau;
-    } else {  // U+ = U2 + 2^(d-1) tau S
-      D.outf[0] = u;
-      D.outf[1] = v;
-      D.base[0] = U2;
-      D.base[1] = V2;
-      D.alpha = (float)ldexp(tau, S->d - 1);
-    }
-  }
+  D.alpha = ps.alpha == kAlphaTau ? (float)tau
+                                  : (ps.alpha == kAlphaTauD ? (float)ldexp(tau, S->d - 1) : 1.0f);
   return D;
 }
 
@@ -796,6 +838,7 @@ static PwDesc make_pw(const TcState* S, const adr_plan_s* P, float* u, float* v)
   W.v2 = (const float*)P->v2;
   W.wu = S->buf[0][0];
   W.wv = S->buf[0][1];
+  W.tau = (float)P->prob.tau;
   W.gx = (int)((S->n[0] + 127) / 128);
   W.gy = (int)S->n[1];
   return W;
@@ -819,7 +862,7 @@ void tc_free(TcOperands* t) {
   t->work[0] = nullptr;
 }
 
-cudaError_t tc_prepare(TcOperands* t, int prec, int d, const int64_t n[3],
+cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t n[3],
                        double* const master[2][3][4], cudaStream_t s) {
   if (prec != ADR_BF16X3) return cudaErrorNotSupported;
   for (int m = 0; m < d; ++m)
@@ -865,11 +908,12 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int d, const int64_t n[3],
   if (e != cudaSuccess) return e;
   for (int c = 0; c < 2; ++c)
     for (int m = 0; m < d; ++m)
-      for (int l = 0; l < 2; ++l) {
+      for (int l = 0; l < 3; ++l) {
+        if ((scheme == ADR_LAWSON2B) != (l == 0)) continue;  // only the matrices the scheme uses
         const int64_t nn = n[m] * n[m];
         e = alloc((void**)&S->phi[c][m][l], (size_t)kPieces * nn * 2);
         if (e != cudaSuccess) return e;
-        split_matrix_kernel<<<grid_for(nn), 256, 0, s>>>(master[c][m][2 + l], S->phi[c][m][l], nn);
+        split_matrix_kernel<<<grid_for(nn), 256, 0, s>>>(master[c][m][1 + l], S->phi[c][m][l], nn);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = encode_pieces(&S->bmap[c][m][l], S->phi[c][m][l], n[m], n[m], bn, sw);
@@ -884,26 +928,51 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int d, const int64_t n[3],
         if (e != cudaSuccess) return e;
       }
     }
-  // step sequence (buffers alternate; the reaction difference writes buffer 0)
-  {
+  // step sequence (piece buffers alternate; pointwise stages write buffer 0)
+  S->scheme = scheme;
+  auto add_tucker = [&](int ell, int last_out, int last_base, int last_alpha, int stage1_fuse) {
     int b = 0;
-    S->rdiff_after = -1;
     for (int mu = 0; mu < d; ++mu) {
-      if (mu < d - 1) {
-        S->passes.push_back({b, mu, 1, kPieces3, 0});
-        b ^= 1;
-      } else if (S->fuse) {
-        S->passes.push_back({b, mu, 1, kStage1, 1});
-        b ^= 1;
-      } else {
-        S->passes.push_back({b, mu, 1, kAxpy, 0});
-        S->rdiff_after = (int)S->passes.size() - 1;
-        b = 0;
+      TcPass ps{b, mu, ell, kPieces3, 0, kOutPieces, kBaseNone, kAlphaOne};
+      if (mu == d - 1) {
+        ps.mode = stage1_fuse ? kStage1 : kAxpy;
+        ps.pair = stage1_fuse;
+        ps.out = last_out;
+        ps.base = last_base;
+        ps.alpha = last_alpha;
       }
-    }
-    for (int mu = 0; mu < d; ++mu) {
-      S->passes.push_back({b, mu, 2, mu < d - 1 ? kPieces3 : kAxpy, 0});
+      S->passes.push_back(ps);
+      S->ops.push_back({kOpTc, (int)S->passes.size() - 1, 0.f});
       b ^= 1;
+    }
+    return b;
+  };
+  if (scheme == ADR_LAWSON2B) {
+    // U2 = (U + tau G) x e^(tau A);  U+ = (U + tau/2 G) x e^(tau A) + tau/2 G(U2, V2)
+    S->ops.push_back({kOpLawsonPre, -1, 1.0f});
+    add_tucker(0, kOutStage, kBaseNone, kAlphaOne, 0);
+    S->ops.push_back({kOpLawsonPre, -1, 0.5f});
+    add_tucker(0, kOutState, kBaseNone, kAlphaOne, 0);
+    S->ops.push_back({kOpLawsonPost, -1, 0.5f});
+  } else {
+    // ETD2RKds: stencil, phi_1 Tucker to U2 (+ reaction difference), phi_2
+    // Tucker back to the state
+    S->ops.push_back({kOpRhs, -1, 0.f});
+    const int b1 = add_tucker(1, kOutStage, kBaseState, kAlphaTau, S->fuse);
+    if (!S->fuse) S->ops.push_back({kOpRdiff, -1, 0.f});
+    // stage 2 reads the reaction difference from buffer 0 (separate kernel)
+    // or from the buffer the fused epilogue wrote
+    const int b2 = S->fuse ? b1 : 0;
+    for (int mu = 0, b = b2; mu < d; ++mu, b ^= 1) {
+      TcPass ps{b, mu, 2, kPieces3, 0, kOutPieces, kBaseNone, kAlphaOne};
+      if (mu == d - 1) {
+        ps.mode = kAxpy;
+        ps.out = kOutState;
+        ps.base = kBaseStage;
+        ps.alpha = kAlphaTauD;
+      }
+      S->passes.push_back(ps);
+      S->ops.push_back({kOpTc, (int)S->passes.size() - 1, 0.f});
     }
   }
   const int np = (int)S->passes.size();
@@ -956,44 +1025,68 @@ cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   return cudaSuccess;
 }
 
-// Launch the kernels of one ETD2RKds step for a group of solves.
+// Launch the kernels of one step for a group of solves (one solve or a
+// batch), following the plan's operation list.
 struct GroupStep {
   int d, variant, num_sms, nsolves;
-  int np, rdiff_after;
+  int np, nops;
+  TcOp ops[16];
   const TcPassDesc* desc;   // [np][nsolves]
   const int* ustart;        // [np][nsolves + 1]
-  int units[8];
-  PwLaunch rhs, rdiff;
-  int rhs_blocks, rdiff_blocks;
+  int units[16];
+  PwLaunch rhs, flat;       // stencil blocks; flat pointwise blocks
+  int rhs_blocks, flat_blocks;
   int* err;
-  double flops[8], bytes[8];  // algorithmic work per pass (timing statistics)
-  double pw_n;                // total points (pointwise statistics)
+  double flops[16], bytes[16];  // algorithmic work per pass (timing statistics)
+  double pw_n;                  // total points (pointwise statistics)
 };
 
 static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
   const double N = G.pw_n;
-  cudaError_t e = timed_kernel(ctl, KC_RHS, N * 2.0 * (6.0 * G.d + 10.0), N * (8.0 + 12.0), [&] {
-    rhs_pieces_kernel<<<G.rhs_blocks, 128, 0, ctl->stream>>>(G.rhs);
-    return cudaGetLastError();
-  });
-  if (e != cudaSuccess) return e;
-  for (int p = 0; p < G.np; ++p) {
-    TcLaunch L;
-    L.desc = G.desc + (size_t)p * G.nsolves;
-    L.ustart = G.ustart + (size_t)p * (G.nsolves + 1);
-    L.nsolves = G.nsolves;
-    L.nunits = G.units[p];
-    L.err = G.err;
-    e = timed_kernel(ctl, KC_MODE_TC, G.flops[p], G.bytes[p],
-                     [&] { return launch_tc(G.variant, G.num_sms, ctl->stream, L); });
-    if (e != cudaSuccess) return e;
-    if (p == G.rdiff_after) {
-      e = timed_kernel(ctl, KC_RDIFF, N * 2.0 * 12.0, N * (16.0 + 12.0), [&] {
-        rdiff_pieces_kernel<<<G.rdiff_blocks, 256, 0, ctl->stream>>>(G.rdiff);
-        return cudaGetLastError();
-      });
-      if (e != cudaSuccess) return e;
+  cudaStream_t st = ctl->stream;
+  for (int o = 0; o < G.nops; ++o) {
+    const TcOp& op = G.ops[o];
+    cudaError_t e = cudaSuccess;
+    switch (op.kind) {
+      case kOpRhs:
+        e = timed_kernel(ctl, KC_RHS, N * 2.0 * (6.0 * G.d + 10.0), N * (8.0 + 12.0), [&] {
+          rhs_pieces_kernel<<<G.rhs_blocks, 128, 0, st>>>(G.rhs);
+          return cudaGetLastError();
+        });
+        break;
+      case kOpRdiff:
+        e = timed_kernel(ctl, KC_RDIFF, N * 2.0 * 12.0, N * (16.0 + 12.0), [&] {
+          rdiff_pieces_kernel<<<G.flat_blocks, 256, 0, st>>>(G.flat);
+          return cudaGetLastError();
+        });
+        break;
+      case kOpLawsonPre:
+        e = timed_kernel(ctl, KC_LAWSON_PW, N * 2.0 * 12.0, N * (8.0 + 12.0), [&] {
+          lawson_pre_pieces_kernel<<<G.flat_blocks, 256, 0, st>>>(G.flat, op.factor);
+          return cudaGetLastError();
+        });
+        break;
+      case kOpLawsonPost:
+        e = timed_kernel(ctl, KC_LAWSON_PW, N * 2.0 * 12.0, N * 16.0, [&] {
+          lawson_post_kernel<<<G.flat_blocks, 256, 0, st>>>(G.flat, op.factor);
+          return cudaGetLastError();
+        });
+        break;
+      case kOpTc: {
+        const int p = op.pass;
+        TcLaunch L;
+        L.desc = G.desc + (size_t)p * G.nsolves;
+        L.ustart = G.ustart + (size_t)p * (G.nsolves + 1);
+        L.nsolves = G.nsolves;
+        L.nunits = G.units[p];
+        L.err = G.err;
+        e = timed_kernel(ctl, KC_MODE_TC, G.flops[p], G.bytes[p],
+                         [&] { return launch_tc(G.variant, G.num_sms, st, L); });
+      } break;
+      default:
+        e = cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -1007,6 +1100,12 @@ static void pass_work(const TcState* S, const TcPass& ps, double& flops, double&
   if (ps.mode == kStage1) bytes += 2.0 * (8.0 + 6.0) * N;
 }
 
+static void fill_ops(GroupStep& G, const TcState* S) {
+  G.np = (int)S->passes.size();
+  G.nops = (int)S->ops.size();
+  for (int o = 0; o < G.nops; ++o) G.ops[o] = S->ops[o];
+}
+
 cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   TcState* S = (TcState*)t->work[0];
   if (!S || !t->ready || S->bound_u != u || S->bound_v != v) return cudaErrorNotSupported;
@@ -1016,8 +1115,7 @@ cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   G.variant = S->variant;
   G.num_sms = S->num_sms;
   G.nsolves = 1;
-  G.np = (int)S->passes.size();
-  G.rdiff_after = S->rdiff_after;
+  fill_ops(G, S);
   G.desc = S->d_desc;
   G.ustart = S->d_ustart;
   for (int p = 0; p < G.np; ++p) {
@@ -1025,9 +1123,9 @@ cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
     pass_work(S, S->passes[p], G.flops[p], G.bytes[p]);
   }
   G.rhs = PwLaunch{S->d_pw, S->d_bstart, 1};
-  G.rdiff = PwLaunch{S->d_pw, S->d_bstart + 2, 1};
+  G.flat = PwLaunch{S->d_pw, S->d_bstart + 2, 1};
   G.rhs_blocks = S->rhs_blocks;
-  G.rdiff_blocks = S->rdiff_blocks;
+  G.flat_blocks = S->rdiff_blocks;
   G.err = S->err;
   G.pw_n = (double)S->N;
   return group_step(P, G);
@@ -1056,7 +1154,8 @@ struct adr_batch_s {
   adr_plan_s* ctl;   // stream, launch counters and timing events of the batch
   int grouped;
   // grouped descriptors
-  int np, rdiff_after, variant, num_sms, d, nsolves;
+  int np, variant, num_sms, d, nsolves;
+  const TcState* proto;   // plan whose operation list every solve shares
   TcPassDesc* d_desc;   // [np][nsolves]
   int* d_ustart;        // [np][nsolves + 1]
   PwDesc* d_pw;         // [nsolves]
@@ -1113,10 +1212,12 @@ extern "C" adr_status adr_batch_create(const adr_plan* plans, int count, void* s
   for (int i = 0; i < count && grouped; ++i) {
     const TcState* S = (const TcState*)plans[i]->tc.work[0];
     grouped = plans[i]->prec == ADR_BF16X3 && S && S0 && S->d == S0->d &&
-              S->variant == S0->variant && S->passes.size() == S0->passes.size() &&
-              S->rdiff_after == S0->rdiff_after;
+              S->variant == S0->variant && S->scheme == S0->scheme &&
+              S->passes.size() == S0->passes.size() && S->ops.size() == S0->ops.size();
     for (size_t p = 0; grouped && p < S->passes.size(); ++p)
-      grouped = S->passes[p].mode == S0->passes[p].mode && S->passes[p].pair == S0->passes[p].pair;
+      grouped = memcmp(&S->passes[p], &S0->passes[p], sizeof(TcPass)) == 0;
+    for (size_t o = 0; grouped && o < S->ops.size(); ++o)
+      grouped = memcmp(&S->ops[o], &S0->ops[o], sizeof(TcOp)) == 0;
   }
   B->grouped = grouped ? 1 : 0;
   cudaError_t e = cudaSuccess;
@@ -1128,7 +1229,7 @@ extern "C" adr_status adr_batch_create(const adr_plan* plans, int count, void* s
   if (B->grouped) {
     const int S_ = count;
     B->np = (int)S0->passes.size();
-    B->rdiff_after = S0->rdiff_after;
+    B->proto = S0;
     B->variant = S0->variant;
     B->num_sms = S0->num_sms;
     B->d = S0->d;
@@ -1225,8 +1326,7 @@ static cudaError_t batch_step_direct(adr_batch B, int64_t nsteps) {
   G.variant = B->variant;
   G.num_sms = B->num_sms;
   G.nsolves = B->nsolves;
-  G.np = B->np;
-  G.rdiff_after = B->rdiff_after;
+  fill_ops(G, B->proto);
   G.desc = B->d_desc;
   G.ustart = B->d_ustart;
   for (int p = 0; p < B->np; ++p) {
@@ -1235,9 +1335,9 @@ static cudaError_t batch_step_direct(adr_batch B, int64_t nsteps) {
     G.bytes[p] = B->bytes[p];
   }
   G.rhs = PwLaunch{B->d_pw, B->d_bstart, B->nsolves};
-  G.rdiff = PwLaunch{B->d_pw, B->d_bstart + (B->nsolves + 1), B->nsolves};
+  G.flat = PwLaunch{B->d_pw, B->d_bstart + (B->nsolves + 1), B->nsolves};
   G.rhs_blocks = B->rhs_blocks;
-  G.rdiff_blocks = B->rdiff_blocks;
+  G.flat_blocks = B->rdiff_blocks;
   G.err = B->d_err;
   G.pw_n = B->pw_n;
   for (int64_t s = 0; s < nsteps; ++s) {

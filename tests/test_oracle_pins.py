@@ -271,8 +271,29 @@ def test_one_step_splitting_error_is_third_order():
     assert 2.8 < s1 < 3.2 and 2.8 < s2 < 3.2
 
 
+def test_dib_derived_parameter_gives_the_equilibrium():
+    """Sec. 4.4: a4v is chosen so that (0, a4u) is an equilibrium of Eq. 15."""
+    prm = wl.dib_parameters()
+    gu, gv = models.reaction(models.DIB, prm, np.array([0.0]), np.array([prm[4]]))
+    assert abs(gu[0]) < 1e-13 and abs(gv[0]) < 1e-12
+    # and the other terms do not vanish there on their own
+    assert abs(prm[5] * (1 - prm[4]) * (1 - prm[7] * (1 - prm[4]))) > 1.0
+
+
+def test_fhn_rho_is_the_fhn_family():
+    """Eq. 13 with rho = 1 is the FHN variant with eps = a1, a1' = a2, a0 = 0."""
+    rng = np.random.default_rng(8)
+    U, V = rng.standard_normal(50), rng.standard_normal(50)
+    a = models.reaction(models.FHN_RHO, (1.0, 11.0, 0.1), U, V)
+    b = models.reaction(models.FHN, (11.0, 0.1, 0.0), U, V)
+    assert np.allclose(a[0], b[0], rtol=1e-15) and np.allclose(a[1], b[1], rtol=1e-15)
+    c = models.reaction(models.FHN_RHO, (65.731, 11.0, 0.1), U, V)
+    assert np.allclose(c[0], 65.731 * a[0], rtol=1e-14)
+
+
 @pytest.mark.parametrize("model,params", [(0, (1000.0, 0.1, 0.9)), (1, (0.05, 2.0, -0.03)),
-                                          (2, (1.0, 3.0))])
+                                          (2, (1.0, 3.0)), (4, (65.731, 11.0, 0.1)),
+                                          (5, wl.dib_parameters())])
 def test_equilibria_preserved(model, params):
     """Spatially constant steady states stay put over 100 steps."""
     p = wl.Problem(d=2, n=(16, 12), lo=(0.0, 0.0), hi=(1.0, 1.0), diff=(1.0, 10.0),

@@ -27,8 +27,14 @@ SCHNAKENBERG = 0
 FHN = 1
 BRUSSELATOR = 2
 NO_REACTION = 3
+FHN_RHO = 4
+DIB = 5
 MODEL_NAMES = {SCHNAKENBERG: "schnakenberg", FHN: "fhn", BRUSSELATOR: "brusselator",
-               NO_REACTION: "none"}
+               NO_REACTION: "none", FHN_RHO: "fhn_rho", DIB: "dib"}
+
+# Scheme identifiers (mirrors the C ABI enum adr_scheme).
+ETD2RKDS = 0
+LAWSON2B = 1
 
 # Precision identifiers (mirrors the C ABI enum adr_precision).
 FP64 = 0
@@ -63,6 +69,7 @@ class Problem:
     precision: int = FP32
     seed: int = 0
     name: str = ""
+    scheme: int = 0   # 0 = ETD2RKds (Eq. 11), 1 = Lawson2b (Eq. 7)
 
     @property
     def shape(self) -> Tuple[int, ...]:
@@ -128,6 +135,10 @@ def equilibrium(model: int, params: Sequence[float]) -> Tuple[float, float]:
         return a, b / a
     if model == NO_REACTION:
         return 1.0, 1.0
+    if model == FHN_RHO:
+        return 0.0, 0.0
+    if model == DIB:
+        return 0.0, params[4]
     if model == FHN:
         # u - u^3 - v = 0 and u - a1 v - a0 = 0  ->  u(1 - 1/a1) - u^3 + a0/a1 = 0;
         # take the root of smallest magnitude by Newton from u = 0.
@@ -146,6 +157,8 @@ def initial_data(p: Problem, kind: str = "auto", amp: float | None = None):
     """Seeded initial data (u0, v0) as float64 arrays of shape p.shape.
 
     kind "uniform": equilibrium + amp * U[-1, 1] (amp defaults to 0.01);
+    kind "uniform01": equilibrium + amp * U[0, 1] (amp defaults to 1e-5; the
+    paper's perturbation of its Sec. 4.1, 4.2 and 4.4 examples);
     kind "normal": amp * N(0, 1) about 0 (amp defaults to 0.05);
     kind "auto": normal for FHN, uniform otherwise.
     The u field takes stream outputs [0, N), the v field [N, 2N).
@@ -159,6 +172,12 @@ def initial_data(p: Problem, kind: str = "auto", amp: float | None = None):
         r = uniform01(p.seed, 2 * N)
         u = ue + a * (2.0 * r[:N] - 1.0)
         v = ve + a * (2.0 * r[N:] - 1.0)
+    elif kind == "uniform01":
+        a = 1e-5 if amp is None else amp
+        ue, ve = equilibrium(p.model, p.params)
+        r = uniform01(p.seed, 2 * N)
+        u = ue + a * r[:N]
+        v = ve + a * r[N:]
     elif kind == "normal":
         a = 0.05 if amp is None else amp
         z = normal(p.seed, 2 * N)
@@ -217,6 +236,37 @@ def brusselator_256(precision: int = FP32, n: int = 256, nsteps: int = 100) -> P
                    adv=(v, v), model=BRUSSELATOR, params=(1.0, 3.0), tau=1e-2,
                    nsteps=nsteps, precision=precision, seed=3,
                    name=f"brusselator3d_adv_{n}")
+
+
+def dib_parameters():
+    """(rho, a1u, a2u, a3u, a4u, a1v, a2v, a3v, a4v, a5v) of Sec. 4.4, with a4v
+    derived so that (0, a4u) is an equilibrium."""
+    rho, a1u, a2u, a3u, a4u = 25.0 / 4.0, 10.0, 1.0, 66.0, 0.5
+    a1v, a2v, a3v, a5v = 3.0, 2.5, 0.2, 1.5
+    a4v = a1v * (1.0 - a4u) * (1.0 - a3v + a3v * a4u) / (a4u * (1.0 + a3v * a4u))
+    return (rho, a1u, a2u, a3u, a4u, a1v, a2v, a3v, a4v, a5v)
+
+
+def dib_200(precision: int = FP32, n: int = 200, nsteps: int = 1250) -> Problem:
+    """2D DIB model of Sec. 4.4 on [0,20]^2, n x n (200), D = (1, 20),
+    T = 2.5 in `nsteps` steps; data (0, a4u) + 1e-5 U(0,1)."""
+    return Problem(d=2, n=(n, n), lo=(0.0, 0.0), hi=(20.0, 20.0), diff=(1.0, 20.0),
+                   adv=((0.0, 0.0), (0.0, 0.0)), model=DIB, params=dib_parameters(),
+                   tau=2.5 / nsteps, nsteps=nsteps, precision=precision, seed=123,
+                   name=f"dib2d_{n}")
+
+
+def fhn_rho(d: int = 2, precision: int = FP32, n: int | None = None,
+            nsteps: int = 20000) -> Problem:
+    """FitzHugh-Nagumo of Sec. 4.2 (2D, n = 100, rho = 65.731) and Sec. 4.3
+    (3D, n = 64, rho = 24.649) on [0, pi]^d, D = (1, 42.1887), a1 = 11,
+    a2 = 0.1, T = 10; data 1e-3 U(0,1) about (0, 0)."""
+    n = n or (100 if d == 2 else 64)
+    rho = 65.731 if d == 2 else 24.649
+    return Problem(d=d, n=(n,) * d, lo=(0.0,) * d, hi=(math.pi,) * d, diff=(1.0, 42.1887),
+                   adv=((0.0,) * d, (0.0,) * d), model=FHN_RHO, params=(rho, 11.0, 0.1),
+                   tau=10.0 / nsteps, nsteps=nsteps, precision=precision, seed=0,
+                   name=f"fhn_rho{d}d_{n}")
 
 
 BATCH_SIDES = (64, 96, 128, 192, 256, 384, 512)
