@@ -146,7 +146,8 @@ adr_status adr_plan_destroy(adr_plan plan);
  *   U2 = U + tau (sum_mu U x_mu A_mu^u + G^u(U,V)) x_mu phi_1(tau A_mu^u)
  *   U+ = U2 + 2^(d-1) tau (G^u(U2,V2) - G^u(U,V)) x_mu phi_2(tau A_mu^u)
  * and likewise for V.  u, v: device pointers to state tensors (layout
- * above), distinct, not aliasing plan memory.  nsteps >= 0.  Asynchronous. */
+ * above), distinct, not aliasing plan memory; for ADR_BF16X3 plans both
+ * 16-byte aligned (ADR_EINVAL otherwise).  nsteps >= 0.  Asynchronous. */
 adr_status adr_step(adr_plan plan, void* u, void* v, int64_t nsteps);
 
 /* Solve from (u0, v0) for nsteps steps into (uT, vT).  Each pointer may be

@@ -432,6 +432,8 @@ static adr_status step_impl(adr_plan P, void* u, void* v, int64_t nsteps) {
   int64_t done = 0;
   if (nsteps == 0) return ADR_OK;
   if (P->prec == ADR_TF32X3 || P->prec == ADR_BF16X3) {
+    if ((((uintptr_t)u) | ((uintptr_t)v)) & 15)
+      return fail(ADR_EINVAL, "adr_step: BF16X3 state buffers must be 16-byte aligned");
     cudaError_t e = tc_bind(&P->tc, P, u, v);
     if (e != cudaSuccess)
       return fail(ADR_ECUDA, std::string("adr_step: binding state buffers: ") + cudaGetErrorString(e));

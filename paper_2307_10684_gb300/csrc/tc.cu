@@ -122,13 +122,39 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// The A operand collector: kColFill reads A from shared memory and keeps it,
+// kColUse / kColLast reuse the kept A (the last use releases it), kColNone
+// reads A and keeps nothing.  Consecutive MMAs on the same A tile then read
+// it from shared memory once.
+enum { kColNone = 0, kColFill = 1, kColUse = 2, kColLast = 3 };
+template <int COL>
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+  if constexpr (COL == kColFill) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else if constexpr (COL == kColUse) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else if constexpr (COL == kColLast) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile(
@@ -149,6 +175,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// tmem_ld16 without the wait: the registers are valid only after
+// tmem_wait_ld() and tmem_fence16() on them.
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Orders every later use of r after the preceding tmem_wait_ld().
+__device__ __forceinline__ void tmem_fence16(uint32_t (&r)[16]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
 }
 
 // Shared-memory matrix descriptor of a K-major tile with SW-byte swizzle
@@ -218,9 +268,9 @@ enum TcMode : int {
   kAxpy = 2       // out = base + alpha acc (FP32)
 };
 
-// The six piece pairs (i, j): A piece i times B piece j, smallest first.
-__device__ __constant__ int kPairA[6] = {1, 0, 2, 0, 1, 0};
-__device__ __constant__ int kPairB[6] = {1, 2, 0, 1, 0, 0};
+// The six piece pairs (i, j), A piece i times B piece j, grouped by A piece
+// so that each A piece is read from shared memory once per K step (A
+// collector), smaller A pieces first: (2,0), (1,1), (1,0), (0,2), (0,1), (0,0).
 
 constexpr int kEpiWarps = 8;                  // two warps per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue
@@ -272,7 +322,7 @@ __device__ __forceinline__ Unit decode_unit(const TcLaunch& L, int u) {
 // Epilogue warp w owns TMEM lane quarter w % 4 and half (w - 2) / 4 of the
 // columns; it prefetches its FP32 base values two 16-column chunks ahead,
 // starting before the accumulator is ready.
-template <int SW, int BN>
+template <int SW, int BN, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) {
   using C = TcCfg<SW, BN>;
   static_assert(4 * BN <= 512, "four accumulators must fit in TMEM");
@@ -318,6 +368,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
     for (int u = blockIdx.x; u < L.nunits && !stop; u += gridDim.x) {
       const Unit w = decode_unit<BN>(L, u);
       const int nk = (w.d->K + C::BK - 1) / C::BK;
+      for (int comp = w.c_lo; comp < w.c_hi; ++comp) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&w.d->amap[comp]) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&w.d->bmap[comp]) : "memory");
+      }
       for (int comp = w.c_lo; comp < w.c_hi && !stop; ++comp) {
         const CUtensorMap* ma = &w.d->amap[comp];
         const CUtensorMap* mb = &w.d->bmap[comp];
@@ -375,12 +429,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
           const uint32_t sb = sa + kPieces * C::TILE_A;
 #pragma unroll
           for (int kk = 0; kk < C::KSTEPS; ++kk) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-              const uint64_t ad = kmajor_desc<SW>(sa + kPairA[q] * C::TILE_A + kk * 32);
-              const uint64_t bd = kmajor_desc<SW>(sb + kPairB[q] * C::TILE_B + kk * 32);
-              mma_bf16(dt, ad, bd, idesc, (kb | kk | q) != 0);
-            }
+            const uint64_t a0 = kmajor_desc<SW>(sa + kk * 32);
+            const uint64_t a1 = kmajor_desc<SW>(sa + C::TILE_A + kk * 32);
+            const uint64_t a2 = kmajor_desc<SW>(sa + 2 * C::TILE_A + kk * 32);
+            const uint64_t b0 = kmajor_desc<SW>(sb + kk * 32);
+            const uint64_t b1 = kmajor_desc<SW>(sb + C::TILE_B + kk * 32);
+            const uint64_t b2 = kmajor_desc<SW>(sb + 2 * C::TILE_B + kk * 32);
+            mma_bf16<kColNone>(dt, a2, b0, idesc, (kb | kk) != 0);
+            mma_bf16<kColFill>(dt, a1, b1, idesc, 1);
+            mma_bf16<kColLast>(dt, a1, b0, idesc, 1);
+            mma_bf16<kColFill>(dt, a0, b2, idesc, 1);
+            mma_bf16<kColUse>(dt, a0, b1, idesc, 1);
+            mma_bf16<kColLast>(dt, a0, b0, idesc, 1);
           }
           mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
         }
@@ -413,6 +473,67 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
       const float* bsrc0 = D->base[w.c_lo];
       const float* bsrc1 = nc == 2 ? D->base[w.c_lo + 1] : nullptr;
       auto chunk_cols = [&](int ch) { return min(16, N - (n0 + ch * 16)); };
+      if constexpr (!PAIR) {
+        // One component: load this warp's whole FP32 base strip (HC columns)
+        // before the accumulator is ready, read all its TMEM columns with one
+        // wait, then write.
+        float bv[HC];
+        const float* bsrc = D->base[w.c_lo];
+#pragma unroll
+        for (int j = 0; j < HC; ++j) {
+          const int col = n0 + j;
+          bv[j] = (fp32_in && bsrc && mrow && col < N) ? __ldg(bsrc + (int64_t)col * M + m) : 0.f;
+        }
+        if (!mbar_wait(&acc_full[slot], (i >> 1) & 1)) {
+          if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
+          *abort_v = 1;
+          break;
+        }
+        tc_fence_after();
+        if (*abort_v) break;
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * 2 * BN + half * HC);
+        // TMEM columns in batches of two 16-column chunks, one wait per batch
+#pragma unroll
+        for (int bt = 0; bt < NCH; bt += 2) {
+          constexpr int NB = NCH >= 2 ? 2 : 1;
+          uint32_t r[NB][16];
+#pragma unroll
+          for (int c = 0; c < NB; ++c) tmem_ld16_nw(ta + (uint32_t)((bt + c) * 16), r[c]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int c = 0; c < NB; ++c) tmem_fence16(r[c]);
+          if (mrow) {
+            if (mode == kPieces3) {
+              __nv_bfloat16* op = D->outp[w.c_lo];
+#pragma unroll
+              for (int jj = 0; jj < 16 * NB; ++jj) {
+                const int col = n0 + bt * 16 + jj;
+                if (col < N) {
+                  const int64_t o = (int64_t)col * M + m;
+                  __nv_bfloat16 b0, b1, b2;
+                  split3(__uint_as_float(r[jj / 16][jj % 16]), b0, b1, b2);
+                  op[o] = b0;
+                  op[plane + o] = b1;
+                  op[2 * plane + o] = b2;
+                }
+              }
+            } else {
+              float* of = D->outf[w.c_lo];
+#pragma unroll
+              for (int jj = 0; jj < 16 * NB; ++jj) {
+                const int col = n0 + bt * 16 + jj;
+                if (col < N)
+                  of[(int64_t)col * M + m] = bv[bt * 16 + jj] + alpha * __uint_as_float(r[jj / 16][jj % 16]);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[slot]))
+                       : "memory");
+      } else {
       // base prefetch, two chunks deep: pb[buffer][component slot][column]
       float pb[2][2][16];
       auto prefetch = [&](int ch, int buf) {
@@ -508,6 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
       if (lane == 0)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[slot]))
                      : "memory");
+      }
     }
   }
   tc_fence_before();
@@ -521,6 +643,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
 // ---------------------------------------------------------------- pointwise
 // Per-solve arguments of the pointwise kernels of the tensor-core path; one
 // launch covers one solve or a whole batch.
+//
+// The stencil kernel sees every grid as three axes: x = i1 (contiguous), y
+// (the x2 direction of a 3D grid, absent in 2D) and z, the slowest axis (x3
+// in 3D, x2 in 2D).  A warp owns a run of 128 x-points (four per lane, so
+// loads are float4 and stores of four BF16 values 8 bytes) on one y row and
+// marches `zlen` consecutive z planes, keeping the z neighbours in registers.
 struct PwDesc {
   PointwiseArgsT<float> a;
   const float* u;
@@ -530,7 +658,9 @@ struct PwDesc {
   __nv_bfloat16* wu;   // pieces [3][N] of the u output
   __nv_bfloat16* wv;
   float tau;
-  int gx, gy;          // stencil blocks of this solve: gx * gy * gz
+  int nx, ny, nz;      // stencil axes (ny = 1 in 2D)
+  int xsegs, zlen, zsegs;
+  int64_t sy, sz;      // element strides of y and z
 };
 
 struct PwLaunch {
@@ -539,59 +669,141 @@ struct PwLaunch {
   int nsolves;
 };
 
-constexpr int kZ = 8;             // x3 planes per stencil thread
-constexpr int kRdiffPerBlock = 1024;
+constexpr int kPwThreads = 256;
+constexpr int kPwWarps = kPwThreads / 32;
+constexpr int kSegX = 128;                          // x-points per warp
+constexpr int kFlatVec = 2;                         // float4 per thread per array
+constexpr int kFlatPerBlock = kPwThreads * 4 * kFlatVec;
 
-__device__ __forceinline__ float zdir(float xm, float xc, float xp, int z, int n3,
-                                      const TridiagT<float>& A) {
-  if (z == 0) return A.b0 * (xp - xc);
-  if (z == n3 - 1) return A.bn * (xm - xc);
-  return A.lo * (xm - xc) + A.up * (xp - xc);
+// The block's solve and its descriptor, staged once in shared memory.
+__device__ __forceinline__ int stage_pw(const PwLaunch& L, PwDesc* sd) {
+  const int s = find_segment(L.bstart, L.nsolves, blockIdx.x);
+  static_assert(sizeof(PwDesc) % 4 == 0, "PwDesc is copied in 32-bit words");
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(L.desc + s);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(sd);
+  for (int w = threadIdx.x; w < (int)(sizeof(PwDesc) / 4); w += blockDim.x) dst[w] = __ldg(src + w);
+  __syncthreads();
+  return s;
 }
 
-// W^c = K^c U^c + G^c(U, V) as BF16 pieces [3][N] in the natural layout.
-// One thread per (i1, i2) marches kZ consecutive x3 planes and keeps the x3
-// neighbours in registers (2D grids have a single plane).
-__global__ void __launch_bounds__(128) rhs_pieces_kernel(const PwLaunch L) {
-  const int s = find_segment(L.bstart, L.nsolves, blockIdx.x);
-  const PwDesc& D = L.desc[s];
-  const PointwiseArgsT<float>& a = D.a;
-  int lb = blockIdx.x - __ldg(L.bstart + s);
-  const int bx = lb % D.gx;
-  lb /= D.gx;
-  const int i2 = lb % D.gy;
-  const int z0 = (lb / D.gy) * kZ;
-  const int n1 = (int)a.n[0], n2 = (int)a.n[1], n3 = a.d == 3 ? (int)a.n[2] : 1;
-  const int i1 = bx * blockDim.x + threadIdx.x;
-  if (i1 >= n1) return;
-  const float* __restrict__ u = D.u;
-  const float* __restrict__ v = D.v;
-  __nv_bfloat16* __restrict__ wu = D.wu;
-  __nv_bfloat16* __restrict__ wv = D.wv;
-  const int64_t P = (int64_t)n1 * n2;
-  const int64_t col = (int64_t)i2 * n1 + i1;
-  float uc = u[z0 * P + col], vc = v[z0 * P + col];
-  float um = z0 > 0 ? u[(z0 - 1) * P + col] : 0.f;
-  float vm = z0 > 0 ? v[(z0 - 1) * P + col] : 0.f;
-#pragma unroll 2
-  for (int k = 0; k < kZ; ++k) {
-    const int z = z0 + k;
-    if (z >= n3) break;
-    const int64_t idx = z * P + col;
-    const float up = z + 1 < n3 ? u[idx + P] : 0.f;
-    const float vp = z + 1 < n3 ? v[idx + P] : 0.f;
-    float ku = stencil_dir(u, idx, 1, i1, n1, a.A[0][0]) +
-               stencil_dir(u, idx, (int64_t)n1, i2, n2, a.A[0][1]);
-    float kv = stencil_dir(v, idx, 1, i1, n1, a.A[1][0]) +
-               stencil_dir(v, idx, (int64_t)n1, i2, n2, a.A[1][1]);
-    if (a.d == 3) {
-      ku += zdir(um, uc, up, z, n3, a.A[0][2]);
-      kv += zdir(vm, vc, vp, z, n3, a.A[1][2]);
+__device__ __forceinline__ float tri_dir(float xm, float xc, float xp, int i, int n, float lo,
+                                         float up, float b0, float bn) {
+  if (i == 0) return b0 * (xp - xc);
+  if (i == n - 1) return bn * (xm - xc);
+  return lo * (xm - xc) + up * (xp - xc);
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float el(const float4& q, int j) {
+  return j == 0 ? q.x : (j == 1 ? q.y : (j == 2 ? q.z : q.w));
+}
+
+// Split four values into BF16 pieces and store piece k of all four at
+// out + k * N + idx (idx a multiple of 4: 8-byte stores).
+__device__ __forceinline__ void store_pieces4(__nv_bfloat16* out, int64_t N, int64_t idx,
+                                              const float (&w)[4]) {
+  __nv_bfloat16 p[3][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) split3(w[j], p[0][j], p[1][j], p[2][j]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    uint2 q;
+    q.x = (uint32_t)__bfloat16_as_ushort(p[k][0]) | ((uint32_t)__bfloat16_as_ushort(p[k][1]) << 16);
+    q.y = (uint32_t)__bfloat16_as_ushort(p[k][2]) | ((uint32_t)__bfloat16_as_ushort(p[k][3]) << 16);
+    *reinterpret_cast<uint2*>(out + k * N + idx) = q;
+  }
+}
+
+// The tridiagonal coefficients of one component on one axis.
+struct Coef {
+  float lo, up, b0, bn;
+};
+__device__ __forceinline__ Coef coef(const TridiagT<float>& A) { return Coef{A.lo, A.up, A.b0, A.bn}; }
+
+// W^c = K^c U^c + G^c(U, V) as BF16 pieces [3][N] in the natural layout
+// (Eq. 11, first stage: the stencil of Eq. 6 plus the reaction).
+__global__ void __launch_bounds__(kPwThreads) rhs_pieces_kernel(const PwLaunch L) {
+  __shared__ PwDesc sd;
+  const int s = stage_pw(L, &sd);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
+  int64_t unit = (int64_t)(blockIdx.x - __ldg(L.bstart + s)) * kPwWarps + warp;
+  if (unit >= (int64_t)sd.xsegs * ny * sd.zsegs) return;  // whole warps only
+  const int y = (int)(unit % ny);
+  unit /= ny;
+  const int xs = (int)(unit % sd.xsegs);
+  const int z0 = (int)(unit / sd.xsegs) * sd.zlen;
+  const int z1 = min(z0 + sd.zlen, nz);
+  const int x0 = xs * kSegX + 4 * lane;
+  const bool act = x0 < nx;
+  const bool d3 = sd.a.d == 3;
+  const int64_t sy = sd.sy, sz = sd.sz, N = sd.a.N;
+  const float* __restrict__ u = sd.u;
+  const float* __restrict__ v = sd.v;
+  __nv_bfloat16* wu = sd.wu;
+  __nv_bfloat16* wv = sd.wv;
+  // axis coefficients: x = mu 1, y = mu 2 (3D), z = mu 3 (3D) or mu 2 (2D)
+  const Coef cxu = coef(sd.a.A[0][0]), cxv = coef(sd.a.A[1][0]);
+  const Coef cyu = coef(sd.a.A[0][1]), cyv = coef(sd.a.A[1][1]);
+  const Coef czu = coef(sd.a.A[0][d3 ? 2 : 1]), czv = coef(sd.a.A[1][d3 ? 2 : 1]);
+  const ReactionT<float> rx = sd.a.rx;
+  const int64_t col = (int64_t)y * sy + x0;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 uc = act ? ld4(u + z0 * sz + col) : zero4;
+  float4 vc = act ? ld4(v + z0 * sz + col) : zero4;
+  float4 um = (act && z0 > 0) ? ld4(u + (z0 - 1) * sz + col) : zero4;
+  float4 vm = (act && z0 > 0) ? ld4(v + (z0 - 1) * sz + col) : zero4;
+  for (int z = z0; z < z1; ++z) {  // trip count uniform over the warp
+    const int64_t idx = z * sz + col;
+    const bool zp = act && z + 1 < nz;
+    const float4 up = zp ? ld4(u + idx + sz) : zero4;
+    const float4 vp = zp ? ld4(v + idx + sz) : zero4;
+    float4 uym = zero4, uyp = zero4, vym = zero4, vyp = zero4;
+    if (d3 && act) {
+      if (y > 0) {
+        uym = ld4(u + idx - sy);
+        vym = ld4(v + idx - sy);
+      }
+      if (y + 1 < ny) {
+        uyp = ld4(u + idx + sy);
+        vyp = ld4(v + idx + sy);
+      }
     }
-    float gu, gv;
-    react<float>(a.rx, uc, vc, gu, gv);
-    split3(ku + gu, wu[idx], wu[a.N + idx], wu[2 * a.N + idx]);
-    split3(kv + gv, wv[idx], wv[a.N + idx], wv[2 * a.N + idx]);
+    // x neighbours across lanes; the ends of the warp's run load their own
+    float ul = __shfl_up_sync(0xffffffffu, uc.w, 1), vl = __shfl_up_sync(0xffffffffu, vc.w, 1);
+    float ur = __shfl_down_sync(0xffffffffu, uc.x, 1), vr = __shfl_down_sync(0xffffffffu, vc.x, 1);
+    if (lane == 0) {
+      ul = (act && x0 > 0) ? u[idx - 1] : 0.f;
+      vl = (act && x0 > 0) ? v[idx - 1] : 0.f;
+    }
+    if (lane == 31) {
+      ur = (act && x0 + 4 < nx) ? u[idx + 4] : 0.f;
+      vr = (act && x0 + 4 < nx) ? v[idx + 4] : 0.f;
+    }
+    float ou[4], ov[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int xi = x0 + j;
+      const float cu = el(uc, j), cv = el(vc, j);
+      const float lu = j == 0 ? ul : el(uc, j - 1), lv = j == 0 ? vl : el(vc, j - 1);
+      const float ru = j == 3 ? ur : el(uc, j + 1), rv = j == 3 ? vr : el(vc, j + 1);
+      float ku = tri_dir(lu, cu, ru, xi, nx, cxu.lo, cxu.up, cxu.b0, cxu.bn);
+      float kv = tri_dir(lv, cv, rv, xi, nx, cxv.lo, cxv.up, cxv.b0, cxv.bn);
+      if (d3) {
+        ku += tri_dir(el(uym, j), cu, el(uyp, j), y, ny, cyu.lo, cyu.up, cyu.b0, cyu.bn);
+        kv += tri_dir(el(vym, j), cv, el(vyp, j), y, ny, cyv.lo, cyv.up, cyv.b0, cyv.bn);
+      }
+      ku += tri_dir(el(um, j), cu, el(up, j), z, nz, czu.lo, czu.up, czu.b0, czu.bn);
+      kv += tri_dir(el(vm, j), cv, el(vp, j), z, nz, czv.lo, czv.up, czv.b0, czv.bn);
+      float gu, gv;
+      react<float>(rx, cu, cv, gu, gv);
+      ou[j] = ku + gu;
+      ov[j] = kv + gv;
+    }
+    if (act) {
+      store_pieces4(wu, N, idx, ou);
+      store_pieces4(wv, N, idx, ov);
+    }
     um = uc;
     uc = up;
     vm = vc;
@@ -599,63 +811,117 @@ __global__ void __launch_bounds__(128) rhs_pieces_kernel(const PwLaunch L) {
   }
 }
 
-// D^c = G^c(U2, V2) - G^c(U, V) written as BF16 pieces [3][N].
-__global__ void __launch_bounds__(256) rdiff_pieces_kernel(const PwLaunch L) {
-  const int s = find_segment(L.bstart, L.nsolves, blockIdx.x);
-  const PwDesc& D = L.desc[s];
-  const int64_t N = D.a.N;
-  const int64_t base = (int64_t)(blockIdx.x - __ldg(L.bstart + s)) * kRdiffPerBlock;
+// Elementwise kernels: thread t of a block handles float4 groups
+// base + k * kPwThreads + t, k < kFlatVec; loads are issued before any store.
+#define FLAT_PROLOGUE                                                            \
+  __shared__ PwDesc sd;                                                          \
+  const int s = stage_pw(L, &sd);                                                \
+  const int64_t N = sd.a.N, N4 = N / 4;                                          \
+  const int64_t g0 = (int64_t)(blockIdx.x - __ldg(L.bstart + s)) * (kFlatPerBlock / 4) + threadIdx.x;
+
+// D^c = G^c(U2, V2) - G^c(U, V) written as BF16 pieces [3][N] (Eq. 11,
+// second stage).
+__global__ void __launch_bounds__(kPwThreads) rdiff_pieces_kernel(const PwLaunch L) {
+  FLAT_PROLOGUE
+  const ReactionT<float> rx = sd.a.rx;
+  float4 a0[kFlatVec], a1[kFlatVec], a2[kFlatVec], a3[kFlatVec];
 #pragma unroll
-  for (int k = 0; k < kRdiffPerBlock / 256; ++k) {
-    const int64_t idx = base + k * 256 + threadIdx.x;
-    if (idx >= N) break;
-    float g0u, g0v, g2u, g2v;
-    react<float>(D.a.rx, D.u[idx], D.v[idx], g0u, g0v);
-    react<float>(D.a.rx, D.u2[idx], D.v2[idx], g2u, g2v);
-    split3(g2u - g0u, D.wu[idx], D.wu[N + idx], D.wu[2 * N + idx]);
-    split3(g2v - g0v, D.wv[idx], D.wv[N + idx], D.wv[2 * N + idx]);
+  for (int k = 0; k < kFlatVec; ++k) {
+    const int64_t g = g0 + k * kPwThreads;
+    if (g < N4) {
+      a0[k] = ld4(sd.u + 4 * g);
+      a1[k] = ld4(sd.v + 4 * g);
+      a2[k] = ld4(sd.u2 + 4 * g);
+      a3[k] = ld4(sd.v2 + 4 * g);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kFlatVec; ++k) {
+    const int64_t g = g0 + k * kPwThreads;
+    if (g >= N4) break;
+    float du[4], dv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float g0u, g0v, g2u, g2v;
+      react<float>(rx, el(a0[k], j), el(a1[k], j), g0u, g0v);
+      react<float>(rx, el(a2[k], j), el(a3[k], j), g2u, g2v);
+      du[j] = g2u - g0u;
+      dv[j] = g2v - g0v;
+    }
+    store_pieces4(sd.wu, N, 4 * g, du);
+    store_pieces4(sd.wv, N, 4 * g, dv);
   }
 }
 
-// Lawson2b (Eq. 7) first pointwise stage: x = u + factor tau G(u, v) as
-// BF16 pieces [3][N] (both components).
-__global__ void __launch_bounds__(256) lawson_pre_pieces_kernel(const PwLaunch L, float factor) {
-  const int s = find_segment(L.bstart, L.nsolves, blockIdx.x);
-  const PwDesc& D = L.desc[s];
-  const int64_t N = D.a.N;
-  const float sc = factor * D.tau;
-  const int64_t base = (int64_t)(blockIdx.x - __ldg(L.bstart + s)) * kRdiffPerBlock;
+// Lawson2b (Eq. 7) first pointwise stage, also used for the second:
+// W^c = U^c + factor tau G^c(U, V) as BF16 pieces [3][N].
+__global__ void __launch_bounds__(kPwThreads) lawson_pre_pieces_kernel(const PwLaunch L,
+                                                                       float factor) {
+  FLAT_PROLOGUE
+  const ReactionT<float> rx = sd.a.rx;
+  const float sc = factor * sd.tau;
+  float4 a0[kFlatVec], a1[kFlatVec];
 #pragma unroll
-  for (int k = 0; k < kRdiffPerBlock / 256; ++k) {
-    const int64_t idx = base + k * 256 + threadIdx.x;
-    if (idx >= N) break;
-    const float uu = D.u[idx], vv = D.v[idx];
-    float gu, gv;
-    react<float>(D.a.rx, uu, vv, gu, gv);
-    split3(uu + sc * gu, D.wu[idx], D.wu[N + idx], D.wu[2 * N + idx]);
-    split3(vv + sc * gv, D.wv[idx], D.wv[N + idx], D.wv[2 * N + idx]);
+  for (int k = 0; k < kFlatVec; ++k) {
+    const int64_t g = g0 + k * kPwThreads;
+    if (g < N4) {
+      a0[k] = ld4(sd.u + 4 * g);
+      a1[k] = ld4(sd.v + 4 * g);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kFlatVec; ++k) {
+    const int64_t g = g0 + k * kPwThreads;
+    if (g >= N4) break;
+    float wu[4], wv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float uu = el(a0[k], j), vv = el(a1[k], j);
+      float gu, gv;
+      react<float>(rx, uu, vv, gu, gv);
+      wu[j] = uu + sc * gu;
+      wv[j] = vv + sc * gv;
+    }
+    store_pieces4(sd.wu, N, 4 * g, wu);
+    store_pieces4(sd.wv, N, 4 * g, wv);
   }
 }
 
 // Lawson2b last stage: u += factor tau G(u2, v2) in FP32, in place.
-__global__ void __launch_bounds__(256) lawson_post_kernel(const PwLaunch L, float factor) {
-  const int s = find_segment(L.bstart, L.nsolves, blockIdx.x);
-  const PwDesc& D = L.desc[s];
-  const int64_t N = D.a.N;
-  const float sc = factor * D.tau;
-  float* u = const_cast<float*>(D.u);
-  float* v = const_cast<float*>(D.v);
-  const int64_t base = (int64_t)(blockIdx.x - __ldg(L.bstart + s)) * kRdiffPerBlock;
+__global__ void __launch_bounds__(kPwThreads) lawson_post_kernel(const PwLaunch L, float factor) {
+  FLAT_PROLOGUE
+  const ReactionT<float> rx = sd.a.rx;
+  const float sc = factor * sd.tau;
+  float* u = const_cast<float*>(sd.u);
+  float* v = const_cast<float*>(sd.v);
+  float4 a0[kFlatVec], a1[kFlatVec], a2[kFlatVec], a3[kFlatVec];
 #pragma unroll
-  for (int k = 0; k < kRdiffPerBlock / 256; ++k) {
-    const int64_t idx = base + k * 256 + threadIdx.x;
-    if (idx >= N) break;
-    float gu, gv;
-    react<float>(D.a.rx, D.u2[idx], D.v2[idx], gu, gv);
-    u[idx] += sc * gu;
-    v[idx] += sc * gv;
+  for (int k = 0; k < kFlatVec; ++k) {
+    const int64_t g = g0 + k * kPwThreads;
+    if (g < N4) {
+      a0[k] = ld4(sd.u2 + 4 * g);
+      a1[k] = ld4(sd.v2 + 4 * g);
+      a2[k] = ld4(u + 4 * g);
+      a3[k] = ld4(v + 4 * g);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kFlatVec; ++k) {
+    const int64_t g = g0 + k * kPwThreads;
+    if (g >= N4) break;
+    float ou[4], ov[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float gu, gv;
+      react<float>(rx, el(a0[k], j), el(a1[k], j), gu, gv);
+      ou[j] = el(a2[k], j) + sc * gu;
+      ov[j] = el(a3[k], j) + sc * gv;
+    }
+    *reinterpret_cast<float4*>(u + 4 * g) = make_float4(ou[0], ou[1], ou[2], ou[3]);
+    *reinterpret_cast<float4*>(v + 4 * g) = make_float4(ov[0], ov[1], ov[2], ov[3]);
   }
 }
+#undef FLAT_PROLOGUE
 
 // Phi (FP64, row-major n x n) -> three BF16 pieces [3][n][n].
 __global__ void split_matrix_kernel(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst,
@@ -710,27 +976,36 @@ constexpr int kNumVariants = 3;
 
 template <int SW, int BN>
 cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(tc_mode_kernel<SW, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              TcCfg<SW, BN>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(tc_mode_kernel<SW, BN, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<SW, BN>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tc_mode_kernel<SW, BN, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<SW, BN>::SMEM);
 }
 
-cudaError_t launch_tc(int v, int num_sms, cudaStream_t s, const TcLaunch& L) {
-  if (L.nunits <= 0) return cudaSuccess;
-  dim3 grid((unsigned)(L.nunits < num_sms ? L.nunits : num_sms));
+template <bool PAIR>
+cudaError_t launch_tc_t(int v, dim3 grid, cudaStream_t s, const TcLaunch& L) {
   switch (v) {
     case 0:
-      tc_mode_kernel<64, 128><<<grid, kThreads, TcCfg<64, 128>::SMEM, s>>>(L);
+      tc_mode_kernel<64, 128, PAIR><<<grid, kThreads, TcCfg<64, 128>::SMEM, s>>>(L);
       break;
     case 1:
-      tc_mode_kernel<128, 128><<<grid, kThreads, TcCfg<128, 128>::SMEM, s>>>(L);
+      tc_mode_kernel<128, 128, PAIR><<<grid, kThreads, TcCfg<128, 128>::SMEM, s>>>(L);
       break;
     case 2:
-      tc_mode_kernel<64, 64><<<grid, kThreads, TcCfg<64, 64>::SMEM, s>>>(L);
+      tc_mode_kernel<64, 64, PAIR><<<grid, kThreads, TcCfg<64, 64>::SMEM, s>>>(L);
       break;
     default:
       return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+// pair: the launch's units are (u, v) pairs (the fused stage-1 epilogue).
+cudaError_t launch_tc(int v, int num_sms, cudaStream_t s, const TcLaunch& L, bool pair) {
+  if (L.nunits <= 0) return cudaSuccess;
+  dim3 grid((unsigned)(L.nunits < num_sms ? L.nunits : num_sms));
+  return pair ? launch_tc_t<true>(v, grid, s, L) : launch_tc_t<false>(v, grid, s, L);
 }
 
 int grid_for(int64_t total) {
@@ -828,6 +1103,29 @@ static TcPassDesc make_desc(const TcState* S, const adr_plan_s* P, const TcPass&
   return D;
 }
 
+// Stencil geometry of a solve (see PwDesc): z runs are long enough to reuse
+// the z neighbours, short enough to leave several warps per SM.
+struct PwGeom {
+  int nx, ny, nz, xsegs, zlen, zsegs;
+  int64_t sy, sz;
+};
+static PwGeom pw_geom(const TcState* S, int num_sms) {
+  PwGeom g;
+  const bool d3 = S->d == 3;
+  g.nx = (int)S->n[0];
+  g.ny = d3 ? (int)S->n[1] : 1;
+  g.nz = d3 ? (int)S->n[2] : (int)S->n[1];
+  g.sy = S->n[0];
+  g.sz = d3 ? S->n[0] * S->n[1] : S->n[0];
+  g.xsegs = (g.nx + kSegX - 1) / kSegX;
+  const int64_t rows = (int64_t)g.xsegs * g.ny * g.nz;
+  const int64_t want = (int64_t)num_sms * 48;  // warps for about three waves of 16 per SM
+  g.zlen = 1;
+  while (g.zlen < 16 && rows / (2 * g.zlen) >= want) g.zlen *= 2;
+  g.zsegs = (g.nz + g.zlen - 1) / g.zlen;
+  return g;
+}
+
 static PwDesc make_pw(const TcState* S, const adr_plan_s* P, float* u, float* v) {
   PwDesc W;
   memset(&W, 0, sizeof(W));
@@ -839,16 +1137,25 @@ static PwDesc make_pw(const TcState* S, const adr_plan_s* P, float* u, float* v)
   W.wu = S->buf[0][0];
   W.wv = S->buf[0][1];
   W.tau = (float)P->prob.tau;
-  W.gx = (int)((S->n[0] + 127) / 128);
-  W.gy = (int)S->n[1];
+  const PwGeom g = pw_geom(S, S->num_sms);
+  W.nx = g.nx;
+  W.ny = g.ny;
+  W.nz = g.nz;
+  W.xsegs = g.xsegs;
+  W.zlen = g.zlen;
+  W.zsegs = g.zsegs;
+  W.sy = g.sy;
+  W.sz = g.sz;
   return W;
 }
 
 static int rhs_blocks_of(const TcState* S) {
-  return (int)(((S->n[0] + 127) / 128) * S->n[1] * ((S->n[2] + kZ - 1) / kZ));
+  const PwGeom g = pw_geom(S, S->num_sms);
+  const int64_t warps = (int64_t)g.xsegs * g.ny * g.zsegs;
+  return (int)((warps + kPwWarps - 1) / kPwWarps);
 }
 static int rdiff_blocks_of(const TcState* S) {
-  return (int)((S->N + kRdiffPerBlock - 1) / kRdiffPerBlock);
+  return (int)((S->N + kFlatPerBlock - 1) / kFlatPerBlock);
 }
 
 void tc_init(TcOperands* t) { memset(t, 0, sizeof(*t)); }
@@ -1034,6 +1341,7 @@ struct GroupStep {
   const TcPassDesc* desc;   // [np][nsolves]
   const int* ustart;        // [np][nsolves + 1]
   int units[16];
+  int pair[16];             // per pass: units are (u, v) pairs
   PwLaunch rhs, flat;       // stencil blocks; flat pointwise blocks
   int rhs_blocks, flat_blocks;
   int* err;
@@ -1050,25 +1358,25 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
     switch (op.kind) {
       case kOpRhs:
         e = timed_kernel(ctl, KC_RHS, N * 2.0 * (6.0 * G.d + 10.0), N * (8.0 + 12.0), [&] {
-          rhs_pieces_kernel<<<G.rhs_blocks, 128, 0, st>>>(G.rhs);
+          rhs_pieces_kernel<<<G.rhs_blocks, kPwThreads, 0, st>>>(G.rhs);
           return cudaGetLastError();
         });
         break;
       case kOpRdiff:
         e = timed_kernel(ctl, KC_RDIFF, N * 2.0 * 12.0, N * (16.0 + 12.0), [&] {
-          rdiff_pieces_kernel<<<G.flat_blocks, 256, 0, st>>>(G.flat);
+          rdiff_pieces_kernel<<<G.flat_blocks, kPwThreads, 0, st>>>(G.flat);
           return cudaGetLastError();
         });
         break;
       case kOpLawsonPre:
         e = timed_kernel(ctl, KC_LAWSON_PW, N * 2.0 * 12.0, N * (8.0 + 12.0), [&] {
-          lawson_pre_pieces_kernel<<<G.flat_blocks, 256, 0, st>>>(G.flat, op.factor);
+          lawson_pre_pieces_kernel<<<G.flat_blocks, kPwThreads, 0, st>>>(G.flat, op.factor);
           return cudaGetLastError();
         });
         break;
       case kOpLawsonPost:
         e = timed_kernel(ctl, KC_LAWSON_PW, N * 2.0 * 12.0, N * 16.0, [&] {
-          lawson_post_kernel<<<G.flat_blocks, 256, 0, st>>>(G.flat, op.factor);
+          lawson_post_kernel<<<G.flat_blocks, kPwThreads, 0, st>>>(G.flat, op.factor);
           return cudaGetLastError();
         });
         break;
@@ -1081,7 +1389,7 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
         L.nunits = G.units[p];
         L.err = G.err;
         e = timed_kernel(ctl, KC_MODE_TC, G.flops[p], G.bytes[p],
-                         [&] { return launch_tc(G.variant, G.num_sms, st, L); });
+                         [&] { return launch_tc(G.variant, G.num_sms, st, L, G.pair[p] != 0); });
       } break;
       default:
         e = cudaErrorInvalidValue;
@@ -1104,6 +1412,7 @@ static void fill_ops(GroupStep& G, const TcState* S) {
   G.np = (int)S->passes.size();
   G.nops = (int)S->ops.size();
   for (int o = 0; o < G.nops; ++o) G.ops[o] = S->ops[o];
+  for (int p = 0; p < G.np; ++p) G.pair[p] = S->passes[p].pair;
 }
 
 cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
@@ -1358,6 +1667,10 @@ extern "C" adr_status adr_batch_step(adr_batch batch, void* const* u, void* cons
   for (int i = 0; i < B->nsolves; ++i) {
     if (!u[i] || !v[i] || u[i] == v[i]) {
       set_error("adr_batch_step: state pointers must be distinct and non-NULL");
+      return ADR_EINVAL;
+    }
+    if (B->grouped && ((((uintptr_t)u[i]) | ((uintptr_t)v[i])) & 15)) {
+      set_error("adr_batch_step: BF16X3 state buffers must be 16-byte aligned");
       return ADR_EINVAL;
     }
   }
