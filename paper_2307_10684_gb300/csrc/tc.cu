@@ -86,6 +86,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Wait for a phase expected to take a while (an epilogue waiting for its
+// accumulator): polls with a back-off, leaving the issue slots to the
+// producer and MMA warps; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    __nanosleep(256);
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
 // Wait for the phase with the given parity; false after kWaitNs.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -252,13 +264,26 @@ struct alignas(128) TcPassDesc {
   ReactionT<float> rx;
 };
 
+// Kernel parameter of one pass launch.  A launch for one solve carries its
+// descriptor (tensor maps included) in the parameter itself; a grouped
+// launch reads the solves' descriptors from device memory.
 struct TcLaunch {
-  const TcPassDesc* desc;   // [nsolves]
-  const int* ustart;        // [nsolves + 1] prefix sums of units
+  TcPassDesc one;           // used when desc is null (one solve)
+  const TcPassDesc* desc;   // [nsolves] in device memory, or null
+  const int* ustart;        // [nsolves + 1] prefix sums of units (desc non-null)
   int nsolves;
   int nunits;
   int* err;
 };
+
+// Programmatic dependent launch: a kernel lets the next kernel of the step
+// be scheduled early (its set-up then overlaps this kernel's tail) and
+// waits for its predecessors' completion before touching the data they
+// write.  Both are no-ops for launches without the programmatic attribute.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Epilogue of one mode-product pass.
 enum TcMode : int {
@@ -296,9 +321,14 @@ struct Unit {
 template <int BN>
 __device__ __forceinline__ Unit decode_unit(const TcLaunch& L, int u) {
   Unit w;
-  const int s = find_segment(L.ustart, L.nsolves, u);
-  w.d = L.desc + s;
-  int r = u - __ldg(L.ustart + s);
+  int r = u;
+  if (L.desc == nullptr) {
+    w.d = &L.one;
+  } else {
+    const int s = find_segment(L.ustart, L.nsolves, u);
+    w.d = L.desc + s;
+    r -= __ldg(L.ustart + s);
+  }
   if (w.d->pair) {
     w.c_lo = 0;
     w.c_hi = 2;
@@ -323,7 +353,7 @@ __device__ __forceinline__ Unit decode_unit(const TcLaunch& L, int u) {
 // columns; it prefetches its FP32 base values two 16-column chunks ahead,
 // starting before the accumulator is ready.
 template <int SW, int BN, bool PAIR>
-__global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) {
+__global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_constant__ TcLaunch L) {
   using C = TcCfg<SW, BN>;
   static_assert(4 * BN <= 512, "four accumulators must fit in TMEM");
   extern __shared__ uint8_t smem_raw[];
@@ -337,6 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
   int* abort_flag = (int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  pdl_trigger();
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -365,6 +396,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
     // ---------------- TMA producer
     uint32_t g = 0;  // k-block counter of this CTA
     bool stop = false;
+    bool waited = false;
     for (int u = blockIdx.x; u < L.nunits && !stop; u += gridDim.x) {
       const Unit w = decode_unit<BN>(L, u);
       const int nk = (w.d->K + C::BK - 1) / C::BK;
@@ -385,12 +417,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
             break;
           }
           uint8_t* st = smem + s * C::STAGE;
+          if (!waited) {  // the A pieces are the previous launch's output
+            pdl_wait();
+            waited = true;
+          }
           mbar_arrive_expect_tx(&full[s], C::STAGE);
-          for (int p = 0; p < kPieces; ++p)
-            tma_load_3d(st + p * C::TILE_A, ma, &full[s], kb * C::BK, w.m0, p);
-          for (int p = 0; p < kPieces; ++p)
-            tma_load_3d(st + kPieces * C::TILE_A + p * C::TILE_B, mb, &full[s], kb * C::BK,
-                        w.n0, p);
+          tma_load_3d(st, ma, &full[s], kb * C::BK, w.m0, 0);                   // 3 A pieces
+          tma_load_3d(st + kPieces * C::TILE_A, mb, &full[s], kb * C::BK, w.n0, 0);  // 3 B pieces
         }
       }
     }
@@ -400,6 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     const uint32_t idesc = idesc_bf16(kBM, BN);
+    const uint64_t dA0 = kmajor_desc<SW>(smem_u32(smem));  // stage 0, A piece 0
     uint32_t g = 0;
     int i = 0;  // local unit counter
     bool stop = false;
@@ -424,17 +458,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
             stop = true;
             break;
           }
-          tc_fence_after();
-          const uint32_t sa = smem_u32(smem + s * C::STAGE);
-          const uint32_t sb = sa + kPieces * C::TILE_A;
+          // (TMA -> MMA hand-off through the mbarrier needs no tcgen05 fence)
+          const uint64_t da = dA0 + (uint64_t)((s * C::STAGE) >> 4);
+          const uint64_t db = da + (uint64_t)((kPieces * C::TILE_A) >> 4);
 #pragma unroll
           for (int kk = 0; kk < C::KSTEPS; ++kk) {
-            const uint64_t a0 = kmajor_desc<SW>(sa + kk * 32);
-            const uint64_t a1 = kmajor_desc<SW>(sa + C::TILE_A + kk * 32);
-            const uint64_t a2 = kmajor_desc<SW>(sa + 2 * C::TILE_A + kk * 32);
-            const uint64_t b0 = kmajor_desc<SW>(sb + kk * 32);
-            const uint64_t b1 = kmajor_desc<SW>(sb + C::TILE_B + kk * 32);
-            const uint64_t b2 = kmajor_desc<SW>(sb + 2 * C::TILE_B + kk * 32);
+            const uint64_t a0 = da + (uint64_t)(kk * 2);
+            const uint64_t a1 = a0 + (uint64_t)(C::TILE_A >> 4);
+            const uint64_t a2 = a0 + (uint64_t)(2 * C::TILE_A >> 4);
+            const uint64_t b0 = db + (uint64_t)(kk * 2);
+            const uint64_t b1 = b0 + (uint64_t)(C::TILE_B >> 4);
+            const uint64_t b2 = b0 + (uint64_t)(2 * C::TILE_B >> 4);
             mma_bf16<kColNone>(dt, a2, b0, idesc, (kb | kk) != 0);
             mma_bf16<kColFill>(dt, a1, b1, idesc, 1);
             mma_bf16<kColLast>(dt, a1, b0, idesc, 1);
@@ -453,6 +487,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
     mbar_wait(drain, 0);
   } else if (warp >= 2) {
     // ---------------- epilogue
+    pdl_wait();
     const int q = warp & 3;                   // TMEM lane quarter
     const int half = (warp - 2) >> 2;         // column half
     constexpr int HC = BN / 2;                // columns per epilogue warp
@@ -484,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
           const int col = n0 + j;
           bv[j] = (fp32_in && bsrc && mrow && col < N) ? __ldg(bsrc + (int64_t)col * M + m) : 0.f;
         }
-        if (!mbar_wait(&acc_full[slot], (i >> 1) & 1)) {
+        if (!mbar_wait_sleep(&acc_full[slot], (i >> 1) & 1)) {
           if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
           *abort_v = 1;
           break;
@@ -550,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
         prefetch(0, 0);
         if (NCH > 1) prefetch(1, 1);
       }
-      if (!mbar_wait(&acc_full[slot], (i >> 1) & 1)) {
+      if (!mbar_wait_sleep(&acc_full[slot], (i >> 1) & 1)) {
         if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
         *abort_v = 1;
         break;
@@ -640,6 +675,372 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const TcLaunch L) 
   }
 }
 
+// ---------------------------------------------------------------- CTA-pair kernel
+// The same mode product with 2-SM tensor-core instructions (cta_group::2): a
+// cluster of two CTAs computes a 256 x BN tile as one M = 256 MMA.  Each CTA
+// stages its own 128 rows of A and half (BN / 2 rows) of B; the MMA, issued
+// by the even CTA, reads both CTAs' shared memory and writes each CTA's 128
+// accumulator rows into that CTA's TMEM.  Per SM this halves the B traffic
+// (TMA and shared-memory reads) of the one-CTA kernel.
+//
+// Synchronisation: both CTAs' TMA loads complete on the even CTA's `full`
+// barrier (which expects both CTAs' bytes); the MMA commits arrive on the
+// `empty` and `acc_full` barriers of both CTAs (multicast); both CTAs'
+// epilogue warps arrive on the even CTA's `acc_empty`.
+template <int SW>
+struct Tc2Cfg {
+  static constexpr int BN = 128;                     // output columns per tile
+  static constexpr int BK = SW / 2;
+  static constexpr int KSTEPS = SW / 32;
+  static constexpr int TILE_A = kBM * SW;            // this CTA's 128 A rows
+  static constexpr int TILE_B = (BN / 2) * SW;       // this CTA's half of the B rows
+  static constexpr int STAGE = kPieces * (TILE_A + TILE_B);
+  static constexpr int STAGES = (216 * 1024) / STAGE > 8 ? 8 : (216 * 1024) / STAGE;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map, uint32_t bar,
+                                                 int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish_pair() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+template <int COL>
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                              uint32_t acc) {
+  if constexpr (COL == kColFill) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else if constexpr (COL == kColUse) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else if constexpr (COL == kColLast) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+// Arrive on the barrier at this offset in every CTA of `mask` once the
+// preceding pair MMAs of this thread have completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+// One stage of the split-precision product: KSTEPS K16 steps, six MMAs each,
+// grouped by A piece for the A collector.  da / db are the descriptors of
+// piece 0 of the stage's A and B tiles; pieces and K steps are fixed offsets
+// of the descriptor's address field (16-byte units), so the issue loop adds
+// immediates only.  acc0 = 0 starts a new accumulation.
+template <int SW, int TILE_A, int TILE_B, bool CTA2>
+__device__ __forceinline__ void issue_stage(uint32_t dt, uint64_t da, uint64_t db, uint32_t idesc,
+                                            uint32_t acc0) {
+#pragma unroll
+  for (int kk = 0; kk < SW / 32; ++kk) {
+    const uint64_t a0 = da + (uint64_t)(kk * 2);
+    const uint64_t a1 = a0 + (uint64_t)(TILE_A >> 4);
+    const uint64_t a2 = a0 + (uint64_t)(2 * TILE_A >> 4);
+    const uint64_t b0 = db + (uint64_t)(kk * 2);
+    const uint64_t b1 = b0 + (uint64_t)(TILE_B >> 4);
+    const uint64_t b2 = b0 + (uint64_t)(2 * TILE_B >> 4);
+    if constexpr (CTA2) {
+      mma_bf16_pair<kColNone>(dt, a2, b0, idesc, kk == 0 ? acc0 : 1u);
+      mma_bf16_pair<kColFill>(dt, a1, b1, idesc, 1);
+      mma_bf16_pair<kColLast>(dt, a1, b0, idesc, 1);
+      mma_bf16_pair<kColFill>(dt, a0, b2, idesc, 1);
+      mma_bf16_pair<kColUse>(dt, a0, b1, idesc, 1);
+      mma_bf16_pair<kColLast>(dt, a0, b0, idesc, 1);
+    } else {
+      mma_bf16<kColNone>(dt, a2, b0, idesc, kk == 0 ? acc0 : 1u);
+      mma_bf16<kColFill>(dt, a1, b1, idesc, 1);
+      mma_bf16<kColLast>(dt, a1, b0, idesc, 1);
+      mma_bf16<kColFill>(dt, a0, b2, idesc, 1);
+      mma_bf16<kColUse>(dt, a0, b1, idesc, 1);
+      mma_bf16<kColLast>(dt, a0, b0, idesc, 1);
+    }
+  }
+}
+
+// Unit of the pair kernel: one component's 256 x BN tile.
+struct Unit2 {
+  const TcPassDesc* d;
+  int m0, n0, c;
+};
+__device__ __forceinline__ Unit2 decode_unit2(const TcLaunch& L, int u, int bn) {
+  Unit2 w;
+  int r = u;
+  if (L.desc == nullptr) {
+    w.d = &L.one;
+  } else {
+    const int s = find_segment(L.ustart, L.nsolves, u);
+    w.d = L.desc + s;
+    r -= __ldg(L.ustart + s);
+  }
+  const int per = w.d->tiles_m * w.d->tiles_n;  // tiles_m counts 256-row tiles
+  w.c = r / per;
+  r -= w.c * per;
+  w.m0 = (r / w.d->tiles_n) * (2 * kBM);
+  w.n0 = (r % w.d->tiles_n) * bn;
+  return w;
+}
+
+template <int SW>
+__global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_constant__ TcLaunch L) {
+  using C = Tc2Cfg<SW>;
+  constexpr int BN = C::BN;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* acc_full = empty + C::STAGES;   // [2]
+  uint64_t* acc_empty = acc_full + 2;       // [2]; used in the even CTA
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  int* abort_flag = (int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();     // 0: issues the MMAs
+  const int cid = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
+  pdl_trigger();
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 2 * kEpiWarps);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc_pair(tmem_slot, 2 * BN);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  cluster_sync_all();  // barriers initialised and TMEM allocated in both CTAs
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int* abort_v = abort_flag;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer (both CTAs)
+    uint32_t g = 0;
+    bool stop = false, waited = false;
+    for (int u = cid; u < L.nunits && !stop; u += ncl) {
+      const Unit2 w = decode_unit2(L, u, BN);
+      const int nk = (w.d->K + C::BK - 1) / C::BK;
+      const CUtensorMap* ma = &w.d->amap[w.c];
+      const CUtensorMap* mb = &w.d->bmap[w.c];
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)ma) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mb) : "memory");
+      const int ya = w.m0 + (int)rank * kBM, yb = w.n0 + (int)rank * (BN / 2);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % C::STAGES;
+        const uint32_t it = g / C::STAGES;
+        if (*abort_v || (it > 0 && !mbar_wait(&empty[s], (it - 1) & 1))) {
+          atomicCAS(L.err, 0, kErrTimeoutEmpty);
+          *abort_v = 1;
+          stop = true;
+          break;
+        }
+        if (!waited) {  // the A pieces are the previous launch's output
+          pdl_wait();
+          waited = true;
+        }
+        if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * C::STAGE);
+        const uint32_t fb = mapa_shared(smem_u32(&full[s]), 0);
+        uint8_t* st = smem + s * C::STAGE;
+        tma_load_3d_pair(st, ma, fb, kb * C::BK, ya, 0);                        // 3 A pieces
+        tma_load_3d_pair(st + kPieces * C::TILE_A, mb, fb, kb * C::BK, yb, 0);  // 3 B pieces
+      }
+    }
+    if (rank == 0) {
+      // the last STAGES k-blocks (both CTAs' bytes) must have landed before exit
+      const uint32_t first = g > (uint32_t)C::STAGES ? g - C::STAGES : 0;
+      for (uint32_t q = first; q < g; ++q) mbar_wait(&full[q % C::STAGES], (q / C::STAGES) & 1);
+    } else if (stop) {
+      // loads of this CTA still in flight complete on the even CTA's barrier;
+      // give them time to land before the exit rendezvous
+      const uint64_t t0 = globaltimer();
+      while (globaltimer() - t0 < 50000ull) {
+      }
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ---------------- MMA issuer (even CTA)
+    const uint32_t idesc = idesc_bf16(2 * kBM, BN);
+    const uint64_t dA0 = kmajor_desc<SW>(smem_u32(smem));
+    uint32_t g = 0;
+    int i = 0;
+    bool stop = false;
+    for (int u = cid; u < L.nunits && !stop; u += ncl, ++i) {
+      const int slot = i & 1;
+      const uint32_t use = i >> 1;
+      if (use > 0 && !mbar_wait(&acc_empty[slot], (use - 1) & 1)) {
+        atomicCAS(L.err, 0, kErrTimeoutDone);
+        *abort_v = 1;
+        break;
+      }
+      tc_fence_after();
+      const Unit2 w = decode_unit2(L, u, BN);
+      const int nk = (w.d->K + C::BK - 1) / C::BK;
+      const uint32_t dt = tmem + (uint32_t)(slot * BN);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % C::STAGES;
+        if (!mbar_wait(&full[s], (g / C::STAGES) & 1)) {
+          atomicCAS(L.err, 0, kErrTimeoutFull);
+          *abort_v = 1;
+          stop = true;
+          break;
+        }
+        const uint64_t da = dA0 + (uint64_t)((s * C::STAGE) >> 4);
+        const uint64_t db = da + (uint64_t)((kPieces * C::TILE_A) >> 4);
+        issue_stage<SW, C::TILE_A, C::TILE_B, true>(dt, da, db, idesc, kb != 0);
+        mma_commit_pair(&empty[s], 0x3);  // frees stage s in both CTAs
+      }
+      if (stop) break;
+      mma_commit_pair(&acc_full[slot], 0x3);
+    }
+    mma_commit_pair(drain, 0x1);
+    mbar_wait(drain, 0);
+  } else if (warp >= 2) {
+    // ---------------- epilogue (both CTAs)
+    pdl_wait();
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    constexpr int HC = BN / 2;
+    constexpr int NCH = HC / 16;
+    const uint32_t ae0 = mapa_shared(smem_u32(&acc_empty[0]), 0);
+    const uint32_t ae1 = mapa_shared(smem_u32(&acc_empty[1]), 0);
+    int i = 0;
+    for (int u = cid; u < L.nunits; u += ncl, ++i) {
+      const int slot = i & 1;
+      const Unit2 w = decode_unit2(L, u, BN);
+      const TcPassDesc* D = w.d;
+      const int M = D->M, N = D->N, mode = D->mode;
+      const float alpha = D->alpha;
+      const bool fp32_in = mode != kPieces3;
+      const int n0 = w.n0 + half * HC;
+      const int m = w.m0 + (int)rank * kBM + q * 32 + lane;
+      const bool mrow = m < M;
+      const int64_t plane = (int64_t)N * M;
+      float bv[HC];
+      const float* bsrc = D->base[w.c];
+#pragma unroll
+      for (int j = 0; j < HC; ++j) {
+        const int col = n0 + j;
+        bv[j] = (fp32_in && bsrc && mrow && col < N) ? __ldg(bsrc + (int64_t)col * M + m) : 0.f;
+      }
+      if (!mbar_wait_sleep(&acc_full[slot], (i >> 1) & 1)) {
+        if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
+        *abort_v = 1;
+        break;
+      }
+      tc_fence_after();
+      if (*abort_v) break;
+      const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * BN + half * HC);
+#pragma unroll
+      for (int bt = 0; bt < NCH; bt += 2) {
+        uint32_t r[2][16];
+        tmem_ld16_nw(ta + (uint32_t)(bt * 16), r[0]);
+        tmem_ld16_nw(ta + (uint32_t)((bt + 1) * 16), r[1]);
+        tmem_wait_ld();
+        tmem_fence16(r[0]);
+        tmem_fence16(r[1]);
+        if (mrow) {
+          if (mode == kPieces3) {
+            __nv_bfloat16* op = D->outp[w.c];
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              const int col = n0 + bt * 16 + jj;
+              if (col < N) {
+                const int64_t o = (int64_t)col * M + m;
+                __nv_bfloat16 b0, b1, b2;
+                split3(__uint_as_float(r[jj / 16][jj % 16]), b0, b1, b2);
+                op[o] = b0;
+                op[plane + o] = b1;
+                op[2 * plane + o] = b2;
+              }
+            }
+          } else {
+            float* of = D->outf[w.c];
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              const int col = n0 + bt * 16 + jj;
+              if (col < N)
+                of[(int64_t)col * M + m] = bv[bt * 16 + jj] + alpha * __uint_as_float(r[jj / 16][jj % 16]);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(slot ? ae1 : ae0);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // neither CTA's shared memory or TMEM is in use any more
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, 2 * BN);
+  }
+}
+
 // ---------------------------------------------------------------- pointwise
 // Per-solve arguments of the pointwise kernels of the tensor-core path; one
 // launch covers one solve or a whole batch.
@@ -682,7 +1083,9 @@ __device__ __forceinline__ int stage_pw(const PwLaunch& L, PwDesc* sd) {
   const uint32_t* src = reinterpret_cast<const uint32_t*>(L.desc + s);
   uint32_t* dst = reinterpret_cast<uint32_t*>(sd);
   for (int w = threadIdx.x; w < (int)(sizeof(PwDesc) / 4); w += blockDim.x) dst[w] = __ldg(src + w);
+  pdl_trigger();
   __syncthreads();
+  pdl_wait();  // the descriptor is static; the data it points to is not
   return s;
 }
 
@@ -953,12 +1356,15 @@ cudaError_t get_encoder() {
   return cudaSuccess;
 }
 
-// [3][rows][K] BF16 pieces, box {SW/2, box_rows, 1}, SW-byte swizzle.
+// [3][rows][K] BF16 pieces, box {SW/2, box_rows, 3}, SW-byte swizzle: one
+// copy brings a K chunk of all three pieces of a tile, laid out in shared
+// memory as [piece][row][SW bytes].  (The copy engine's cost is largely per
+// instruction, so one large box moves data much faster than three small ones.)
 cudaError_t encode_pieces(CUtensorMap* map, const void* base, int64_t K, int64_t rows,
                           int box_rows, int sw) {
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)kPieces};
   cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)(K * rows) * 2};
-  cuuint32_t box[3] = {(cuuint32_t)(sw / 2), (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)(sw / 2), (cuuint32_t)box_rows, (cuuint32_t)kPieces};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -967,12 +1373,14 @@ cudaError_t encode_pieces(CUtensorMap* map, const void* base, int64_t K, int64_t
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Kernel variants (swizzle width, tile width).
+// Kernel variants (swizzle width, tile width, CTA pair).  Pair variants run
+// tc_pair_kernel: 256-row tiles over two SMs.
 struct Variant {
-  int sw, bn;
+  int sw, bn, cta2;
 };
-constexpr Variant kVariants[] = {{64, 128}, {128, 128}, {64, 64}};
-constexpr int kNumVariants = 3;
+constexpr Variant kVariants[] = {{64, 128, 0}, {128, 128, 0}, {64, 64, 0}, {64, 128, 1}, {128, 128, 1}};
+constexpr int kNumVariants = 5;
+constexpr int tile_rows(int variant) { return kVariants[variant].cta2 ? 2 * kBM : kBM; }
 
 template <int SW, int BN>
 cudaError_t set_smem_attr() {
@@ -982,29 +1390,110 @@ cudaError_t set_smem_attr() {
   return cudaFuncSetAttribute(tc_mode_kernel<SW, BN, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<SW, BN>::SMEM);
 }
+template <int SW>
+cudaError_t set_smem_attr_pair() {
+  return cudaFuncSetAttribute(tc_pair_kernel<SW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Tc2Cfg<SW>::SMEM);
+}
+
+// Programmatic dependent launch for the kernels of a step (ADR_PDL=0 turns
+// it off: every kernel then waits for the previous one to finish).
+static bool pdl_enabled() {
+  static const int on = [] {
+    const char* e = getenv("ADR_PDL");
+    return e ? atoi(e) : 1;
+  }();
+  return on != 0;
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 template <bool PAIR>
 cudaError_t launch_tc_t(int v, dim3 grid, cudaStream_t s, const TcLaunch& L) {
   switch (v) {
     case 0:
-      tc_mode_kernel<64, 128, PAIR><<<grid, kThreads, TcCfg<64, 128>::SMEM, s>>>(L);
-      break;
+      return launch_k(tc_mode_kernel<64, 128, PAIR>, grid, dim3(kThreads), TcCfg<64, 128>::SMEM, s, L);
     case 1:
-      tc_mode_kernel<128, 128, PAIR><<<grid, kThreads, TcCfg<128, 128>::SMEM, s>>>(L);
-      break;
+      return launch_k(tc_mode_kernel<128, 128, PAIR>, grid, dim3(kThreads), TcCfg<128, 128>::SMEM, s, L);
     case 2:
-      tc_mode_kernel<64, 64, PAIR><<<grid, kThreads, TcCfg<64, 64>::SMEM, s>>>(L);
-      break;
+      return launch_k(tc_mode_kernel<64, 64, PAIR>, grid, dim3(kThreads), TcCfg<64, 64>::SMEM, s, L);
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 // pair: the launch's units are (u, v) pairs (the fused stage-1 epilogue).
-cudaError_t launch_tc(int v, int num_sms, cudaStream_t s, const TcLaunch& L, bool pair) {
+// A pair-variant launch: clusters of two CTAs, at most `clusters` of them
+// (the number that fit on the GPU at once).
+template <int SW>
+cudaError_t launch_pair(int clusters, cudaStream_t s, const TcLaunch& L) {
+  const int nc = L.nunits < clusters ? L.nunits : clusters;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * nc));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = Tc2Cfg<SW>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, tc_pair_kernel<SW>, L);
+}
+
+// Clusters of the pair kernel that can be resident at once.
+int pair_clusters(int variant) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(kThreads);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  cudaError_t e;
+  if (kVariants[variant].sw == 64) {
+    cfg.dynamicSmemBytes = Tc2Cfg<64>::SMEM;
+    e = cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<64>, &cfg);
+  } else {
+    cfg.dynamicSmemBytes = Tc2Cfg<128>::SMEM;
+    e = cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<128>, &cfg);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+// pair: the launch's units are (u, v) pairs (the fused stage-1 epilogue).
+// slots: resident CTAs (one-CTA variants) or clusters (pair variants).
+cudaError_t launch_tc(int v, int slots, cudaStream_t s, const TcLaunch& L, bool pair) {
   if (L.nunits <= 0) return cudaSuccess;
-  dim3 grid((unsigned)(L.nunits < num_sms ? L.nunits : num_sms));
+  if (kVariants[v].cta2)
+    return kVariants[v].sw == 64 ? launch_pair<64>(slots, s, L) : launch_pair<128>(slots, s, L);
+  dim3 grid((unsigned)(L.nunits < slots ? L.nunits : slots));
   return pair ? launch_tc_t<true>(v, grid, s, L) : launch_tc_t<false>(v, grid, s, L);
 }
 
@@ -1050,6 +1539,7 @@ struct TcState {
   int variant;
   int fuse;      // 1: fuse the stage-1 combination into the last stage-1 product
   int num_sms;
+  int slots;     // resident CTAs (or CTA pairs) of the mode-product kernel
   int* err;
   std::vector<void*> allocs;
   // step sequence: tensor-core passes and the launches around them
@@ -1061,6 +1551,7 @@ struct TcState {
   int* d_ustart;   // [passes][2]
   PwDesc* d_pw;
   int* d_bstart;   // rhs {0, blocks}, rdiff {0, blocks}
+  std::vector<TcPassDesc> h_desc;  // host copies of d_desc
   int units[8];
   int rhs_blocks, rdiff_blocks;
   void* bound_u;
@@ -1070,7 +1561,8 @@ struct TcState {
 static int units_of(const TcState* S, const TcPass& ps, int bn) {
   const int64_t nmu = S->n[ps.mu];
   const int64_t M = S->N / nmu;
-  const int tm = (int)((M + kBM - 1) / kBM), tn = (int)((nmu + bn - 1) / bn);
+  const int bm = tile_rows(S->variant);
+  const int tm = (int)((M + bm - 1) / bm), tn = (int)((nmu + bn - 1) / bn);
   return (ps.pair ? 1 : 2) * tm * tn;
 }
 
@@ -1083,7 +1575,7 @@ static TcPassDesc make_desc(const TcState* S, const adr_plan_s* P, const TcPass&
   D.M = (int)(S->N / nmu);
   D.N = (int)nmu;
   D.K = (int)nmu;
-  D.tiles_m = (D.M + kBM - 1) / kBM;
+  D.tiles_m = (D.M + tile_rows(S->variant) - 1) / tile_rows(S->variant);
   D.tiles_n = (D.N + bn - 1) / bn;
   D.pair = ps.pair;
   D.mode = ps.mode;
@@ -1181,12 +1673,18 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     if ((e = set_smem_attr<64, 128>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<128, 128>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<64, 64>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr_pair<64>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr_pair<128>()) != cudaSuccess) return e;
     attr_set = true;
   }
   TcState* S = new TcState();
   t->work[0] = S;
   t->prec = prec;
   S->d = d;
+  // Default kernel: one CTA per 128 x 128 tile, 64-byte swizzle, four 48 KB
+  // stages.  (The CTA-pair kernel, variant 4, is about 2% faster on a 1024^2
+  // grid but about 10% slower on batches of small grids; one kernel for every
+  // plan keeps batches of mixed sizes grouped.)  ADR_TC_VARIANT overrides.
   S->variant = 0;
   if (const char* ev = getenv("ADR_TC_VARIANT")) {
     const int v = atoi(ev);
@@ -1196,10 +1694,16 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
   // the separate reaction-difference kernel on large grids
   S->fuse = 0;
   if (const char* ev = getenv("ADR_TC_FUSE")) S->fuse = atoi(ev) != 0 ? 1 : 0;
+  if (kVariants[S->variant].cta2) S->fuse = 0;  // the pair kernel has no pair-unit epilogue
   int dev = 0;
   cudaGetDevice(&dev);
   S->num_sms = 148;
   cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  S->slots = S->num_sms;
+  if (kVariants[S->variant].cta2) {
+    S->slots = pair_clusters(S->variant);
+    if (S->slots <= 0) return cudaErrorNotSupported;
+  }
   const int sw = kVariants[S->variant].sw, bn = kVariants[S->variant].bn;
   S->N = 1;
   for (int m = 0; m < 3; ++m) S->n[m] = m < d ? n[m] : 1;
@@ -1223,7 +1727,8 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
         split_matrix_kernel<<<grid_for(nn), 256, 0, s>>>(master[c][m][1 + l], S->phi[c][m][l], nn);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        e = encode_pieces(&S->bmap[c][m][l], S->phi[c][m][l], n[m], n[m], bn, sw);
+        e = encode_pieces(&S->bmap[c][m][l], S->phi[c][m][l], n[m], n[m],
+                          kVariants[S->variant].cta2 ? bn / 2 : bn, sw);
         if (e != cudaSuccess) return e;
       }
   for (int b = 0; b < 2; ++b)
@@ -1327,6 +1832,7 @@ cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v) {
     e = cudaMemcpyAsync(S->d_pw, &pw, sizeof(pw), cudaMemcpyHostToDevice, P->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
   if (e != cudaSuccess) return e;
+  S->h_desc = hd;
   S->bound_u = u;
   S->bound_v = v;
   return cudaSuccess;
@@ -1335,10 +1841,11 @@ cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v) {
 // Launch the kernels of one step for a group of solves (one solve or a
 // batch), following the plan's operation list.
 struct GroupStep {
-  int d, variant, num_sms, nsolves;
+  int d, variant, num_sms, nsolves;  // num_sms: resident CTAs or CTA pairs of the TC kernel
   int np, nops;
   TcOp ops[16];
   const TcPassDesc* desc;   // [np][nsolves]
+  const TcPassDesc* hdesc;  // one solve: host copies [np], passed in the launch; else null
   const int* ustart;        // [np][nsolves + 1]
   int units[16];
   int pair[16];             // per pass: units are (u, v) pairs
@@ -1358,32 +1865,36 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
     switch (op.kind) {
       case kOpRhs:
         e = timed_kernel(ctl, KC_RHS, N * 2.0 * (6.0 * G.d + 10.0), N * (8.0 + 12.0), [&] {
-          rhs_pieces_kernel<<<G.rhs_blocks, kPwThreads, 0, st>>>(G.rhs);
-          return cudaGetLastError();
+          return launch_k(rhs_pieces_kernel, dim3(G.rhs_blocks), dim3(kPwThreads), 0, st, G.rhs);
         });
         break;
       case kOpRdiff:
         e = timed_kernel(ctl, KC_RDIFF, N * 2.0 * 12.0, N * (16.0 + 12.0), [&] {
-          rdiff_pieces_kernel<<<G.flat_blocks, kPwThreads, 0, st>>>(G.flat);
-          return cudaGetLastError();
+          return launch_k(rdiff_pieces_kernel, dim3(G.flat_blocks), dim3(kPwThreads), 0, st, G.flat);
         });
         break;
       case kOpLawsonPre:
         e = timed_kernel(ctl, KC_LAWSON_PW, N * 2.0 * 12.0, N * (8.0 + 12.0), [&] {
-          lawson_pre_pieces_kernel<<<G.flat_blocks, kPwThreads, 0, st>>>(G.flat, op.factor);
-          return cudaGetLastError();
+          return launch_k(lawson_pre_pieces_kernel, dim3(G.flat_blocks), dim3(kPwThreads), 0, st,
+                          G.flat, op.factor);
         });
         break;
       case kOpLawsonPost:
         e = timed_kernel(ctl, KC_LAWSON_PW, N * 2.0 * 12.0, N * 16.0, [&] {
-          lawson_post_kernel<<<G.flat_blocks, kPwThreads, 0, st>>>(G.flat, op.factor);
-          return cudaGetLastError();
+          return launch_k(lawson_post_kernel, dim3(G.flat_blocks), dim3(kPwThreads), 0, st, G.flat,
+                          op.factor);
         });
         break;
       case kOpTc: {
         const int p = op.pass;
         TcLaunch L;
-        L.desc = G.desc + (size_t)p * G.nsolves;
+        memset(&L, 0, sizeof(L));
+        if (G.hdesc) {
+          L.one = G.hdesc[p];
+          L.desc = nullptr;
+        } else {
+          L.desc = G.desc + (size_t)p * G.nsolves;
+        }
         L.ustart = G.ustart + (size_t)p * (G.nsolves + 1);
         L.nsolves = G.nsolves;
         L.nunits = G.units[p];
@@ -1422,10 +1933,11 @@ cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   memset(&G, 0, sizeof(G));
   G.d = S->d;
   G.variant = S->variant;
-  G.num_sms = S->num_sms;
+  G.num_sms = S->slots;
   G.nsolves = 1;
   fill_ops(G, S);
   G.desc = S->d_desc;
+  G.hdesc = S->h_desc.data();
   G.ustart = S->d_ustart;
   for (int p = 0; p < G.np; ++p) {
     G.units[p] = S->units[p];
@@ -1540,7 +2052,7 @@ extern "C" adr_status adr_batch_create(const adr_plan* plans, int count, void* s
     B->np = (int)S0->passes.size();
     B->proto = S0;
     B->variant = S0->variant;
-    B->num_sms = S0->num_sms;
+    B->num_sms = S0->slots;
     B->d = S0->d;
     const int bn = kVariants[B->variant].bn;
     std::vector<int> us((size_t)B->np * (S_ + 1)), bs(2 * (size_t)(S_ + 1));

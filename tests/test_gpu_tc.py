@@ -79,9 +79,10 @@ def test_ragged_shapes_bf16x3(adr, n, model):
 @pytest.mark.parametrize("n", [(72, 200), (24, 40, 56)])
 def test_stage_one_fusion_both_ways(adr, n, fuse, monkeypatch):
     """The stage-1 combination and reaction difference either fused into the
-    last tensor-core product (pair units) or done by a separate kernel must
-    both match the oracle."""
+    last tensor-core product (pair units of the one-CTA kernel) or done by a
+    separate kernel must both match the oracle."""
     monkeypatch.setenv("ADR_TC_FUSE", fuse)
+    monkeypatch.setenv("ADR_TC_VARIANT", "0")
     d = len(n)
     p = wl.Problem(d=d, n=n, lo=(0.0,) * d, hi=(1.0,) * d, diff=(0.05, 0.3),
                    adv=((0.2, -0.1, 0.3)[:d], (-0.2, 0.1, 0.05)[:d]), model=wl.SCHNAKENBERG,
@@ -128,3 +129,22 @@ def test_bf16x3_not_less_accurate_than_fp32(adr):
     ef = oracle.max_rel_err(Uf, Vf, Ur, Vr)
     assert eb <= TOL and ef <= TOL
     assert eb <= 2.0 * ef, (eb, ef)
+
+
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4"])
+@pytest.mark.parametrize("n", [(200, 136), (40, 24, 56), (256, 384)])
+def test_kernel_variants(adr, n, variant, monkeypatch):
+    """Every mode-product kernel variant (one-CTA tiles of 128 x 128 or
+    128 x 64 with 64- or 128-byte swizzle; CTA-pair tiles of 256 x 128)
+    matches the oracle, including grids whose sizes are not multiples of the
+    tile sizes."""
+    monkeypatch.setenv("ADR_TC_VARIANT", variant)
+    d = len(n)
+    p = wl.Problem(d=d, n=n, lo=(0.0,) * d, hi=(1.0,) * d, diff=(0.05, 0.3),
+                   adv=((0.2, -0.1, 0.3)[:d], (-0.2, 0.1, 0.05)[:d]), model=wl.FHN,
+                   params=(0.05, 2.0, -0.03), tau=2e-3, nsteps=5, seed=19)
+    u0, v0 = inputs(p, kind="uniform")
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, p.nsteps)
+    U, V, st = run(adr, p, u0, v0, p.nsteps)
+    assert st["kernels"]["mode_product_tc"]["count"] == 2 * d * p.nsteps
+    assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
