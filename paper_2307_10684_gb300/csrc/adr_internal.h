@@ -171,7 +171,11 @@ struct adr_plan_s {
   int64_t launches;
   int64_t steps;
   bool timing;
-  std::vector<TimedLaunch> timed;
+  std::vector<TimedLaunch> timed;        // directly launched, not yet harvested
+  std::vector<TimedLaunch> graph_timed;  // captured in the timed graph; harvested per replay
+  bool capturing;                        // a graph capture is recording the launches
+  double acc_ms[KC_COUNT], acc_flops[KC_COUNT], acc_bytes[KC_COUNT];
+  int64_t acc_count[KC_COUNT];
   std::vector<cudaEvent_t> event_pool;
   size_t event_next;
   // CUDA graph of kGraphChunk steps for one (u, v) pair, replayed by adr_step
@@ -181,6 +185,11 @@ struct adr_plan_s {
   void* g_u;
   void* g_v;
   int64_t g_launches;        // kernels per replay
+  // timing mode: the same chunk captured with an event-record node before and
+  // after every kernel, so that per-kernel times exclude host launch gaps
+  cudaGraphExec_t gexec_timed;
+  void* gt_u;
+  void* gt_v;
 };
 
 
@@ -205,6 +214,14 @@ inline cudaEvent_t pool_event(adr_plan_s* P) {
   return e;
 }
 
+// Inside a capture the event becomes an event-record node of the graph.
+inline void record_event(adr_plan_s* P, cudaEvent_t e) {
+  if (P->capturing)
+    cudaEventRecordWithFlags(e, P->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, P->stream);
+}
+
 // Launch wrapper: counts launches and, when timing is on, brackets the
 // launch with events on the plan's stream.
 template <typename F>
@@ -213,14 +230,29 @@ inline cudaError_t timed_kernel(adr_plan_s* P, int cls, double flops, double byt
   if (P->timing) {
     e0 = pool_event(P);
     e1 = pool_event(P);
-    if (e0) cudaEventRecord(e0, P->stream);
+    if (e0) record_event(P, e0);
   }
   cudaError_t err = fn();
   P->launches++;
   if (P->timing && e0 && e1) {
-    cudaEventRecord(e1, P->stream);
-    P->timed.push_back(TimedLaunch{cls, e0, e1, flops, bytes});
+    record_event(P, e1);
+    (P->capturing ? P->graph_timed : P->timed).push_back(TimedLaunch{cls, e0, e1, flops, bytes});
   }
   return err;
+}
+
+// Add the elapsed times of `v`'s launches (completed) to the plan's totals.
+inline void harvest_timing(adr_plan_s* P, const std::vector<TimedLaunch>& v) {
+  for (const TimedLaunch& t : v) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.e0, t.e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    P->acc_count[t.cls]++;
+    P->acc_ms[t.cls] += ms;
+    P->acc_flops[t.cls] += t.flops;
+    P->acc_bytes[t.cls] += t.bytes;
+  }
 }
 }  // namespace adr

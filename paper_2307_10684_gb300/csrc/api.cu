@@ -233,6 +233,7 @@ static void plan_free(adr_plan P) {
   for (void* q : P->allocs) cudaFree(q);
   for (cudaEvent_t e : P->event_pool) cudaEventDestroy(e);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->gexec_timed) cudaGraphExecDestroy(P->gexec_timed);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   tc_free(&P->tc);
   delete P;
@@ -264,6 +265,13 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
   P->dstate[0] = P->dstate[1] = nullptr;
   P->gexec = nullptr;
   P->g_u = P->g_v = nullptr;
+  P->gexec_timed = nullptr;
+  P->gt_u = P->gt_v = nullptr;
+  P->capturing = false;
+  memset(P->acc_ms, 0, sizeof(P->acc_ms));
+  memset(P->acc_flops, 0, sizeof(P->acc_flops));
+  memset(P->acc_bytes, 0, sizeof(P->acc_bytes));
+  memset(P->acc_count, 0, sizeof(P->acc_count));
   P->g_launches = 0;
   P->cap_stream = nullptr;
   P->use_graphs = 1;
@@ -395,16 +403,22 @@ static cudaError_t step_direct(adr_plan P, void* u, void* v, int64_t nsteps) {
 // hundred kernels per cudaGraphLaunch.
 static constexpr int64_t kGraphChunk = 32;
 
-// Capture kGraphChunk steps on (u, v) into P->gexec.  On any failure graphs
-// are switched off for this plan and the caller launches directly.
+// Capture kGraphChunk steps on (u, v) into P->gexec (P->gexec_timed when
+// timing: the capture then also records the event-record nodes around every
+// kernel).  On any failure graphs are switched off for this plan and the
+// caller launches directly.
 static void build_graph(adr_plan P, void* u, void* v) {
-  if (P->gexec) {
-    cudaGraphExecDestroy(P->gexec);
-    P->gexec = nullptr;
+  const bool timed = P->timing;
+  cudaGraphExec_t& ge = timed ? P->gexec_timed : P->gexec;
+  if (ge) {
+    cudaGraphExecDestroy(ge);
+    ge = nullptr;
   }
   const int64_t l0 = P->launches, s0 = P->steps;
   cudaStream_t saved = P->stream;
   P->stream = P->cap_stream;
+  if (timed) P->graph_timed.clear();
+  P->capturing = true;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
@@ -412,20 +426,26 @@ static void build_graph(adr_plan P, void* u, void* v) {
     cudaError_t e2 = cudaStreamEndCapture(P->cap_stream, &g);
     e = e1 != cudaSuccess ? e1 : e2;
   }
+  P->capturing = false;
   P->stream = saved;
   P->g_launches = P->launches - l0;
   P->launches = l0;
   P->steps = s0;
-  if (e == cudaSuccess && g) e = cudaGraphInstantiate(&P->gexec, g, 0);
+  if (e == cudaSuccess && g) e = cudaGraphInstantiate(&ge, g, 0);
   if (g) cudaGraphDestroy(g);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    P->gexec = nullptr;
+    ge = nullptr;
     P->use_graphs = 0;
     return;
   }
-  P->g_u = u;
-  P->g_v = v;
+  if (timed) {
+    P->gt_u = u;
+    P->gt_v = v;
+  } else {
+    P->g_u = u;
+    P->g_v = v;
+  }
 }
 
 static adr_status step_impl(adr_plan P, void* u, void* v, int64_t nsteps) {
@@ -438,15 +458,25 @@ static adr_status step_impl(adr_plan P, void* u, void* v, int64_t nsteps) {
     if (e != cudaSuccess)
       return fail(ADR_ECUDA, std::string("adr_step: binding state buffers: ") + cudaGetErrorString(e));
   }
-  if (P->use_graphs && !P->timing && nsteps >= kGraphChunk) {
-    if (!P->gexec || P->g_u != u || P->g_v != v) build_graph(P, u, v);
-    if (P->gexec) {
+  if (P->use_graphs && nsteps >= kGraphChunk) {
+    const bool timed = P->timing;
+    if (timed ? (!P->gexec_timed || P->gt_u != u || P->gt_v != v)
+              : (!P->gexec || P->g_u != u || P->g_v != v))
+      build_graph(P, u, v);
+    cudaGraphExec_t ge = timed ? P->gexec_timed : P->gexec;
+    if (ge) {
       for (; done + kGraphChunk <= nsteps; done += kGraphChunk) {
-        cudaError_t e = cudaGraphLaunch(P->gexec, P->stream);
+        cudaError_t e = cudaGraphLaunch(ge, P->stream);
         if (e != cudaSuccess)
           return fail(ADR_ECUDA, std::string("adr_step: cudaGraphLaunch: ") + cudaGetErrorString(e));
         P->launches += P->g_launches;
         P->steps += kGraphChunk;
+        if (timed) {  // the replay's events are re-recorded by the next replay
+          e = cudaStreamSynchronize(P->stream);
+          if (e != cudaSuccess)
+            return fail(ADR_ECUDA, std::string("adr_step: ") + cudaGetErrorString(e));
+          harvest_timing(P, P->graph_timed);
+        }
       }
     }
   }
@@ -544,6 +574,16 @@ extern "C" adr_status adr_plan_set_timing(adr_plan plan, int enable) {
   plan->timing = enable != 0;
   if (int* ew = tc_error_word(&plan->tc)) ADR_CUDA_TRY(cudaMemset(ew, 0, sizeof(int)));
   plan->timed.clear();
+  plan->graph_timed.clear();
+  if (plan->gexec_timed) {  // holds pool events that are handed out again
+    cudaGraphExecDestroy(plan->gexec_timed);
+    plan->gexec_timed = nullptr;
+  }
+  plan->gt_u = plan->gt_v = nullptr;
+  memset(plan->acc_ms, 0, sizeof(plan->acc_ms));
+  memset(plan->acc_flops, 0, sizeof(plan->acc_flops));
+  memset(plan->acc_bytes, 0, sizeof(plan->acc_bytes));
+  memset(plan->acc_count, 0, sizeof(plan->acc_count));
   plan->event_next = 0;
   plan->launches = 0;
   plan->steps = 0;
@@ -566,16 +606,13 @@ extern "C" adr_status adr_plan_stats(adr_plan plan, adr_stats* out) {
   for (int k = 0; k < KC_COUNT; ++k) snprintf(out->name[k], 32, "%s", kClassNames[k]);
   if (plan->timing) {
     ADR_CUDA_TRY(cudaStreamSynchronize(plan->stream));
-    for (const TimedLaunch& t : plan->timed) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, t.e0, t.e1) != cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      out->count[t.cls]++;
-      out->ms[t.cls] += ms;
-      out->flops[t.cls] += t.flops;
-      out->bytes[t.cls] += t.bytes;
+    harvest_timing(plan, plan->timed);  // direct launches since the last call
+    plan->timed.clear();
+    for (int k = 0; k < KC_COUNT; ++k) {
+      out->count[k] = plan->acc_count[k];
+      out->ms[k] = plan->acc_ms[k];
+      out->flops[k] = plan->acc_flops[k];
+      out->bytes[k] = plan->acc_bytes[k];
     }
   }
   return ADR_OK;

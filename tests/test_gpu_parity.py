@@ -227,3 +227,28 @@ def test_graph_replay_matches_direct_launches(adr, precision, monkeypatch):
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
     assert outs[0][2]["launches"] == outs[1][2]["launches"]
     assert outs[0][2]["steps"] == outs[1][2]["steps"] == p.nsteps
+
+
+def test_timed_graph_replay(adr):
+    """With timing on, adr_step replays graph chunks that carry event-record
+    nodes around every kernel: the result is bitwise that of the untimed run
+    and every launch is timed."""
+    import torch
+    p = wl.fhn_1024(precision=wl.BF16X3, n=64, nsteps=70)
+    u0, v0 = inputs(p, wl.BF16X3)
+    outs = []
+    for timing in (False, True):
+        u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+        with adr.Plan(p) as plan:
+            plan.set_timing(timing)
+            plan.step(u, v, p.nsteps)
+            st = plan.stats()
+        outs.append((u.cpu(), v.cpu(), st))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    st = outs[1][2]
+    assert st["launches"] == 6 * p.nsteps and st["device_error"] == 0
+    k = st["kernels"]
+    assert k["mode_product_tc"]["count"] == 4 * p.nsteps
+    assert k["rhs_stencil_reaction"]["count"] == p.nsteps == k["reaction_diff"]["count"]
+    assert all(k[c]["ms"] > 0 for c in ("mode_product_tc", "rhs_stencil_reaction", "reaction_diff"))
