@@ -1064,9 +1064,12 @@ struct PwDesc {
   int64_t sy, sz;      // element strides of y and z
 };
 
+// Kernel parameter of a pointwise launch: one solve carries its descriptor
+// in the parameter; a grouped launch reads them from device memory.
 struct PwLaunch {
-  const PwDesc* desc;
-  const int* bstart;   // [nsolves + 1] prefix sums of this kernel's blocks
+  PwDesc one;          // used when desc is null
+  const PwDesc* desc;  // [nsolves] in device memory, or null
+  const int* bstart;   // [nsolves + 1] prefix sums of this kernel's blocks (desc non-null)
   int nsolves;
 };
 
@@ -1076,17 +1079,26 @@ constexpr int kSegX = 128;                          // x-points per warp
 constexpr int kFlatVec = 2;                         // float4 per thread per array
 constexpr int kFlatPerBlock = kPwThreads * 4 * kFlatVec;
 
-// The block's solve and its descriptor, staged once in shared memory.
-__device__ __forceinline__ int stage_pw(const PwLaunch& L, PwDesc* sd) {
+// The block's descriptor: the launch parameter for one solve, else staged
+// once in shared memory.  lb = the block's index within its solve.  Waits
+// for the previous kernel of the step before returning (the descriptor is
+// static; the data it points to is not).
+__device__ __forceinline__ const PwDesc* block_desc(const PwLaunch& L, PwDesc* sd, int& lb) {
+  pdl_trigger();
+  if (L.desc == nullptr) {
+    lb = blockIdx.x;
+    pdl_wait();
+    return &L.one;
+  }
   const int s = find_segment(L.bstart, L.nsolves, blockIdx.x);
   static_assert(sizeof(PwDesc) % 4 == 0, "PwDesc is copied in 32-bit words");
   const uint32_t* src = reinterpret_cast<const uint32_t*>(L.desc + s);
   uint32_t* dst = reinterpret_cast<uint32_t*>(sd);
   for (int w = threadIdx.x; w < (int)(sizeof(PwDesc) / 4); w += blockDim.x) dst[w] = __ldg(src + w);
-  pdl_trigger();
+  lb = blockIdx.x - __ldg(L.bstart + s);
   __syncthreads();
-  pdl_wait();  // the descriptor is static; the data it points to is not
-  return s;
+  pdl_wait();
+  return sd;
 }
 
 __device__ __forceinline__ float tri_dir(float xm, float xc, float xp, int i, int n, float lo,
@@ -1124,107 +1136,135 @@ struct Coef {
 __device__ __forceinline__ Coef coef(const TridiagT<float>& A) { return Coef{A.lo, A.up, A.b0, A.bn}; }
 
 // W^c = K^c U^c + G^c(U, V) as BF16 pieces [3][N] in the natural layout
-// (Eq. 11, first stage: the stencil of Eq. 6 plus the reaction).
-__global__ void __launch_bounds__(kPwThreads) rhs_pieces_kernel(const PwLaunch L) {
+// (Eq. 11, first stage: the stencil of Eq. 6 plus the reaction).  Each
+// iteration of a warp covers ZB consecutive z planes and issues all their
+// loads (the planes, the y neighbours in 3D, the x values beyond the warp's
+// run) before any arithmetic, so that a warp keeps several planes of
+// loads in flight; the planes z - 1 and z + ZB carry over.
+template <bool D3, int ZB>
+__global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_constant__ PwLaunch L) {
   __shared__ PwDesc sd;
-  const int s = stage_pw(L, &sd);
+  int lb;
+  const PwDesc* dp = block_desc(L, &sd, lb);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
-  int64_t unit = (int64_t)(blockIdx.x - __ldg(L.bstart + s)) * kPwWarps + warp;
-  if (unit >= (int64_t)sd.xsegs * ny * sd.zsegs) return;  // whole warps only
+  const int nx = dp->nx, ny = dp->ny, nz = dp->nz, xsegs = dp->xsegs;
+  int64_t unit = (int64_t)lb * kPwWarps + warp;
+  if (unit >= (int64_t)xsegs * ny * dp->zsegs) return;  // whole warps only
   const int y = (int)(unit % ny);
   unit /= ny;
-  const int xs = (int)(unit % sd.xsegs);
-  const int z0 = (int)(unit / sd.xsegs) * sd.zlen;
-  const int z1 = min(z0 + sd.zlen, nz);
+  const int xs = (int)(unit % xsegs);
+  const int z0 = (int)(unit / xsegs) * dp->zlen;
+  const int z1 = min(z0 + dp->zlen, nz);
   const int x0 = xs * kSegX + 4 * lane;
   const bool act = x0 < nx;
-  const bool d3 = sd.a.d == 3;
-  const int64_t sy = sd.sy, sz = sd.sz, N = sd.a.N;
-  const float* __restrict__ u = sd.u;
-  const float* __restrict__ v = sd.v;
-  __nv_bfloat16* wu = sd.wu;
-  __nv_bfloat16* wv = sd.wv;
+  const int64_t sy = dp->sy, sz = dp->sz, N = dp->a.N;
+  const float* __restrict__ u = dp->u;
+  const float* __restrict__ v = dp->v;
+  __nv_bfloat16* wu = dp->wu;
+  __nv_bfloat16* wv = dp->wv;
   // axis coefficients: x = mu 1, y = mu 2 (3D), z = mu 3 (3D) or mu 2 (2D)
-  const Coef cxu = coef(sd.a.A[0][0]), cxv = coef(sd.a.A[1][0]);
-  const Coef cyu = coef(sd.a.A[0][1]), cyv = coef(sd.a.A[1][1]);
-  const Coef czu = coef(sd.a.A[0][d3 ? 2 : 1]), czv = coef(sd.a.A[1][d3 ? 2 : 1]);
-  const ReactionT<float> rx = sd.a.rx;
+  const Coef cxu = coef(dp->a.A[0][0]), cxv = coef(dp->a.A[1][0]);
+  const Coef czu = coef(dp->a.A[0][D3 ? 2 : 1]), czv = coef(dp->a.A[1][D3 ? 2 : 1]);
+  Coef cyu = cxu, cyv = cxv;
+  if (D3) {
+    cyu = coef(dp->a.A[0][1]);
+    cyv = coef(dp->a.A[1][1]);
+  }
+  const ReactionT<float> rx = dp->a.rx;
   const int64_t col = (int64_t)y * sy + x0;
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 uc = act ? ld4(u + z0 * sz + col) : zero4;
-  float4 vc = act ? ld4(v + z0 * sz + col) : zero4;
-  float4 um = (act && z0 > 0) ? ld4(u + (z0 - 1) * sz + col) : zero4;
-  float4 vm = (act && z0 > 0) ? ld4(v + (z0 - 1) * sz + col) : zero4;
-  for (int z = z0; z < z1; ++z) {  // trip count uniform over the warp
-    const int64_t idx = z * sz + col;
-    const bool zp = act && z + 1 < nz;
-    const float4 up = zp ? ld4(u + idx + sz) : zero4;
-    const float4 vp = zp ? ld4(v + idx + sz) : zero4;
-    float4 uym = zero4, uyp = zero4, vym = zero4, vyp = zero4;
-    if (d3 && act) {
-      if (y > 0) {
-        uym = ld4(u + idx - sy);
-        vym = ld4(v + idx - sy);
-      }
-      if (y + 1 < ny) {
-        uyp = ld4(u + idx + sy);
-        vyp = ld4(v + idx + sy);
-      }
-    }
-    // x neighbours across lanes; the ends of the warp's run load their own
-    float ul = __shfl_up_sync(0xffffffffu, uc.w, 1), vl = __shfl_up_sync(0xffffffffu, vc.w, 1);
-    float ur = __shfl_down_sync(0xffffffffu, uc.x, 1), vr = __shfl_down_sync(0xffffffffu, vc.x, 1);
-    if (lane == 0) {
-      ul = (act && x0 > 0) ? u[idx - 1] : 0.f;
-      vl = (act && x0 > 0) ? v[idx - 1] : 0.f;
-    }
-    if (lane == 31) {
-      ur = (act && x0 + 4 < nx) ? u[idx + 4] : 0.f;
-      vr = (act && x0 + 4 < nx) ? v[idx + 4] : 0.f;
-    }
-    float ou[4], ov[4];
+  // run ends: lane 0 needs x0 - 1, lane 31 needs x0 + 4 (others come by shuffle)
+  const int64_t eoff = lane == 0 ? -1 : 4;
+  const bool eok = act && ((lane == 0 && x0 > 0) || (lane == 31 && x0 + 4 < nx));
+  float4 pu[ZB + 2], pv[ZB + 2];  // planes z - 1 .. z + ZB
+  pu[0] = (act && z0 > 0) ? ld4(u + (z0 - 1) * sz + col) : zero4;
+  pv[0] = (act && z0 > 0) ? ld4(v + (z0 - 1) * sz + col) : zero4;
+  pu[1] = act ? ld4(u + z0 * sz + col) : zero4;
+  pv[1] = act ? ld4(v + z0 * sz + col) : zero4;
+  for (int z = z0; z < z1; z += ZB) {  // trip counts uniform over the warp
+    float4 yum[ZB], yup[ZB], yvm[ZB], yvp[ZB];
+    float eu[ZB], ev[ZB];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int xi = x0 + j;
-      const float cu = el(uc, j), cv = el(vc, j);
-      const float lu = j == 0 ? ul : el(uc, j - 1), lv = j == 0 ? vl : el(vc, j - 1);
-      const float ru = j == 3 ? ur : el(uc, j + 1), rv = j == 3 ? vr : el(vc, j + 1);
-      float ku = tri_dir(lu, cu, ru, xi, nx, cxu.lo, cxu.up, cxu.b0, cxu.bn);
-      float kv = tri_dir(lv, cv, rv, xi, nx, cxv.lo, cxv.up, cxv.b0, cxv.bn);
-      if (d3) {
-        ku += tri_dir(el(uym, j), cu, el(uyp, j), y, ny, cyu.lo, cyu.up, cyu.b0, cyu.bn);
-        kv += tri_dir(el(vym, j), cv, el(vyp, j), y, ny, cyv.lo, cyv.up, cyv.b0, cyv.bn);
+    for (int j = 2; j < ZB + 2; ++j) {
+      const int zz = z + j - 1;
+      const bool ok = act && zz < nz;
+      pu[j] = ok ? ld4(u + zz * sz + col) : zero4;
+      pv[j] = ok ? ld4(v + zz * sz + col) : zero4;
+    }
+#pragma unroll
+    for (int q = 0; q < ZB; ++q) {
+      const int64_t idx = (int64_t)(z + q) * sz + col;
+      const bool ok = act && z + q < z1;
+      eu[q] = (ok && eok) ? u[idx + eoff] : 0.f;
+      ev[q] = (ok && eok) ? v[idx + eoff] : 0.f;
+      if (D3) {
+        yum[q] = (ok && y > 0) ? ld4(u + idx - sy) : zero4;
+        yvm[q] = (ok && y > 0) ? ld4(v + idx - sy) : zero4;
+        yup[q] = (ok && y + 1 < ny) ? ld4(u + idx + sy) : zero4;
+        yvp[q] = (ok && y + 1 < ny) ? ld4(v + idx + sy) : zero4;
       }
-      ku += tri_dir(el(um, j), cu, el(up, j), z, nz, czu.lo, czu.up, czu.b0, czu.bn);
-      kv += tri_dir(el(vm, j), cv, el(vp, j), z, nz, czv.lo, czv.up, czv.b0, czv.bn);
-      float gu, gv;
-      react<float>(rx, cu, cv, gu, gv);
-      ou[j] = ku + gu;
-      ov[j] = kv + gv;
     }
-    if (act) {
-      store_pieces4(wu, N, idx, ou);
-      store_pieces4(wv, N, idx, ov);
+#pragma unroll
+    for (int q = 0; q < ZB; ++q) {
+      const int zq = z + q;
+      if (zq >= z1) break;  // uniform
+      const float4 uc = pu[q + 1], vc = pv[q + 1];
+      float ul = __shfl_up_sync(0xffffffffu, uc.w, 1), vl = __shfl_up_sync(0xffffffffu, vc.w, 1);
+      float ur = __shfl_down_sync(0xffffffffu, uc.x, 1), vr = __shfl_down_sync(0xffffffffu, vc.x, 1);
+      if (lane == 0) {
+        ul = eu[q];
+        vl = ev[q];
+      }
+      if (lane == 31) {
+        ur = eu[q];
+        vr = ev[q];
+      }
+      float ou[4], ov[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int xi = x0 + j;
+        const float cu = el(uc, j), cv = el(vc, j);
+        const float lu = j == 0 ? ul : el(uc, j - 1), lv = j == 0 ? vl : el(vc, j - 1);
+        const float ru = j == 3 ? ur : el(uc, j + 1), rv = j == 3 ? vr : el(vc, j + 1);
+        float ku = tri_dir(lu, cu, ru, xi, nx, cxu.lo, cxu.up, cxu.b0, cxu.bn);
+        float kv = tri_dir(lv, cv, rv, xi, nx, cxv.lo, cxv.up, cxv.b0, cxv.bn);
+        if (D3) {
+          ku += tri_dir(el(yum[q], j), cu, el(yup[q], j), y, ny, cyu.lo, cyu.up, cyu.b0, cyu.bn);
+          kv += tri_dir(el(yvm[q], j), cv, el(yvp[q], j), y, ny, cyv.lo, cyv.up, cyv.b0, cyv.bn);
+        }
+        ku += tri_dir(el(pu[q], j), cu, el(pu[q + 2], j), zq, nz, czu.lo, czu.up, czu.b0, czu.bn);
+        kv += tri_dir(el(pv[q], j), cv, el(pv[q + 2], j), zq, nz, czv.lo, czv.up, czv.b0, czv.bn);
+        float gu, gv;
+        react<float>(rx, cu, cv, gu, gv);
+        ou[j] = ku + gu;
+        ov[j] = kv + gv;
+      }
+      if (act) {
+        const int64_t idx = (int64_t)zq * sz + col;
+        store_pieces4(wu, N, idx, ou);
+        store_pieces4(wv, N, idx, ov);
+      }
     }
-    um = uc;
-    uc = up;
-    vm = vc;
-    vc = vp;
+    pu[0] = pu[ZB];
+    pv[0] = pv[ZB];
+    pu[1] = pu[ZB + 1];
+    pv[1] = pv[ZB + 1];
   }
 }
+constexpr int kZB2 = 4, kZB3 = 1;  // planes per iteration: 2D, 3D
 
 // Elementwise kernels: thread t of a block handles float4 groups
 // base + k * kPwThreads + t, k < kFlatVec; loads are issued before any store.
 #define FLAT_PROLOGUE                                                            \
-  __shared__ PwDesc sd;                                                          \
-  const int s = stage_pw(L, &sd);                                                \
+  __shared__ PwDesc sdesc;                                                       \
+  int lb;                                                                        \
+  const PwDesc& sd = *block_desc(L, &sdesc, lb);                                 \
   const int64_t N = sd.a.N, N4 = N / 4;                                          \
-  const int64_t g0 = (int64_t)(blockIdx.x - __ldg(L.bstart + s)) * (kFlatPerBlock / 4) + threadIdx.x;
+  const int64_t g0 = (int64_t)lb * (kFlatPerBlock / 4) + threadIdx.x;
 
 // D^c = G^c(U2, V2) - G^c(U, V) written as BF16 pieces [3][N] (Eq. 11,
 // second stage).
-__global__ void __launch_bounds__(kPwThreads) rdiff_pieces_kernel(const PwLaunch L) {
+__global__ void __launch_bounds__(kPwThreads) rdiff_pieces_kernel(const __grid_constant__ PwLaunch L) {
   FLAT_PROLOGUE
   const ReactionT<float> rx = sd.a.rx;
   float4 a0[kFlatVec], a1[kFlatVec], a2[kFlatVec], a3[kFlatVec];
@@ -1258,7 +1298,7 @@ __global__ void __launch_bounds__(kPwThreads) rdiff_pieces_kernel(const PwLaunch
 
 // Lawson2b (Eq. 7) first pointwise stage, also used for the second:
 // W^c = U^c + factor tau G^c(U, V) as BF16 pieces [3][N].
-__global__ void __launch_bounds__(kPwThreads) lawson_pre_pieces_kernel(const PwLaunch L,
+__global__ void __launch_bounds__(kPwThreads) lawson_pre_pieces_kernel(const __grid_constant__ PwLaunch L,
                                                                        float factor) {
   FLAT_PROLOGUE
   const ReactionT<float> rx = sd.a.rx;
@@ -1291,7 +1331,7 @@ __global__ void __launch_bounds__(kPwThreads) lawson_pre_pieces_kernel(const PwL
 }
 
 // Lawson2b last stage: u += factor tau G(u2, v2) in FP32, in place.
-__global__ void __launch_bounds__(kPwThreads) lawson_post_kernel(const PwLaunch L, float factor) {
+__global__ void __launch_bounds__(kPwThreads) lawson_post_kernel(const __grid_constant__ PwLaunch L, float factor) {
   FLAT_PROLOGUE
   const ReactionT<float> rx = sd.a.rx;
   const float sc = factor * sd.tau;
@@ -1552,6 +1592,7 @@ struct TcState {
   PwDesc* d_pw;
   int* d_bstart;   // rhs {0, blocks}, rdiff {0, blocks}
   std::vector<TcPassDesc> h_desc;  // host copies of d_desc
+  PwDesc h_pw;                      // host copy of d_pw
   int units[8];
   int rhs_blocks, rdiff_blocks;
   void* bound_u;
@@ -1610,10 +1651,17 @@ static PwGeom pw_geom(const TcState* S, int num_sms) {
   g.sy = S->n[0];
   g.sz = d3 ? S->n[0] * S->n[1] : S->n[0];
   g.xsegs = (g.nx + kSegX - 1) / kSegX;
-  const int64_t rows = (int64_t)g.xsegs * g.ny * g.nz;
-  const int64_t want = (int64_t)num_sms * 48;  // warps for about three waves of 16 per SM
-  g.zlen = 1;
-  while (g.zlen < 16 && rows / (2 * g.zlen) >= want) g.zlen *= 2;
+  // z runs: a multiple of the planes per iteration, as long as leaves about
+  // four waves of 16 warps per SM (whole waves balance the SMs; each warp
+  // keeps several planes of loads in flight), at most 64 planes
+  const int zb = d3 ? kZB3 : kZB2;
+  const int64_t cols = (int64_t)g.xsegs * g.ny;
+  const int64_t want = (int64_t)num_sms * 16 * 4;
+  int64_t zl = (cols * g.nz + want - 1) / want;
+  zl = ((zl + zb - 1) / zb) * zb;
+  if (zl < zb) zl = zb;
+  if (zl > 64) zl = 64;
+  g.zlen = (int)zl;
   g.zsegs = (g.nz + g.zlen - 1) / g.zlen;
   return g;
 }
@@ -1833,6 +1881,7 @@ cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
   if (e != cudaSuccess) return e;
   S->h_desc = hd;
+  S->h_pw = pw;
   S->bound_u = u;
   S->bound_v = v;
   return cudaSuccess;
@@ -1865,7 +1914,11 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
     switch (op.kind) {
       case kOpRhs:
         e = timed_kernel(ctl, KC_RHS, N * 2.0 * (6.0 * G.d + 10.0), N * (8.0 + 12.0), [&] {
-          return launch_k(rhs_pieces_kernel, dim3(G.rhs_blocks), dim3(kPwThreads), 0, st, G.rhs);
+          if (G.d == 3)
+            return launch_k(rhs_pieces_kernel<true, kZB3>, dim3(G.rhs_blocks), dim3(kPwThreads), 0,
+                            st, G.rhs);
+          return launch_k(rhs_pieces_kernel<false, kZB2>, dim3(G.rhs_blocks), dim3(kPwThreads), 0,
+                          st, G.rhs);
         });
         break;
       case kOpRdiff:
@@ -1943,8 +1996,9 @@ cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
     G.units[p] = S->units[p];
     pass_work(S, S->passes[p], G.flops[p], G.bytes[p]);
   }
-  G.rhs = PwLaunch{S->d_pw, S->d_bstart, 1};
-  G.flat = PwLaunch{S->d_pw, S->d_bstart + 2, 1};
+  memset(&G.rhs, 0, sizeof(G.rhs));
+  G.rhs.one = S->h_pw;  // one solve: the descriptor travels in the launch
+  G.flat = G.rhs;
   G.rhs_blocks = S->rhs_blocks;
   G.flat_blocks = S->rdiff_blocks;
   G.err = S->err;
@@ -2155,8 +2209,12 @@ static cudaError_t batch_step_direct(adr_batch B, int64_t nsteps) {
     G.flops[p] = B->flops[p];
     G.bytes[p] = B->bytes[p];
   }
-  G.rhs = PwLaunch{B->d_pw, B->d_bstart, B->nsolves};
-  G.flat = PwLaunch{B->d_pw, B->d_bstart + (B->nsolves + 1), B->nsolves};
+  memset(&G.rhs, 0, sizeof(G.rhs));
+  G.rhs.desc = B->d_pw;
+  G.rhs.bstart = B->d_bstart;
+  G.rhs.nsolves = B->nsolves;
+  G.flat = G.rhs;
+  G.flat.bstart = B->d_bstart + (B->nsolves + 1);
   G.rhs_blocks = B->rhs_blocks;
   G.flat_blocks = B->rdiff_blocks;
   G.err = B->d_err;
