@@ -482,7 +482,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="fhn1024")
-    ap.add_argument("--precision", default="bf16x3", choices=sorted(PREC))
+    ap.add_argument("--precision", default=None, choices=sorted(PREC),
+                    help="default: fp64 for schnak64 (the plain-method FP64 workload), else bf16x3")
     ap.add_argument("--compare", default="fp32",
                     help="also time this precision on the same workload ('none' to skip)")
     ap.add_argument("--time-steps", type=int, default=None,
@@ -493,6 +494,8 @@ def main():
     ap.add_argument("--requests", type=int, default=400, help="serving workload: request count")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device-memory budget")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "fp64" if args.workload == "schnak64" else "bf16x3"
 
     if args.impl == "reference":
         reference_arm(args)
