@@ -29,6 +29,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "adr_internal.h"
 #include "pointwise.cuh"
 
@@ -1586,13 +1588,10 @@ struct TcState {
   int scheme;
   std::vector<TcPass> passes;
   std::vector<TcOp> ops;
-  // descriptors of this plan as a group of one, bound to (bound_u, bound_v)
-  TcPassDesc* d_desc;
-  int* d_ustart;   // [passes][2]
-  PwDesc* d_pw;
-  int* d_bstart;   // rhs {0, blocks}, rdiff {0, blocks}
-  std::vector<TcPassDesc> h_desc;  // host copies of d_desc
-  PwDesc h_pw;                      // host copy of d_pw
+  // descriptors of this plan as a group of one, bound to (bound_u, bound_v);
+  // they travel in the kernel parameters of every launch
+  std::vector<TcPassDesc> h_desc;  // [passes]
+  PwDesc h_pw;
   int units[8];
   int rhs_blocks, rdiff_blocks;
   void* bound_u;
@@ -1839,49 +1838,24 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
   for (int p = 0; p < np; ++p) S->units[p] = units_of(S, S->passes[p], bn);
   S->rhs_blocks = rhs_blocks_of(S);
   S->rdiff_blocks = rdiff_blocks_of(S);
-  e = alloc((void**)&S->d_desc, sizeof(TcPassDesc) * np);
-  if (e != cudaSuccess) return e;
-  e = alloc((void**)&S->d_ustart, sizeof(int) * 2 * np);
-  if (e != cudaSuccess) return e;
-  e = alloc((void**)&S->d_pw, sizeof(PwDesc));
-  if (e != cudaSuccess) return e;
-  e = alloc((void**)&S->d_bstart, sizeof(int) * 4);
-  if (e != cudaSuccess) return e;
-  std::vector<int> us(2 * np);
-  for (int p = 0; p < np; ++p) {
-    us[2 * p] = 0;
-    us[2 * p + 1] = S->units[p];
-  }
-  e = cudaMemcpyAsync(S->d_ustart, us.data(), sizeof(int) * 2 * np, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return e;
-  const int bs[4] = {0, S->rhs_blocks, 0, S->rdiff_blocks};
-  e = cudaMemcpyAsync(S->d_bstart, bs, sizeof(bs), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(s);  // the host arrays above go out of scope
+  e = cudaStreamSynchronize(s);  // the split matrices are complete
   if (e != cudaSuccess) return e;
   S->bound_u = S->bound_v = nullptr;
   t->ready = 1;
   return cudaSuccess;
 }
 
-// Point this plan's descriptors at the state buffers (u, v).  Called before
-// stepping (outside any stream capture); a no-op when already bound.
+// Point this plan's descriptors at the state buffers (u, v).  The
+// descriptors are host copies passed by value in every launch, so binding
+// neither copies to the device nor synchronises.  A no-op when already bound.
 cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   TcState* S = (TcState*)t->work[0];
   if (!S || !t->ready) return cudaErrorNotSupported;
   if (S->bound_u == u && S->bound_v == v) return cudaSuccess;
   const int np = (int)S->passes.size();
-  std::vector<TcPassDesc> hd(np);
-  for (int p = 0; p < np; ++p) hd[p] = make_desc(S, P, S->passes[p], (float*)u, (float*)v);
-  const PwDesc pw = make_pw(S, P, (float*)u, (float*)v);
-  cudaError_t e = cudaMemcpyAsync(S->d_desc, hd.data(), sizeof(TcPassDesc) * np,
-                                  cudaMemcpyHostToDevice, P->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(S->d_pw, &pw, sizeof(pw), cudaMemcpyHostToDevice, P->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
-  if (e != cudaSuccess) return e;
-  S->h_desc = hd;
-  S->h_pw = pw;
+  S->h_desc.resize(np);
+  for (int p = 0; p < np; ++p) S->h_desc[p] = make_desc(S, P, S->passes[p], (float*)u, (float*)v);
+  S->h_pw = make_pw(S, P, (float*)u, (float*)v);
   S->bound_u = u;
   S->bound_v = v;
   return cudaSuccess;
@@ -1945,10 +1919,11 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
         if (G.hdesc) {
           L.one = G.hdesc[p];
           L.desc = nullptr;
+          L.ustart = nullptr;
         } else {
           L.desc = G.desc + (size_t)p * G.nsolves;
+          L.ustart = G.ustart + (size_t)p * (G.nsolves + 1);
         }
-        L.ustart = G.ustart + (size_t)p * (G.nsolves + 1);
         L.nsolves = G.nsolves;
         L.nunits = G.units[p];
         L.err = G.err;
@@ -1989,9 +1964,9 @@ cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   G.num_sms = S->slots;
   G.nsolves = 1;
   fill_ops(G, S);
-  G.desc = S->d_desc;
+  G.desc = nullptr;
   G.hdesc = S->h_desc.data();
-  G.ustart = S->d_ustart;
+  G.ustart = nullptr;
   for (int p = 0; p < G.np; ++p) {
     G.units[p] = S->units[p];
     pass_work(S, S->passes[p], G.flops[p], G.bytes[p]);
@@ -2043,22 +2018,127 @@ struct adr_batch_s {
   // CUDA graph of kBatchChunk steps
   cudaStream_t cap;
   cudaGraphExec_t gexec;
+  cudaGraphExec_t gexec_timed;   // timing mode: with event-record nodes
   int64_t g_launches;
   std::vector<void*> allocs;
 };
 
 static constexpr int64_t kBatchChunk = 16;
 
+// Uploads of descriptor tables that never synchronise: the bytes are staged
+// in a page-locked ring (one per process) and copied asynchronously on the
+// caller's stream.  An event recorded after each copy guards its slice, and
+// a slice is reused only once that event has completed.
+class PinnedRing {
+ public:
+  cudaError_t upload(void* dst, const void* src, size_t n, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(mu_);
+    const size_t n16 = (n + 15) & ~(size_t)15;
+    cudaError_t e = reserve(n16);
+    if (e != cudaSuccess) return e;
+    if (head_ + n16 > cap_) head_ = 0;
+    // retire finished slices; wait for the unfinished ones this slice overlaps
+    for (size_t i = 0; i < pend_.size();) {
+      Slice& q = pend_[i];
+      const bool overlap = q.lo < head_ + n16 && q.hi > head_;
+      if (cudaEventQuery(q.ev) == cudaSuccess || (overlap && cudaEventSynchronize(q.ev) == cudaSuccess)) {
+        events_.push_back(q.ev);
+        pend_[i] = pend_.back();
+        pend_.pop_back();
+      } else {
+        cudaGetLastError();
+        if (overlap) return cudaErrorUnknown;
+        ++i;
+      }
+    }
+    memcpy(buf_ + head_, src, n);
+    e = cudaMemcpyAsync(dst, buf_ + head_, n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t ev;
+    if (!events_.empty()) {
+      ev = events_.back();
+      events_.pop_back();
+    } else if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+      return e;
+    }
+    if ((e = cudaEventRecord(ev, s)) != cudaSuccess) return e;
+    pend_.push_back(Slice{head_, head_ + n16, ev});
+    head_ += n16;
+    return cudaSuccess;
+  }
+
+ private:
+  struct Slice {
+    size_t lo, hi;
+    cudaEvent_t ev;
+  };
+  // Room for a slice of n bytes (grows rarely: waits for every pending copy).
+  cudaError_t reserve(size_t n) {
+    if (n <= cap_) return cudaSuccess;
+    for (Slice& q : pend_) {
+      cudaEventSynchronize(q.ev);
+      events_.push_back(q.ev);
+    }
+    pend_.clear();
+    size_t cap = cap_ ? 2 * cap_ : ((size_t)1 << 20);
+    while (cap < n) cap *= 2;
+    uint8_t* nb = nullptr;
+    cudaError_t e = cudaHostAlloc((void**)&nb, cap, cudaHostAllocDefault);
+    if (e != cudaSuccess) return e;
+    if (buf_) cudaFreeHost(buf_);
+    buf_ = nb;
+    cap_ = cap;
+    head_ = 0;
+    return cudaSuccess;
+  }
+  std::mutex mu_;
+  uint8_t* buf_ = nullptr;
+  size_t cap_ = 0, head_ = 0;
+  std::vector<Slice> pend_;
+  std::vector<cudaEvent_t> events_;
+};
+PinnedRing g_upload_ring;
+
+// The library's pool for batch descriptors on the current device (created
+// once per device; freed memory stays in the pool).  Null on failure.
+static cudaMemPool_t batch_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+// Frees nothing synchronously: graph and stream destruction are deferred by
+// CUDA until their work completes, and the device arrays are returned to
+// the stream-ordered pool after the batch's last launch on its stream.
 static void batch_free(adr_batch B) {
   if (!B) return;
+  cudaStream_t st = B->ctl ? B->ctl->stream : nullptr;
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);
+  if (B->gexec_timed) cudaGraphExecDestroy(B->gexec_timed);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  for (void* q : B->allocs) cudaFreeAsync(q, st);
   if (B->ctl) {
-    cudaStreamSynchronize(B->ctl->stream);
     for (cudaEvent_t e : B->ctl->event_pool) cudaEventDestroy(e);
     delete B->ctl;
   }
-  if (B->gexec) cudaGraphExecDestroy(B->gexec);
-  if (B->cap) cudaStreamDestroy(B->cap);
-  for (void* q : B->allocs) cudaFree(q);
   delete B;
 }
 
@@ -2096,8 +2176,17 @@ extern "C" adr_status adr_batch_create(const adr_plan* plans, int count, void* s
   }
   B->grouped = grouped ? 1 : 0;
   cudaError_t e = cudaSuccess;
+  // stream-ordered device memory from the library's own pool (one per
+  // device, keeping freed memory): creating a batch never synchronises, and
+  // a server that creates and destroys batches all the time reuses memory.
+  cudaMemPool_t pool = batch_pool();
+  if (!pool) {
+    set_error("adr_batch_create: no memory pool");
+    batch_free(B);
+    return ADR_ECUDA;
+  }
   auto alloc = [&](void** q, size_t bytes) -> cudaError_t {
-    cudaError_t r = cudaMalloc(q, bytes < 16 ? 16 : bytes);
+    cudaError_t r = cudaMallocFromPoolAsync(q, bytes < 16 ? 16 : bytes, pool, (cudaStream_t)stream);
     if (r == cudaSuccess) B->allocs.push_back(*q);
     return r;
   };
@@ -2144,10 +2233,10 @@ extern "C" adr_status adr_batch_create(const adr_plan* plans, int count, void* s
         (e = alloc((void**)&B->d_pw, sizeof(PwDesc) * S_)) == cudaSuccess &&
         (e = alloc((void**)&B->d_bstart, sizeof(int) * bs.size())) == cudaSuccess &&
         (e = alloc((void**)&B->d_err, sizeof(int))) == cudaSuccess)
-      e = cudaMemcpy(B->d_ustart, us.data(), sizeof(int) * us.size(), cudaMemcpyHostToDevice);
+      e = g_upload_ring.upload(B->d_ustart, us.data(), sizeof(int) * us.size(), (cudaStream_t)stream);
     if (e == cudaSuccess)
-      e = cudaMemcpy(B->d_bstart, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(B->d_err, 0, sizeof(int));
+      e = g_upload_ring.upload(B->d_bstart, bs.data(), sizeof(int) * bs.size(), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_err, 0, sizeof(int), (cudaStream_t)stream);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -2178,18 +2267,20 @@ static cudaError_t batch_bind(adr_batch B, void* const* u, void* const* v) {
       hd[(size_t)p * S_ + i] = make_desc(S, P, S->passes[p], (float*)u[i], (float*)v[i]);
     hp[i] = make_pw(S, P, (float*)u[i], (float*)v[i]);
   }
-  cudaError_t e = cudaMemcpyAsync(B->d_desc, hd.data(), sizeof(TcPassDesc) * hd.size(),
-                                  cudaMemcpyHostToDevice, B->ctl->stream);
+  cudaError_t e = g_upload_ring.upload(B->d_desc, hd.data(), sizeof(TcPassDesc) * hd.size(),
+                                       B->ctl->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(B->d_pw, hp.data(), sizeof(PwDesc) * hp.size(), cudaMemcpyHostToDevice,
-                        B->ctl->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(B->ctl->stream);
+    e = g_upload_ring.upload(B->d_pw, hp.data(), sizeof(PwDesc) * hp.size(), B->ctl->stream);
   if (e != cudaSuccess) return e;
   B->bound_u.assign(u, u + S_);
   B->bound_v.assign(v, v + S_);
   if (B->gexec) {  // the graph's descriptors now describe new buffers; recapture
     cudaGraphExecDestroy(B->gexec);
     B->gexec = nullptr;
+  }
+  if (B->gexec_timed) {
+    cudaGraphExecDestroy(B->gexec_timed);
+    B->gexec_timed = nullptr;
   }
   return cudaSuccess;
 }
@@ -2259,11 +2350,17 @@ extern "C" adr_status adr_batch_step(adr_batch batch, void* const* u, void* cons
   }
   adr_plan_s* ctl = B->ctl;
   int64_t done = 0;
-  if (ctl->use_graphs && !ctl->timing && nsteps >= kBatchChunk) {
-    if (!B->gexec) {
+  if (ctl->use_graphs && nsteps >= kBatchChunk) {
+    // timing mode replays a second graph with event-record nodes around
+    // every kernel and harvests the times after each replay
+    const bool timed = ctl->timing;
+    cudaGraphExec_t& ge = timed ? B->gexec_timed : B->gexec;
+    if (!ge) {
       const int64_t l0 = ctl->launches, s0 = ctl->steps;
       cudaStream_t saved = ctl->stream;
       ctl->stream = B->cap;
+      if (timed) ctl->graph_timed.clear();
+      ctl->capturing = true;
       cudaGraph_t g = nullptr;
       cudaError_t ce = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal);
       if (ce == cudaSuccess) {
@@ -2271,27 +2368,36 @@ extern "C" adr_status adr_batch_step(adr_batch batch, void* const* u, void* cons
         cudaError_t e2 = cudaStreamEndCapture(B->cap, &g);
         ce = e1 != cudaSuccess ? e1 : e2;
       }
+      ctl->capturing = false;
       ctl->stream = saved;
       B->g_launches = ctl->launches - l0;
       ctl->launches = l0;
       ctl->steps = s0;
-      if (ce == cudaSuccess && g) ce = cudaGraphInstantiate(&B->gexec, g, 0);
+      if (ce == cudaSuccess && g) ce = cudaGraphInstantiate(&ge, g, 0);
       if (g) cudaGraphDestroy(g);
       if (ce != cudaSuccess) {
         cudaGetLastError();
-        B->gexec = nullptr;
+        ge = nullptr;
         ctl->use_graphs = 0;
       }
     }
-    if (B->gexec) {
+    if (ge) {
       for (; done + kBatchChunk <= nsteps; done += kBatchChunk) {
-        e = cudaGraphLaunch(B->gexec, ctl->stream);
+        e = cudaGraphLaunch(ge, ctl->stream);
         if (e != cudaSuccess) {
           set_error(std::string("adr_batch_step: cudaGraphLaunch: ") + cudaGetErrorString(e));
           return ADR_ECUDA;
         }
         ctl->launches += B->g_launches;
         ctl->steps += kBatchChunk;
+        if (timed) {
+          e = cudaStreamSynchronize(ctl->stream);
+          if (e != cudaSuccess) {
+            set_error(std::string("adr_batch_step: ") + cudaGetErrorString(e));
+            return ADR_ECUDA;
+          }
+          harvest_timing(ctl, ctl->graph_timed);
+        }
       }
     }
   }
@@ -2305,6 +2411,11 @@ extern "C" adr_status adr_batch_step(adr_batch batch, void* const* u, void* cons
 
 extern "C" adr_status adr_batch_set_timing(adr_batch batch, int enable) {
   if (!batch) return ADR_EINVAL;
+  if (batch->gexec_timed) {  // its event nodes use events the plan hands out again
+    cudaStreamSynchronize(batch->ctl->stream);
+    cudaGraphExecDestroy(batch->gexec_timed);
+    batch->gexec_timed = nullptr;
+  }
   adr_status st = adr_plan_set_timing(batch->ctl, enable);
   if (st == ADR_OK && batch->d_err) {
     if (cudaMemset(batch->d_err, 0, sizeof(int)) != cudaSuccess) return ADR_ECUDA;

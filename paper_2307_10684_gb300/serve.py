@@ -11,8 +11,11 @@ The server:
   advances all active solves: those with at least ``chunk`` steps left
   together, one grouped batch per dimension (``adr_batch_step``), the
   others individually;
-* retires finished solves (results copied to host, memory returned) and
-  records each request's latency, completion minus arrival.
+* retires finished solves without stalling the stepping loop: the results
+  are copied to page-locked host memory asynchronously, and a request is
+  complete when its copy event has fired (its latency is that moment minus
+  its arrival); plans are destroyed on a separate thread, because freeing
+  device memory synchronises the device.
 
 PyTorch supplies device memory, streams and events; every step runs in the
 library's kernels through the C ABI.
@@ -69,15 +72,17 @@ class Server:
     """One-GPU continuous-batching ETD2RKds server.
 
     budget_bytes: device memory the server may hold for plans and states.
-    chunk: steps per tick for batched solves.
+    chunk: steps per tick for batched solves (32 = one captured graph chunk).
+    planners: threads that build plans (FP64 matrix functions) concurrently.
     """
 
-    def __init__(self, budget_bytes: int, chunk: int = 16, max_active: int = 1024,
-                 keep_results: bool = False, keep_ids=None):
+    def __init__(self, budget_bytes: int, chunk: int = 32, max_active: int = 1024,
+                 keep_results: bool = False, keep_ids=None, planners: int = 3):
         import torch
         self.device = torch.cuda.current_device()
         self.budget = int(budget_bytes)
         self.chunk = int(chunk)
+        self.planners = max(1, int(planners))
         self.max_active = int(max_active)
         self.keep = keep_results
         self.keep_ids = set(keep_ids or ())
@@ -108,6 +113,18 @@ class Server:
             except Exception as exc:  # reported, request dropped
                 outq.put((req, None, nbytes, None, exc))
 
+    # ---------------------------------------------------------------- reaper
+    @staticmethod
+    def _reaper(q: "queue.Queue"):
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            try:
+                item.close()
+            except Exception:  # a failed teardown must not stop the server
+                pass
+
     # ---------------------------------------------------------------- run
     def run(self, requests: Sequence[Request], clock: Optional[Callable[[], float]] = None):
         import torch
@@ -116,8 +133,14 @@ class Server:
         waiting: "collections.deque[Tuple[Request, int]]" = collections.deque()
         inq: "queue.Queue" = queue.Queue()
         outq: "queue.Queue" = queue.Queue()
-        planner = threading.Thread(target=self._planner, args=(inq, outq), daemon=True)
-        planner.start()
+        planners = [threading.Thread(target=self._planner, args=(inq, outq), daemon=True)
+                    for _ in range(self.planners)]
+        for th in planners:
+            th.start()
+        reapq: "queue.Queue" = queue.Queue()
+        reaper = threading.Thread(target=self._reaper, args=(reapq,), daemon=True)
+        reaper.start()
+        retiring: List[Tuple[_Slot, object, object, object]] = []  # (slot, event, host u, host v)
         t0 = time.perf_counter()
         now = clock or (lambda: time.perf_counter() - t0)
         in_planning = 0
@@ -125,6 +148,21 @@ class Server:
         total = len(reqs)
         while len(self.results) < total:
             t = now()
+            # solves whose result copies have landed are complete
+            if retiring:
+                still = []
+                for s, ev, hu, hv in retiring:
+                    if not ev.query():
+                        still.append((s, ev, hu, hv))
+                        continue
+                    res = Result(s.req.rid, s.req.arrival, s.admitted, now(), s.req.nsteps,
+                                 int(s.u.numel()))
+                    if hu is not None:
+                        res.u, res.v = hu, hv
+                    self.results[s.req.rid] = res
+                    self.used -= s.nbytes   # its memory goes back once the reaper frees it
+                    reapq.put(s.plan)
+                retiring = still
             # arrivals join the waiting queue with their memory demand
             while arrivals and arrivals[0].arrival <= t:
                 r = arrivals.popleft()
@@ -159,7 +197,7 @@ class Server:
                 self.active.append(_Slot(r, plan, u, v, now(), nbytes))
                 changed = True
             if not self.active:
-                if in_planning == 0 and not waiting and arrivals:
+                if in_planning == 0 and not waiting and arrivals and not retiring:
                     time.sleep(max(0.0, min(0.002, arrivals[0].arrival - now())))
                 else:
                     time.sleep(0.0005)
@@ -174,6 +212,12 @@ class Server:
                     self.stats["tail_steps"] += s.left
                     s.left = 0
             for d, slots in groups.items():
+                if len(slots) == 1:  # a group of one steps its plan (and its graph) directly
+                    s = slots[0]
+                    s.plan.step(s.u, s.v, self.chunk)
+                    s.left -= self.chunk
+                    self.stats["single_ticks"] += 1
+                    continue
                 key = tuple(id(s) for s in slots)
                 if d not in batches or batches[d][0] != key:
                     if d in batches:
@@ -184,31 +228,31 @@ class Server:
                 for s in slots:
                     s.left -= self.chunk
                 self.stats["ticks"] += 1
-            # retire finished solves
+            # retire finished solves: copy results out asynchronously
             done = [s for s in self.active if s.left == 0]
-            if done:
+            for s in done:
+                hu = hv = None
+                if self.keep or s.req.rid in self.keep_ids:
+                    hu = torch.empty(s.u.shape, dtype=s.u.dtype, pin_memory=True)
+                    hv = torch.empty(s.v.shape, dtype=s.v.dtype, pin_memory=True)
+                    hu.copy_(s.u, non_blocking=True)
+                    hv.copy_(s.v, non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(self.stream)
-                ev.synchronize()   # the server's stream only: planning goes on
-                for s in done:
-                    fin = now()
-                    res = Result(s.req.rid, s.req.arrival, s.admitted, fin, s.req.nsteps,
-                                 int(s.u.numel()))
-                    if self.keep or s.req.rid in self.keep_ids:
-                        res.u = s.u.cpu()
-                        res.v = s.v.cpu()
-                    self.results[s.req.rid] = res
-                    self.active.remove(s)
-                    self.used -= s.nbytes
-                    for d in list(batches):
-                        if any(id(s) == k for k in batches[d][0]):
-                            batches[d][1].close()
-                            del batches[d]
-                    s.plan.close()
-        inq.put(None)
-        planner.join(timeout=10)
+                retiring.append((s, ev, hu, hv))
+                self.active.remove(s)
+                for d in list(batches):
+                    if any(id(s) == k for k in batches[d][0]):
+                        batches[d][1].close()   # stream-ordered; does not synchronise
+                        del batches[d]
+        for _ in planners:
+            inq.put(None)
+        for th in planners:
+            th.join(timeout=10)
         for _, b in batches.values():
             b.close()
+        reapq.put(None)
+        reaper.join(timeout=60)
         return [self.results[r.rid] for r in reqs]
 
 
