@@ -120,3 +120,43 @@ def test_batch_of_fp32_plans_steps_each(adr):
                                   Ur, Vr) <= TOL
     for plan in plans:
         plan.close()
+
+
+def test_batch_churn_without_synchronisation(adr):
+    """Batches created, stepped and destroyed back to back on one stream with
+    no synchronisation in between (descriptor uploads through the page-locked
+    ring, stream-ordered batch memory, deferred teardown): every solve equals
+    the same solve stepped alone.  The loop uploads more descriptor bytes than
+    the ring's first capacity, so the ring wraps and waits for its events."""
+    import torch
+    probs = mixed_problems(d=2, count=6)
+    plans = [adr.Plan(p) for p in probs]
+    us, vs, inits = states(adr, probs)
+    ref = []
+    for p, pl, (u0, v0) in zip(probs, plans, inits):
+        u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+        pl.step(u, v, 40)
+        ref.append((u, v))
+    steps_done = [0] * len(probs)
+    rounds = 0
+    for r in range(120):  # about 120 x 5 x (4 passes x 768 B + ...) > 1 MB of uploads
+        members = [i for i in range(len(probs)) if (i + r) % 6 != 0]
+        members = [i for i in members if steps_done[i] < 40]
+        if len(members) < 2:
+            break
+        b = adr.Batch([plans[i] for i in members])
+        b.step([us[i] for i in members], [vs[i] for i in members], 1)
+        for i in members:
+            steps_done[i] += 1
+        b.close()
+        rounds += 1
+    for i, pl in enumerate(plans):
+        if steps_done[i] < 40:
+            pl.step(us[i], vs[i], 40 - steps_done[i])
+    torch.cuda.synchronize()
+    assert rounds > 30
+    for i in range(len(probs)):
+        assert torch.equal(us[i], ref[i][0]) and torch.equal(vs[i], ref[i][1]), i
+    for pl in plans:
+        pl.close()
