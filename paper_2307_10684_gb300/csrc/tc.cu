@@ -52,7 +52,7 @@ struct TcCfg {
   static constexpr int TILE_B = BN * SW;             // bytes of one B piece tile
   static constexpr int STAGE = kPieces * (TILE_A + TILE_B);
   static constexpr int STAGES = (224 * 1024) / STAGE > 8 ? 8 : (224 * 1024) / STAGE;
-  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 512;  // + alignment, barriers
   static constexpr int TMEM_COLS = 2 * BN;           // two accumulators
   static constexpr uint32_t LAYOUT = SW == 128 ? 2u : 4u;   // descriptor swizzle code
   static constexpr uint32_t SBO = 8 * SW;            // bytes between 8-row groups
@@ -96,6 +96,26 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity) 
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
     __nanosleep(256);
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+// Wait with acquire semantics at cluster scope (the phase is completed by
+// arrivals from the other CTA of the cluster); false after kWaitNs.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait_cluster(bar, parity)) {
     if (globaltimer() - t0 > kWaitNs) return false;
   }
   return true;
@@ -292,7 +312,9 @@ enum TcMode : int {
   kPieces3 = 0,   // out pieces [3][N][M] of acc
   kStage1 = 1,    // pair units only: U2 = U + alpha acc_u, V2 = V + alpha acc_v
                   // (FP32 out) and D = G(U2, V2) - G(U, V) as pieces
-  kAxpy = 2       // out = base + alpha acc (FP32)
+  kAxpy = 2,      // out = base + alpha acc (FP32)
+  kStage1X = 3    // as kStage1 with one component per CTA: the two CTAs of a
+                  // cluster hold u and v of the same tile and exchange U2, V2
 };
 
 // The six piece pairs (i, j), A piece i times B piece j, grouped by A piece
@@ -334,6 +356,10 @@ __device__ __forceinline__ Unit decode_unit(const TcLaunch& L, int u) {
   if (w.d->pair) {
     w.c_lo = 0;
     w.c_hi = 2;
+  } else if (w.d->mode == kStage1X) {  // unit 2 t + c: component c of tile t
+    w.c_lo = r & 1;
+    w.c_hi = w.c_lo + 1;
+    r >>= 1;
   } else {
     const int per = w.d->tiles_m * w.d->tiles_n;
     w.c_lo = r / per;
@@ -345,6 +371,26 @@ __device__ __forceinline__ Unit decode_unit(const TcLaunch& L, int u) {
   return w;
 }
 
+// ---- cluster helpers (CTA rank, addresses in the other CTA, barriers)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
 // Persistent kernel.  CTA b handles units b, b + gridDim.x, ... of the
 // launch's unit list (all solves' tiles, solve-major, n-tile fastest within
 // a solve so that CTAs running together share A tiles in L2).  For each unit
@@ -354,7 +400,14 @@ __device__ __forceinline__ Unit decode_unit(const TcLaunch& L, int u) {
 // Epilogue warp w owns TMEM lane quarter w % 4 and half (w - 2) / 4 of the
 // columns; it prefetches its FP32 base values two 16-column chunks ahead,
 // starting before the accumulator is ready.
-template <int SW, int BN, bool PAIR>
+//
+// XCHG instantiation (launched in clusters of two, for the kStage1X pass):
+// CTA 2k + c holds component c of the tile, forms U2 (or V2) in its
+// epilogue, stores it, then each epilogue warp signals its counterpart in
+// the other CTA through that CTA's `xready` barrier and waits for its own;
+// it then reads the other component's base and stage values (L2) and writes
+// its component of D = G(U2, V2) - G(U, V) as BF16 pieces.
+template <int SW, int BN, bool PAIR, bool XCHG>
 __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_constant__ TcLaunch L) {
   using C = TcCfg<SW, BN>;
   static_assert(4 * BN <= 512, "four accumulators must fit in TMEM");
@@ -367,6 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   int* abort_flag = (int*)(tmem_slot + 1);
+  uint64_t* xready = drain + 3;  // [2 slots][kEpiWarps] (XCHG), after tmem_slot and abort_flag
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   pdl_trigger();
@@ -381,6 +435,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
       mbar_init(&acc_empty[b], kEpiWarps);
     }
     mbar_init(drain, 1);
+    if (XCHG)
+      for (int b = 0; b < 2 * kEpiWarps; ++b) mbar_init(&xready[b], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -390,6 +446,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
   }
   tc_fence_before();
   __syncthreads();
+  if (XCHG) cluster_sync_all();  // the other CTA's exchange barriers are initialised
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   volatile int* abort_v = abort_flag;
@@ -510,7 +567,97 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
       const float* bsrc0 = D->base[w.c_lo];
       const float* bsrc1 = nc == 2 ? D->base[w.c_lo + 1] : nullptr;
       auto chunk_cols = [&](int ch) { return min(16, N - (n0 + ch * 16)); };
-      if constexpr (!PAIR) {
+      if constexpr (XCHG) {
+        // kStage1X: this CTA's component c; the other CTA of the cluster has 1 - c
+        const int c = w.c_lo;
+        float bv[HC];  // own base U^c
+        const float* bsrc = D->base[c];
+#pragma unroll
+        for (int j = 0; j < HC; ++j) {
+          const int col = n0 + j;
+          bv[j] = (mrow && col < N) ? __ldg(bsrc + (int64_t)col * M + m) : 0.f;
+        }
+        if (!mbar_wait_sleep(&acc_full[slot], (i >> 1) & 1)) {
+          if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
+          *abort_v = 1;
+          break;
+        }
+        tc_fence_after();
+        if (*abort_v) break;
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * 2 * BN + half * HC);
+        float* of = D->outf[c];
+#pragma unroll
+        for (int bt = 0; bt < NCH; bt += 2) {  // U2^c = U^c + alpha acc, stored
+          uint32_t r[2][16];
+          tmem_ld16_nw(ta + (uint32_t)(bt * 16), r[0]);
+          tmem_ld16_nw(ta + (uint32_t)((bt + 1) * 16), r[1]);
+          tmem_wait_ld();
+          tmem_fence16(r[0]);
+          tmem_fence16(r[1]);
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const int col = n0 + bt * 16 + jj;
+            if (mrow && col < N)
+              of[(int64_t)col * M + m] = bv[bt * 16 + jj] + alpha * __uint_as_float(r[jj / 16][jj % 16]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0)  // the accumulator slot is free again
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[slot]))
+                       : "memory");
+        // publish U2^c to the other CTA's counterpart warp, wait for its U2^(1-c)
+        __threadfence();
+        __syncwarp();
+        uint64_t* mine = &xready[slot * kEpiWarps + (warp - 2)];
+        if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(mine), cluster_rank() ^ 1u));
+        if (!mbar_wait_cluster(mine, (i >> 1) & 1)) {
+          if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
+          *abort_v = 1;
+          break;
+        }
+        __syncwarp();
+        // D^c = g^c(U2, V2) - g^c(U, V) as pieces
+        const float* ob = D->base[1 - c];
+        const float* os = D->outf[1 - c];
+        __nv_bfloat16* op = D->outp[c];
+        const ReactionT<float> rx = D->rx;
+        constexpr int XC = 8;  // columns per exchange chunk (register budget)
+#pragma unroll 1
+        for (int ch = 0; ch < HC / XC; ++ch) {
+          float x2[XC], yb[XC], y2[XC];
+#pragma unroll
+          for (int j = 0; j < XC; ++j) {
+            const int col = n0 + ch * XC + j;
+            const bool ok = mrow && col < N;
+            const int64_t o = (int64_t)col * M + m;
+            x2[j] = ok ? __ldcg(of + o) : 0.f;
+            yb[j] = ok ? __ldcg(ob + o) : 0.f;
+            y2[j] = ok ? __ldcg(os + o) : 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < XC; ++j) {
+            const int col = n0 + ch * XC + j;
+            if (mrow && col < N) {
+              float xb = 0.f;
+#pragma unroll
+              for (int t = 0; t < HC / XC; ++t)
+                if (t == ch) xb = bv[t * XC + j];  // register-indexed select
+              const float u0 = c == 0 ? xb : yb[j], v0 = c == 0 ? yb[j] : xb;
+              const float u2 = c == 0 ? x2[j] : y2[j], v2 = c == 0 ? y2[j] : x2[j];
+              float g0u, g0v, g2u, g2v;
+              react<float>(rx, u0, v0, g0u, g0v);
+              react<float>(rx, u2, v2, g2u, g2v);
+              const int64_t o = (int64_t)col * M + m;
+              __nv_bfloat16 b0, b1, b2;
+              split3(c == 0 ? g2u - g0u : g2v - g0v, b0, b1, b2);
+              op[o] = b0;
+              op[plane + o] = b1;
+              op[2 * plane + o] = b2;
+            }
+          }
+        }
+      } else if constexpr (!PAIR) {
         // One component: load this warp's whole FP32 base strip (HC columns)
         // before the accumulator is ready, read all its TMEM columns with one
         // wait, then write.
@@ -671,6 +818,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
   }
   tc_fence_before();
   __syncthreads();
+  if (XCHG) cluster_sync_all();  // no exchange arrival can still target this CTA
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, 4 * BN);
@@ -701,25 +849,6 @@ struct Tc2Cfg {
   static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
 };
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// Address of the same shared-memory location in CTA `rank` of the cluster.
-__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-               : "memory");
-}
 __device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map, uint32_t bar,
                                                  int x, int y, int z) {
   asm volatile(
@@ -1426,11 +1555,16 @@ constexpr int tile_rows(int variant) { return kVariants[variant].cta2 ? 2 * kBM 
 
 template <int SW, int BN>
 cudaError_t set_smem_attr() {
-  cudaError_t e = cudaFuncSetAttribute(tc_mode_kernel<SW, BN, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<SW, BN>::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc_mode_kernel<SW, BN, true>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<SW, BN>::SMEM);
+  const int sm = TcCfg<SW, BN>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(tc_mode_kernel<SW, BN, false, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_mode_kernel<SW, BN, true, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_mode_kernel<SW, BN, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
 }
 template <int SW>
 cudaError_t set_smem_attr_pair() {
@@ -1468,14 +1602,79 @@ template <bool PAIR>
 cudaError_t launch_tc_t(int v, dim3 grid, cudaStream_t s, const TcLaunch& L) {
   switch (v) {
     case 0:
-      return launch_k(tc_mode_kernel<64, 128, PAIR>, grid, dim3(kThreads), TcCfg<64, 128>::SMEM, s, L);
+      return launch_k(tc_mode_kernel<64, 128, PAIR, false>, grid, dim3(kThreads), TcCfg<64, 128>::SMEM, s, L);
     case 1:
-      return launch_k(tc_mode_kernel<128, 128, PAIR>, grid, dim3(kThreads), TcCfg<128, 128>::SMEM, s, L);
+      return launch_k(tc_mode_kernel<128, 128, PAIR, false>, grid, dim3(kThreads), TcCfg<128, 128>::SMEM, s, L);
     case 2:
-      return launch_k(tc_mode_kernel<64, 64, PAIR>, grid, dim3(kThreads), TcCfg<64, 64>::SMEM, s, L);
+      return launch_k(tc_mode_kernel<64, 64, PAIR, false>, grid, dim3(kThreads), TcCfg<64, 64>::SMEM, s, L);
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+// The kStage1X pass: clusters of two CTAs (u and v of one tile).
+template <int SW, int BN>
+cudaError_t launch_xchg_t(int clusters, cudaStream_t s, const TcLaunch& L) {
+  const int pairs = L.nunits / 2;
+  const int nc = pairs < clusters ? pairs : clusters;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * nc));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = TcCfg<SW, BN>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, tc_mode_kernel<SW, BN, false, true>, L);
+}
+cudaError_t launch_xchg(int v, int clusters, cudaStream_t s, const TcLaunch& L) {
+  if (L.nunits <= 0) return cudaSuccess;
+  switch (v) {
+    case 0:
+      return launch_xchg_t<64, 128>(clusters, s, L);
+    case 1:
+      return launch_xchg_t<128, 128>(clusters, s, L);
+    case 2:
+      return launch_xchg_t<64, 64>(clusters, s, L);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+// Clusters of the XCHG kernel that fit on the GPU at once.
+int xchg_clusters(int v) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(kThreads);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (v == 0) {
+    cfg.dynamicSmemBytes = TcCfg<64, 128>::SMEM;
+    e = cudaOccupancyMaxActiveClusters(&n, tc_mode_kernel<64, 128, false, true>, &cfg);
+  } else if (v == 1) {
+    cfg.dynamicSmemBytes = TcCfg<128, 128>::SMEM;
+    e = cudaOccupancyMaxActiveClusters(&n, tc_mode_kernel<128, 128, false, true>, &cfg);
+  } else if (v == 2) {
+    cfg.dynamicSmemBytes = TcCfg<64, 64>::SMEM;
+    e = cudaOccupancyMaxActiveClusters(&n, tc_mode_kernel<64, 64, false, true>, &cfg);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 // pair: the launch's units are (u, v) pairs (the fused stage-1 epilogue).
@@ -1582,6 +1781,7 @@ struct TcState {
   int fuse;      // 1: fuse the stage-1 combination into the last stage-1 product
   int num_sms;
   int slots;     // resident CTAs (or CTA pairs) of the mode-product kernel
+  int xslots;    // resident clusters of the exchanging (kStage1X) kernel
   int* err;
   std::vector<void*> allocs;
   // step sequence: tensor-core passes and the launches around them
@@ -1739,9 +1939,14 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
   }
   // the fused stage-1 epilogue is kept behind ADR_TC_FUSE=1 until it beats
   // the separate reaction-difference kernel on large grids
+  // Stage-1 reaction difference: 0 = separate kernel, 1 = pair units (u and
+  // v of a tile in one CTA), 2 = clusters of two CTAs exchanging U2 and V2.
   S->fuse = 0;
-  if (const char* ev = getenv("ADR_TC_FUSE")) S->fuse = atoi(ev) != 0 ? 1 : 0;
-  if (kVariants[S->variant].cta2) S->fuse = 0;  // the pair kernel has no pair-unit epilogue
+  if (const char* ev = getenv("ADR_TC_FUSE")) {
+    const int f = atoi(ev);
+    S->fuse = f >= 0 && f <= 2 ? f : 0;
+  }
+  if (kVariants[S->variant].cta2) S->fuse = 0;  // the CTA-pair kernel has neither epilogue
   int dev = 0;
   cudaGetDevice(&dev);
   S->num_sms = 148;
@@ -1750,6 +1955,11 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
   if (kVariants[S->variant].cta2) {
     S->slots = pair_clusters(S->variant);
     if (S->slots <= 0) return cudaErrorNotSupported;
+  }
+  S->xslots = 0;
+  if (S->fuse == 2) {
+    S->xslots = xchg_clusters(S->variant);
+    if (S->xslots <= 0) S->fuse = 0;  // clusters unavailable: separate kernel
   }
   const int sw = kVariants[S->variant].sw, bn = kVariants[S->variant].bn;
   S->N = 1;
@@ -1794,8 +2004,8 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     for (int mu = 0; mu < d; ++mu) {
       TcPass ps{b, mu, ell, kPieces3, 0, kOutPieces, kBaseNone, kAlphaOne};
       if (mu == d - 1) {
-        ps.mode = stage1_fuse ? kStage1 : kAxpy;
-        ps.pair = stage1_fuse;
+        ps.mode = stage1_fuse == 1 ? kStage1 : (stage1_fuse == 2 ? kStage1X : kAxpy);
+        ps.pair = stage1_fuse == 1;
         ps.out = last_out;
         ps.base = last_base;
         ps.alpha = last_alpha;
@@ -1872,6 +2082,8 @@ struct GroupStep {
   const int* ustart;        // [np][nsolves + 1]
   int units[16];
   int pair[16];             // per pass: units are (u, v) pairs
+  int xchg[16];             // per pass: kStage1X (clusters of two)
+  int xslots;               // resident clusters of the exchanging kernel
   PwLaunch rhs, flat;       // stencil blocks; flat pointwise blocks
   int rhs_blocks, flat_blocks;
   int* err;
@@ -1928,7 +2140,10 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
         L.nunits = G.units[p];
         L.err = G.err;
         e = timed_kernel(ctl, KC_MODE_TC, G.flops[p], G.bytes[p],
-                         [&] { return launch_tc(G.variant, G.num_sms, st, L, G.pair[p] != 0); });
+                         [&] {
+                           if (G.xchg[p]) return launch_xchg(G.variant, G.xslots, st, L);
+                           return launch_tc(G.variant, G.num_sms, st, L, G.pair[p] != 0);
+                         });
       } break;
       default:
         e = cudaErrorInvalidValue;
@@ -1944,14 +2159,18 @@ static void pass_work(const TcState* S, const TcPass& ps, double& flops, double&
   bytes = 2.0 * (6.0 * N + 6.0 * nmu * nmu);
   if (ps.mode == kPieces3) bytes += 2.0 * 6.0 * N;
   if (ps.mode == kAxpy) bytes += 2.0 * 8.0 * N;
-  if (ps.mode == kStage1) bytes += 2.0 * (8.0 + 6.0) * N;
+  if (ps.mode == kStage1 || ps.mode == kStage1X) bytes += 2.0 * (8.0 + 6.0) * N;
 }
 
 static void fill_ops(GroupStep& G, const TcState* S) {
   G.np = (int)S->passes.size();
   G.nops = (int)S->ops.size();
   for (int o = 0; o < G.nops; ++o) G.ops[o] = S->ops[o];
-  for (int p = 0; p < G.np; ++p) G.pair[p] = S->passes[p].pair;
+  for (int p = 0; p < G.np; ++p) {
+    G.pair[p] = S->passes[p].pair;
+    G.xchg[p] = S->passes[p].mode == kStage1X;
+  }
+  G.xslots = S->xslots;
 }
 
 cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {

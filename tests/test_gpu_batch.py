@@ -160,3 +160,27 @@ def test_batch_churn_without_synchronisation(adr):
         assert torch.equal(us[i], ref[i][0]) and torch.equal(vs[i], ref[i][1]), i
     for pl in plans:
         pl.close()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_batch_with_cluster_exchange_equals_alone(adr, d, monkeypatch):
+    """Grouped batches whose stage-1 reaction difference is fused through the
+    two-CTA cluster exchange give every solve the result it gets alone."""
+    import torch
+    monkeypatch.setenv("ADR_TC_FUSE", "2")
+    probs = mixed_problems(d=d, count=5)
+    plans = [adr.Plan(p) for p in probs]
+    us, vs, inits = states(adr, probs)
+    b = adr.Batch(plans)
+    assert b.grouped
+    b.step(us, vs, 20)
+    torch.cuda.synchronize()
+    for i, (p, pl, (u0, v0)) in enumerate(zip(probs, plans, inits)):
+        u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+        pl.step(u, v, 20)
+        torch.cuda.synchronize()
+        assert torch.equal(u, us[i]) and torch.equal(v, vs[i]), i
+    b.close()
+    for pl in plans:
+        pl.close()

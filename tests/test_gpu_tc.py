@@ -75,12 +75,13 @@ def test_ragged_shapes_bf16x3(adr, n, model):
     assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
 
 
-@pytest.mark.parametrize("fuse", ["0", "1"])
-@pytest.mark.parametrize("n", [(72, 200), (24, 40, 56)])
+@pytest.mark.parametrize("fuse", ["0", "1", "2"])
+@pytest.mark.parametrize("n", [(72, 200), (24, 40, 56), (136, 64)])
 def test_stage_one_fusion_both_ways(adr, n, fuse, monkeypatch):
-    """The stage-1 combination and reaction difference either fused into the
-    last tensor-core product (pair units of the one-CTA kernel) or done by a
-    separate kernel must both match the oracle."""
+    """The stage-1 combination and reaction difference done by a separate
+    kernel (0), fused into the last tensor-core product with u and v of a
+    tile in one CTA (1), or fused with u and v in the two CTAs of a cluster
+    exchanging U2 and V2 (2) must all match the oracle."""
     monkeypatch.setenv("ADR_TC_FUSE", fuse)
     monkeypatch.setenv("ADR_TC_VARIANT", "0")
     d = len(n)
@@ -90,7 +91,7 @@ def test_stage_one_fusion_both_ways(adr, n, fuse, monkeypatch):
     u0, v0 = inputs(p, kind="uniform")
     Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, p.nsteps)
     U, V, st = run(adr, p, u0, v0, p.nsteps)
-    assert st["kernels"]["reaction_diff"]["count"] == (0 if fuse == "1" else p.nsteps)
+    assert st["kernels"]["reaction_diff"]["count"] == (0 if fuse != "0" else p.nsteps)
     assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
 
 
