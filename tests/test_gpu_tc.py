@@ -149,3 +149,25 @@ def test_kernel_variants(adr, n, variant, monkeypatch):
     U, V, st = run(adr, p, u0, v0, p.nsteps)
     assert st["kernels"]["mode_product_tc"]["count"] == 2 * d * p.nsteps
     assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+def test_largest_direction_bf16x3(adr):
+    """The largest direction the tensor path takes, n = 4096 (with 512 in the
+    other direction), two steps against the oracle.  The oracle's matrix
+    functions come from its eigen route (exact for these symmetric operators,
+    no advection), because Pade on the 3n x 3n augmented matrix takes minutes
+    at this size."""
+    from oracle import fd, matfun
+    p = wl.Problem(d=2, n=(4096, 512), lo=(0.0, 0.0), hi=(100.0, 100.0), diff=(1.0, 20.0),
+                   adv=((0.0, 0.0), (0.0, 0.0)), model=wl.FHN, params=(0.05, 2.0, -0.03),
+                   tau=1e-2, nsteps=2, precision=wl.BF16X3, seed=23)
+    A = [fd.direction_matrices(p, 0), fd.direction_matrices(p, 1)]
+    fns = [[matfun.phi_eigen(p.tau * Am) for Am in A[c]] for c in range(2)]
+    plan = schemes.Plan(d=2, tau=p.tau, model=p.model, params=tuple(p.params), A=A,
+                        E=[[f[0] for f in fc] for fc in fns],
+                        phi1=[[f[1] for f in fc] for fc in fns],
+                        phi2=[[f[2] for f in fc] for fc in fns])
+    u0, v0 = inputs(p)
+    Ur, Vr = schemes.etd2rkds_solve(plan, u0, v0, p.nsteps)
+    U, V, _ = run(adr, p, u0, v0, p.nsteps)
+    assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
