@@ -391,6 +391,13 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
                : "memory");
 }
+// Arrival that orders no memory: for "these TMEM columns have been read"
+// (tcgen05.wait::ld has completed the reads).  A release at cluster scope
+// would first wait for every preceding global store of the thread.
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
 // Persistent kernel.  CTA b handles units b, b + gridDim.x, ... of the
 // launch's unit list (all solves' tiles, solve-major, n-tile fastest within
 // a solve so that CTAs running together share A tiles in L2).  For each unit
@@ -1160,7 +1167,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(slot ? ae1 : ae0);
+      if (lane == 0) mbar_arrive_cluster_relaxed(slot ? ae1 : ae0);
     }
   }
   tc_fence_before();
@@ -1928,11 +1935,18 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
   t->work[0] = S;
   t->prec = prec;
   S->d = d;
-  // Default kernel: one CTA per 128 x 128 tile, 64-byte swizzle, four 48 KB
-  // stages.  (The CTA-pair kernel, variant 4, is about 2% faster on a 1024^2
-  // grid but about 10% slower on batches of small grids; one kernel for every
-  // plan keeps batches of mixed sizes grouped.)  ADR_TC_VARIANT overrides.
-  S->variant = 0;
+  // Default kernel: on 2D grids of about a million points and more, the
+  // CTA-pair kernel (256 x 128 tiles over two SMs, 128-byte swizzle, three
+  // 72 KB stages: the tensor pipe stays fed); otherwise one CTA per 128 x 128
+  // tile with 64-byte swizzle and four 48 KB stages, whose smaller tiles
+  // waste less on small grids and which is faster on 3D grids (bound by
+  // HBM traffic and the epilogue).  A batch mixing the two runs one grouped
+  // launch sequence per kernel.  ADR_TC_VARIANT overrides.
+  {
+    int64_t npts = 1;
+    for (int m = 0; m < d; ++m) npts *= n[m];
+    S->variant = (d == 2 && npts >= 1000000) ? 4 : 0;
+  }
   if (const char* ev = getenv("ADR_TC_VARIANT")) {
     const int v = atoi(ev);
     if (v >= 0 && v < kNumVariants) S->variant = v;
@@ -1954,7 +1968,10 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
   S->slots = S->num_sms;
   if (kVariants[S->variant].cta2) {
     S->slots = pair_clusters(S->variant);
-    if (S->slots <= 0) return cudaErrorNotSupported;
+    if (S->slots <= 0) {  // no room for clusters of two: the one-CTA kernel
+      S->variant = 0;
+      S->slots = S->num_sms;
+    }
   }
   S->xslots = 0;
   if (S->fuse == 2) {
@@ -2240,6 +2257,10 @@ struct adr_batch_s {
   cudaGraphExec_t gexec_timed;   // timing mode: with event-record nodes
   int64_t g_launches;
   std::vector<void*> allocs;
+  // a batch of plans that cannot all share one launch sequence is split into
+  // parts, each a batch of mutually compatible plans (solve indices in idx)
+  std::vector<adr_batch_s*> parts;
+  std::vector<std::vector<int>> idx;
 };
 
 static constexpr int64_t kBatchChunk = 16;
@@ -2349,6 +2370,7 @@ static cudaMemPool_t batch_pool() {
 // the stream-ordered pool after the batch's last launch on its stream.
 static void batch_free(adr_batch B) {
   if (!B) return;
+  for (adr_batch_s* q : B->parts) batch_free(q);
   cudaStream_t st = B->ctl ? B->ctl->stream : nullptr;
   if (B->gexec) cudaGraphExecDestroy(B->gexec);
   if (B->gexec_timed) cudaGraphExecDestroy(B->gexec_timed);
@@ -2361,6 +2383,24 @@ static void batch_free(adr_batch B) {
   delete B;
 }
 
+// Plans a and b can share grouped launches: tensor-core plans running the
+// same kernels and step sequence (sizes and coefficients may differ).
+static bool same_sequence(const adr_plan_s* a, const adr_plan_s* b) {
+  const TcState* A = (const TcState*)a->tc.work[0];
+  const TcState* S = (const TcState*)b->tc.work[0];
+  if (a->prec != ADR_BF16X3 || b->prec != ADR_BF16X3 || !A || !S) return false;
+  if (S->d != A->d || S->variant != A->variant || S->scheme != A->scheme ||
+      S->passes.size() != A->passes.size() || S->ops.size() != A->ops.size())
+    return false;
+  for (size_t p = 0; p < S->passes.size(); ++p)
+    if (memcmp(&S->passes[p], &A->passes[p], sizeof(TcPass)) != 0) return false;
+  for (size_t o = 0; o < S->ops.size(); ++o)
+    if (memcmp(&S->ops[o], &A->ops[o], sizeof(TcOp)) != 0) return false;
+  return true;
+}
+
+static adr_status batch_create_one(const adr_plan* plans, int count, void* stream, adr_batch* out);
+
 extern "C" adr_status adr_batch_create(const adr_plan* plans, int count, void* stream,
                                        adr_batch* out) {
   if (!plans || count < 1 || !out) {
@@ -2372,6 +2412,47 @@ extern "C" adr_status adr_batch_create(const adr_plan* plans, int count, void* s
       set_error("adr_batch_create: NULL plan");
       return ADR_EINVAL;
     }
+  // classes of mutually compatible plans, in order of first appearance; plans
+  // that group with nothing (not BF16X3) form one class stepped plan by plan
+  std::vector<std::vector<int>> cls;
+  int loose = -1;
+  for (int i = 0; i < count; ++i) {
+    int c = -1;
+    if (same_sequence(plans[i], plans[i])) {
+      for (size_t k = 0; k < cls.size() && c < 0; ++k)
+        if ((int)k != loose && same_sequence(plans[cls[k][0]], plans[i])) c = (int)k;
+    } else {
+      c = loose;
+    }
+    if (c < 0) {
+      cls.emplace_back();
+      c = (int)cls.size() - 1;
+      if (!same_sequence(plans[i], plans[i])) loose = c;
+    }
+    cls[c].push_back(i);
+  }
+  if (cls.size() == 1) return batch_create_one(plans, count, stream, out);
+  adr_batch B = new adr_batch_s();
+  B->plans.assign(plans, plans + count);
+  B->nsolves = count;
+  B->grouped = loose < 0 ? 1 : 0;
+  for (const std::vector<int>& c : cls) {
+    std::vector<adr_plan> sub;
+    for (int i : c) sub.push_back(plans[i]);
+    adr_batch part = nullptr;
+    adr_status st = batch_create_one(sub.data(), (int)sub.size(), stream, &part);
+    if (st != ADR_OK) {
+      batch_free(B);
+      return st;
+    }
+    B->parts.push_back(part);
+    B->idx.push_back(c);
+  }
+  *out = B;
+  return ADR_OK;
+}
+
+static adr_status batch_create_one(const adr_plan* plans, int count, void* stream, adr_batch* out) {
   adr_batch B = new adr_batch_s();
   B->plans.assign(plans, plans + count);
   B->ctl = new adr_plan_s();
@@ -2381,18 +2462,9 @@ extern "C" adr_status adr_batch_create(const adr_plan* plans, int count, void* s
   if (const char* ev = getenv("ADR_GRAPHS")) B->ctl->use_graphs = atoi(ev) != 0;
   B->nsolves = count;
   // grouped only if every plan runs the same tensor-core step sequence
-  bool grouped = true;
   const TcState* S0 = (const TcState*)plans[0]->tc.work[0];
-  for (int i = 0; i < count && grouped; ++i) {
-    const TcState* S = (const TcState*)plans[i]->tc.work[0];
-    grouped = plans[i]->prec == ADR_BF16X3 && S && S0 && S->d == S0->d &&
-              S->variant == S0->variant && S->scheme == S0->scheme &&
-              S->passes.size() == S0->passes.size() && S->ops.size() == S0->ops.size();
-    for (size_t p = 0; grouped && p < S->passes.size(); ++p)
-      grouped = memcmp(&S->passes[p], &S0->passes[p], sizeof(TcPass)) == 0;
-    for (size_t o = 0; grouped && o < S->ops.size(); ++o)
-      grouped = memcmp(&S->ops[o], &S0->ops[o], sizeof(TcOp)) == 0;
-  }
+  bool grouped = true;
+  for (int i = 0; i < count && grouped; ++i) grouped = same_sequence(plans[0], plans[i]);
   B->grouped = grouped ? 1 : 0;
   cudaError_t e = cudaSuccess;
   // stream-ordered device memory from the library's own pool (one per
@@ -2544,6 +2616,18 @@ extern "C" adr_status adr_batch_step(adr_batch batch, void* const* u, void* cons
     return ADR_EINVAL;
   }
   adr_batch B = batch;
+  if (!B->parts.empty()) {  // one grouped launch sequence per part
+    for (size_t k = 0; k < B->parts.size(); ++k) {
+      std::vector<void*> pu, pv;
+      for (int i : B->idx[k]) {
+        pu.push_back(u[i]);
+        pv.push_back(v[i]);
+      }
+      adr_status st = adr_batch_step(B->parts[k], pu.data(), pv.data(), nsteps);
+      if (st != ADR_OK) return st;
+    }
+    return ADR_OK;
+  }
   for (int i = 0; i < B->nsolves; ++i) {
     if (!u[i] || !v[i] || u[i] == v[i]) {
       set_error("adr_batch_step: state pointers must be distinct and non-NULL");
@@ -2630,6 +2714,13 @@ extern "C" adr_status adr_batch_step(adr_batch batch, void* const* u, void* cons
 
 extern "C" adr_status adr_batch_set_timing(adr_batch batch, int enable) {
   if (!batch) return ADR_EINVAL;
+  if (!batch->parts.empty()) {
+    for (adr_batch_s* q : batch->parts) {
+      adr_status st = adr_batch_set_timing(q, enable);
+      if (st != ADR_OK) return st;
+    }
+    return ADR_OK;
+  }
   if (batch->gexec_timed) {  // its event nodes use events the plan hands out again
     cudaStreamSynchronize(batch->ctl->stream);
     cudaGraphExecDestroy(batch->gexec_timed);
@@ -2644,6 +2735,27 @@ extern "C" adr_status adr_batch_set_timing(adr_batch batch, int enable) {
 
 extern "C" adr_status adr_batch_stats(adr_batch batch, adr_stats* out) {
   if (!batch || !out) return ADR_EINVAL;
+  if (!batch->parts.empty()) {  // sums over the parts (steps: those of one part)
+    memset(out, 0, sizeof(*out));
+    for (size_t k = 0; k < batch->parts.size(); ++k) {
+      adr_stats q;
+      adr_status st = adr_batch_stats(batch->parts[k], &q);
+      if (st != ADR_OK) return st;
+      if (k == 0) {
+        *out = q;
+        continue;
+      }
+      out->launches += q.launches;
+      out->device_error = out->device_error ? out->device_error : q.device_error;
+      for (int c = 0; c < 16; ++c) {
+        out->count[c] += q.count[c];
+        out->ms[c] += q.ms[c];
+        out->flops[c] += q.flops[c];
+        out->bytes[c] += q.bytes[c];
+      }
+    }
+    return ADR_OK;
+  }
   adr_status st = adr_plan_stats(batch->ctl, out);
   if (st == ADR_OK && batch->d_err) {
     int h = 0;

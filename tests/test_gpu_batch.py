@@ -184,3 +184,29 @@ def test_batch_with_cluster_exchange_equals_alone(adr, d, monkeypatch):
     b.close()
     for pl in plans:
         pl.close()
+
+
+def test_batch_mixing_kernels_is_split_and_equals_alone(adr):
+    """A batch whose plans run different mode-product kernels (a 1024 x 1024
+    grid takes the CTA-pair kernel, smaller grids the one-CTA kernel) runs
+    one grouped launch sequence per kernel; every solve equals its solve
+    alone."""
+    import torch
+    probs = mixed_problems(d=2, count=3) + [wl.fhn_1024(precision=wl.BF16X3, nsteps=20)]
+    plans = [adr.Plan(p) for p in probs]
+    us, vs, inits = states(adr, probs)
+    b = adr.Batch(plans)
+    assert b.grouped
+    b.step(us, vs, 20)
+    st = b.stats()
+    assert st["device_error"] == 0
+    torch.cuda.synchronize()
+    for i, (pl, (u0, v0)) in enumerate(zip(plans, inits)):
+        u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+        pl.step(u, v, 20)
+        torch.cuda.synchronize()
+        assert torch.equal(u, us[i]) and torch.equal(v, vs[i]), i
+    b.close()
+    for pl in plans:
+        pl.close()
