@@ -1935,17 +1935,16 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
   t->work[0] = S;
   t->prec = prec;
   S->d = d;
-  // Default kernel: on 2D grids of about a million points and more, the
+  // Default kernel: on grids of about a million points and more, the
   // CTA-pair kernel (256 x 128 tiles over two SMs, 128-byte swizzle, three
-  // 72 KB stages: the tensor pipe stays fed); otherwise one CTA per 128 x 128
-  // tile with 64-byte swizzle and four 48 KB stages, whose smaller tiles
-  // waste less on small grids and which is faster on 3D grids (bound by
-  // HBM traffic and the epilogue).  A batch mixing the two runs one grouped
-  // launch sequence per kernel.  ADR_TC_VARIANT overrides.
+  // 72 KB stages: the tensor pipe stays fed, and each SM streams half of B);
+  // on smaller grids one CTA per 128 x 128 tile with 64-byte swizzle and four
+  // 48 KB stages, whose smaller tiles waste less.  A batch mixing the two runs
+  // one grouped launch sequence per kernel.  ADR_TC_VARIANT overrides.
   {
     int64_t npts = 1;
     for (int m = 0; m < d; ++m) npts *= n[m];
-    S->variant = (d == 2 && npts >= 1000000) ? 4 : 0;
+    S->variant = npts >= 1000000 ? 4 : 0;
   }
   if (const char* ev = getenv("ADR_TC_VARIANT")) {
     const int v = atoi(ev);
