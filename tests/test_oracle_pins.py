@@ -352,6 +352,47 @@ def test_order_two_on_brusselator():
     assert 1.9 <= o1 <= 2.2 and 1.9 <= o2 <= 2.2, (errs, o1, o2)
 
 
+def _lawson_orders(step):
+    n = 12
+    ref_steps = 16 * 200
+    p = _brusselator_e6(n, ref_steps)
+    U0, V0 = wl.brusselator_e6_initial(p)
+
+    def solve(m):
+        plan = schemes.make_plan(p, tau=1.0 / m)
+        U, V = U0, V0
+        for _ in range(m):
+            U, V = step(plan, U, V)
+        return U, V
+
+    Ur, Vr = solve(ref_steps)
+    errs = [metrics.paper_rel_err(*solve(m), Ur, Vr) for m in (50, 100, 200)]
+    return errs, math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])
+
+
+def test_lawson2b_order_two_on_brusselator():
+    """Lawson2b (Eq. 7) converges with order 2 under step halving against a
+    16x finer Lawson2b run on the Sec. 4.6 Brusselator."""
+    errs, o1, o2 = _lawson_orders(schemes.lawson2b_step)
+    assert 1.8 <= o1 <= 2.3 and 1.8 <= o2 <= 2.3, (errs, o1, o2)
+
+
+def test_lawson2b_without_final_reaction_is_first_order():
+    """Planted mistake: dropping the last stage's tau/2 G(U2, V2) term of
+    Eq. 7 makes the scheme inconsistent at order 2 (observed order about 1),
+    so the order pin above would catch it."""
+    from oracle.models import reaction
+    from oracle.tensor import tucker
+
+    def broken(plan, U, V):
+        tau = plan.tau
+        GU, GV = reaction(plan.model, plan.params, U, V)
+        return (tucker(U + 0.5 * tau * GU, plan.E[0]), tucker(V + 0.5 * tau * GV, plan.E[1]))
+
+    errs, o1, o2 = _lawson_orders(broken)
+    assert o1 < 1.5 and o2 < 1.5, (errs, o1, o2)
+
+
 def test_split_and_unsplit_etd2rk_errors_comparable():
     """On a tiny grid the split scheme's global error is within a small
     factor of unsplit ETD2RK's (Eq. 8 with dense phi(tau K)); the paper's
