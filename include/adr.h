@@ -81,9 +81,11 @@ typedef enum {
 /* Arithmetic of the mode products (the Tucker operators).
  *  ADR_FP64   : double state, double SIMT products.
  *  ADR_FP32   : float state, float SIMT products (FP32 FMA).
- *  ADR_TF32X3 : reserved for TF32 hi+lo tensor-core products; plans return
- *               ADR_EUNSUPPORTED (the 2^-21 split misses the FP32-class
- *               accuracy target on fine grids).
+ *  ADR_TF32X3 : float state, tcgen05 kind::tf32 products with operands split
+ *               into two TF32 parts, hi + lo (three MMAs: the lo x lo term is
+ *               dropped), FP32 accumulation.  About 22 significant bits per
+ *               operand: less accurate than ADR_BF16X3, at the same MMA cost
+ *               and more operand bytes.  Same grid rule as ADR_BF16X3.
  *  ADR_BF16X3 : float state, tcgen05 tensor-core products with operands
  *               split into three BF16 parts (6 MMAs, FP32 accumulation);
  *               needs every n[mu] to be a multiple of 8, else

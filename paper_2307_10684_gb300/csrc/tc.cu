@@ -39,18 +39,30 @@ namespace adr {
 namespace {
 
 constexpr int kBM = 128;       // rows per tile (TMEM lanes)
-constexpr int kPieces = 3;
+constexpr int kPieces = 3;     // BF16 pieces of an FP32 value
+
+// Operand formats of the tensor-core path: three BF16 pieces per value with
+// six products (kind::f16), or two TF32 pieces (stored as FP32 words whose
+// low 13 mantissa bits are zero) with three products (kind::tf32).  Both
+// take 32 bytes of K per MMA, so the shared-memory layouts are the same.
+enum { kFmtBF16 = 0, kFmtTF32 = 1 };
+template <int F>
+struct Fmt {
+  static constexpr int P = F == kFmtTF32 ? 2 : 3;     // pieces
+  static constexpr int ESZ = F == kFmtTF32 ? 4 : 2;   // bytes per piece element
+};
 constexpr uint64_t kWaitNs = 2000000000ull;    // bounded waits: 2 s
 
 // Tile configuration: SW = bytes of K per stage row (the swizzle width: 64
 // or 128, i.e. 32 or 64 BF16 values), BN = output columns per tile.
-template <int SW, int BN>
+template <int SW, int BN, int F = kFmtBF16>
 struct TcCfg {
-  static constexpr int BK = SW / 2;                  // K elements per stage
-  static constexpr int KSTEPS = SW / 32;             // K16 MMA steps per stage
+  static constexpr int P = Fmt<F>::P;
+  static constexpr int BK = SW / Fmt<F>::ESZ;        // K elements per stage
+  static constexpr int KSTEPS = SW / 32;             // 32-byte MMA K steps per stage
   static constexpr int TILE_A = kBM * SW;            // bytes of one A piece tile
   static constexpr int TILE_B = BN * SW;             // bytes of one B piece tile
-  static constexpr int STAGE = kPieces * (TILE_A + TILE_B);
+  static constexpr int STAGE = P * (TILE_A + TILE_B);
   static constexpr int STAGES = (224 * 1024) / STAGE > 8 ? 8 : (224 * 1024) / STAGE;
   static constexpr int SMEM = STAGES * STAGE + 1024 + 512;  // + alignment, barriers
   static constexpr int TMEM_COLS = 2 * BN;           // two accumulators
@@ -190,6 +202,30 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
         : "memory");
   }
 }
+// kind::tf32 (A and B TF32 in shared memory, FP32 accumulate), same collector use.
+template <int COL>
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  if constexpr (COL == kColFill) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else if constexpr (COL == kColLast) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -257,6 +293,24 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::tf32: as above with A = B = TF32 (code 2).
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// x = hi + lo with hi, lo TF32 (round to nearest, ties away, at each level);
+// about 22 significant bits of x.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void split2_tf32(float x, float& hi, float& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - hi);
 }
 
 __device__ __forceinline__ void split3(float x, __nv_bfloat16& b0, __nv_bfloat16& b1,
@@ -414,9 +468,10 @@ __device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cluster_add
 // the other CTA through that CTA's `xready` barrier and waits for its own;
 // it then reads the other component's base and stage values (L2) and writes
 // its component of D = G(U2, V2) - G(U, V) as BF16 pieces.
-template <int SW, int BN, bool PAIR, bool XCHG>
+template <int SW, int BN, bool PAIR, bool XCHG, int F = kFmtBF16>
 __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_constant__ TcLaunch L) {
-  using C = TcCfg<SW, BN>;
+  using C = TcCfg<SW, BN, F>;
+  static_assert(F == kFmtBF16 || (!PAIR && !XCHG), "TF32 pieces: plain epilogues only");
   static_assert(4 * BN <= 512, "four accumulators must fit in TMEM");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -489,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
           }
           mbar_arrive_expect_tx(&full[s], C::STAGE);
           tma_load_3d(st, ma, &full[s], kb * C::BK, w.m0, 0);                   // 3 A pieces
-          tma_load_3d(st + kPieces * C::TILE_A, mb, &full[s], kb * C::BK, w.n0, 0);  // 3 B pieces
+          tma_load_3d(st + C::P * C::TILE_A, mb, &full[s], kb * C::BK, w.n0, 0);  // B pieces
         }
       }
     }
@@ -498,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
     for (uint32_t q = first; q < g; ++q) mbar_wait(&full[q % C::STAGES], (q / C::STAGES) & 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    const uint32_t idesc = idesc_bf16(kBM, BN);
+    const uint32_t idesc = F == kFmtTF32 ? idesc_tf32(kBM, BN) : idesc_bf16(kBM, BN);
     const uint64_t dA0 = kmajor_desc<SW>(smem_u32(smem));  // stage 0, A piece 0
     uint32_t g = 0;
     int i = 0;  // local unit counter
@@ -526,21 +581,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
           }
           // (TMA -> MMA hand-off through the mbarrier needs no tcgen05 fence)
           const uint64_t da = dA0 + (uint64_t)((s * C::STAGE) >> 4);
-          const uint64_t db = da + (uint64_t)((kPieces * C::TILE_A) >> 4);
+          const uint64_t db = da + (uint64_t)((C::P * C::TILE_A) >> 4);
 #pragma unroll
           for (int kk = 0; kk < C::KSTEPS; ++kk) {
             const uint64_t a0 = da + (uint64_t)(kk * 2);
             const uint64_t a1 = a0 + (uint64_t)(C::TILE_A >> 4);
-            const uint64_t a2 = a0 + (uint64_t)(2 * C::TILE_A >> 4);
             const uint64_t b0 = db + (uint64_t)(kk * 2);
             const uint64_t b1 = b0 + (uint64_t)(C::TILE_B >> 4);
-            const uint64_t b2 = b0 + (uint64_t)(2 * C::TILE_B >> 4);
-            mma_bf16<kColNone>(dt, a2, b0, idesc, (kb | kk) != 0);
-            mma_bf16<kColFill>(dt, a1, b1, idesc, 1);
-            mma_bf16<kColLast>(dt, a1, b0, idesc, 1);
-            mma_bf16<kColFill>(dt, a0, b2, idesc, 1);
-            mma_bf16<kColUse>(dt, a0, b1, idesc, 1);
-            mma_bf16<kColLast>(dt, a0, b0, idesc, 1);
+            if constexpr (F == kFmtTF32) {
+              // (lo, hi), (hi, lo), (hi, hi): the lo x lo term (2^-22) is dropped
+              mma_tf32<kColNone>(dt, a1, b0, idesc, (kb | kk) != 0);
+              mma_tf32<kColFill>(dt, a0, b1, idesc, 1);
+              mma_tf32<kColLast>(dt, a0, b0, idesc, 1);
+            } else {
+              const uint64_t a2 = a0 + (uint64_t)(2 * C::TILE_A >> 4);
+              const uint64_t b2 = b0 + (uint64_t)(2 * C::TILE_B >> 4);
+              mma_bf16<kColNone>(dt, a2, b0, idesc, (kb | kk) != 0);
+              mma_bf16<kColFill>(dt, a1, b1, idesc, 1);
+              mma_bf16<kColLast>(dt, a1, b0, idesc, 1);
+              mma_bf16<kColFill>(dt, a0, b2, idesc, 1);
+              mma_bf16<kColUse>(dt, a0, b1, idesc, 1);
+              mma_bf16<kColLast>(dt, a0, b0, idesc, 1);
+            }
           }
           mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
         }
@@ -694,7 +756,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
 #pragma unroll
           for (int c = 0; c < NB; ++c) tmem_fence16(r[c]);
           if (mrow) {
-            if (mode == kPieces3) {
+            if (mode == kPieces3 && F == kFmtTF32) {  // two TF32 pieces, FP32 words
+              float* op = reinterpret_cast<float*>(D->outp[w.c_lo]);
+#pragma unroll
+              for (int jj = 0; jj < 16 * NB; ++jj) {
+                const int col = n0 + bt * 16 + jj;
+                if (col < N) {
+                  const int64_t o = (int64_t)col * M + m;
+                  float hi, lo;
+                  split2_tf32(__uint_as_float(r[jj / 16][jj % 16]), hi, lo);
+                  op[o] = hi;
+                  op[plane + o] = lo;
+                }
+              }
+            } else if (mode == kPieces3) {
               __nv_bfloat16* op = D->outp[w.c_lo];
 #pragma unroll
               for (int jj = 0; jj < 16 * NB; ++jj) {
@@ -1267,6 +1342,23 @@ __device__ __forceinline__ void store_pieces4(__nv_bfloat16* out, int64_t N, int
   }
 }
 
+// The same in the operand format F: for TF32, two FP32 words per value
+// (piece k of the four values at out + k * N + idx, 16-byte stores).
+template <int F>
+__device__ __forceinline__ void store_pieces_fmt(__nv_bfloat16* out, int64_t N, int64_t idx,
+                                                 const float (&w)[4]) {
+  if constexpr (F == kFmtTF32) {
+    float* o = reinterpret_cast<float*>(out);
+    float hi[4], lo[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) split2_tf32(w[j], hi[j], lo[j]);
+    *reinterpret_cast<float4*>(o + idx) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<float4*>(o + N + idx) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+  } else {
+    store_pieces4(out, N, idx, w);
+  }
+}
+
 // The tridiagonal coefficients of one component on one axis.
 struct Coef {
   float lo, up, b0, bn;
@@ -1279,7 +1371,7 @@ __device__ __forceinline__ Coef coef(const TridiagT<float>& A) { return Coef{A.l
 // loads (the planes, the y neighbours in 3D, the x values beyond the warp's
 // run) before any arithmetic, so that a warp keeps several planes of
 // loads in flight; the planes z - 1 and z + ZB carry over.
-template <bool D3, int ZB>
+template <bool D3, int ZB, int F = kFmtBF16>
 __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_constant__ PwLaunch L) {
   __shared__ PwDesc sd;
   int lb;
@@ -1379,8 +1471,8 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_
       }
       if (act) {
         const int64_t idx = (int64_t)zq * sz + col;
-        store_pieces4(wu, N, idx, ou);
-        store_pieces4(wv, N, idx, ov);
+        store_pieces_fmt<F>(wu, N, idx, ou);
+        store_pieces_fmt<F>(wv, N, idx, ov);
       }
     }
     pu[0] = pu[ZB];
@@ -1402,6 +1494,7 @@ constexpr int kZB2 = 4, kZB3 = 1;  // planes per iteration: 2D, 3D
 
 // D^c = G^c(U2, V2) - G^c(U, V) written as BF16 pieces [3][N] (Eq. 11,
 // second stage).
+template <int F = kFmtBF16>
 __global__ void __launch_bounds__(kPwThreads) rdiff_pieces_kernel(const __grid_constant__ PwLaunch L) {
   FLAT_PROLOGUE
   const ReactionT<float> rx = sd.a.rx;
@@ -1429,13 +1522,14 @@ __global__ void __launch_bounds__(kPwThreads) rdiff_pieces_kernel(const __grid_c
       du[j] = g2u - g0u;
       dv[j] = g2v - g0v;
     }
-    store_pieces4(sd.wu, N, 4 * g, du);
-    store_pieces4(sd.wv, N, 4 * g, dv);
+    store_pieces_fmt<F>(sd.wu, N, 4 * g, du);
+    store_pieces_fmt<F>(sd.wv, N, 4 * g, dv);
   }
 }
 
 // Lawson2b (Eq. 7) first pointwise stage, also used for the second:
 // W^c = U^c + factor tau G^c(U, V) as BF16 pieces [3][N].
+template <int F = kFmtBF16>
 __global__ void __launch_bounds__(kPwThreads) lawson_pre_pieces_kernel(const __grid_constant__ PwLaunch L,
                                                                        float factor) {
   FLAT_PROLOGUE
@@ -1463,8 +1557,8 @@ __global__ void __launch_bounds__(kPwThreads) lawson_pre_pieces_kernel(const __g
       wu[j] = uu + sc * gu;
       wv[j] = vv + sc * gv;
     }
-    store_pieces4(sd.wu, N, 4 * g, wu);
-    store_pieces4(sd.wv, N, 4 * g, wv);
+    store_pieces_fmt<F>(sd.wu, N, 4 * g, wu);
+    store_pieces_fmt<F>(sd.wv, N, 4 * g, wv);
   }
 }
 
@@ -1520,6 +1614,19 @@ __global__ void split_matrix_kernel(const double* __restrict__ src, __nv_bfloat1
   }
 }
 
+// Phi (FP64, row-major n x n) -> two TF32 pieces [2][n][n] (FP32 words):
+// hi = tf32(x), lo = tf32(x - hi) with the difference taken in FP64.
+__global__ void split_matrix_tf32_kernel(const double* __restrict__ src, float* __restrict__ dst,
+                                         int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = src[i];
+    const float hi = tf32_rna((float)x);
+    dst[i] = hi;
+    dst[count + i] = tf32_rna((float)(x - (double)hi));
+  }
+}
+
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -1538,13 +1645,16 @@ cudaError_t get_encoder() {
 // copy brings a K chunk of all three pieces of a tile, laid out in shared
 // memory as [piece][row][SW bytes].  (The copy engine's cost is largely per
 // instruction, so one large box moves data much faster than three small ones.)
+// TF32 pieces: [2][rows][K] FP32 words, box {SW/4, box_rows, 2}.
 cudaError_t encode_pieces(CUtensorMap* map, const void* base, int64_t K, int64_t rows,
-                          int box_rows, int sw) {
-  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)kPieces};
-  cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)(K * rows) * 2};
-  cuuint32_t box[3] = {(cuuint32_t)(sw / 2), (cuuint32_t)box_rows, (cuuint32_t)kPieces};
+                          int box_rows, int sw, int fmt = kFmtBF16) {
+  const int np = fmt == kFmtTF32 ? 2 : kPieces, esz = fmt == kFmtTF32 ? 4 : 2;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)np};
+  cuuint64_t strides[2] = {(cuuint64_t)K * esz, (cuuint64_t)(K * rows) * esz};
+  cuuint32_t box[3] = {(cuuint32_t)(sw / esz), (cuuint32_t)box_rows, (cuuint32_t)np};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
+  CUresult r = g_encode(map, fmt == kFmtTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                        3, const_cast<void*>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         sw == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1785,6 +1895,7 @@ struct TcState {
   CUtensorMap amap[2][2][3];     // [b][c][mu]: buffer b viewed as [3][N/n_mu][n_mu]
   CUtensorMap bmap[2][3][3];     // [c][mu][ell]
   int variant;
+  int fmt;       // operand format: kFmtBF16 (three BF16 pieces) or kFmtTF32 (two TF32 pieces)
   int fuse;      // 1: fuse the stage-1 combination into the last stage-1 product
   int num_sms;
   int slots;     // resident CTAs (or CTA pairs) of the mode-product kernel
@@ -1917,7 +2028,7 @@ void tc_free(TcOperands* t) {
 
 cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t n[3],
                        double* const master[2][3][4], cudaStream_t s) {
-  if (prec != ADR_BF16X3) return cudaErrorNotSupported;
+  if (prec != ADR_BF16X3 && prec != ADR_TF32X3) return cudaErrorNotSupported;
   for (int m = 0; m < d; ++m)
     if (n[m] % 8 != 0) return cudaErrorNotSupported;  // TMA row strides: 16-byte multiples
   cudaError_t e = get_encoder();
@@ -1929,12 +2040,17 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     if ((e = set_smem_attr<64, 64>()) != cudaSuccess) return e;
     if ((e = set_smem_attr_pair<64>()) != cudaSuccess) return e;
     if ((e = set_smem_attr_pair<128>()) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(tc_mode_kernel<128, 128, false, false, kFmtTF32>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  TcCfg<128, 128, kFmtTF32>::SMEM)) != cudaSuccess)
+      return e;
     attr_set = true;
   }
   TcState* S = new TcState();
   t->work[0] = S;
   t->prec = prec;
   S->d = d;
+  S->fmt = prec == ADR_TF32X3 ? kFmtTF32 : kFmtBF16;
   // Default kernel: on grids of about a million points and more, the
   // CTA-pair kernel (256 x 128 tiles over two SMs, 128-byte swizzle, three
   // 72 KB stages: the tensor pipe stays fed, and each SM streams half of B);
@@ -1960,6 +2076,10 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     S->fuse = f >= 0 && f <= 2 ? f : 0;
   }
   if (kVariants[S->variant].cta2) S->fuse = 0;  // the CTA-pair kernel has neither epilogue
+  if (S->fmt == kFmtTF32) {  // TF32 pieces: the one-CTA kernel, 128-byte swizzle, plain epilogues
+    S->variant = 1;
+    S->fuse = 0;
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   S->num_sms = 148;
@@ -1995,21 +2115,26 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
       for (int l = 0; l < 3; ++l) {
         if ((scheme == ADR_LAWSON2B) != (l == 0)) continue;  // only the matrices the scheme uses
         const int64_t nn = n[m] * n[m];
-        e = alloc((void**)&S->phi[c][m][l], (size_t)kPieces * nn * 2);
+        const size_t pb = S->fmt == kFmtTF32 ? 2 * 4 : (size_t)kPieces * 2;  // piece bytes per value
+        e = alloc((void**)&S->phi[c][m][l], pb * nn);
         if (e != cudaSuccess) return e;
-        split_matrix_kernel<<<grid_for(nn), 256, 0, s>>>(master[c][m][1 + l], S->phi[c][m][l], nn);
+        if (S->fmt == kFmtTF32)
+          split_matrix_tf32_kernel<<<grid_for(nn), 256, 0, s>>>(master[c][m][1 + l],
+                                                                 (float*)S->phi[c][m][l], nn);
+        else
+          split_matrix_kernel<<<grid_for(nn), 256, 0, s>>>(master[c][m][1 + l], S->phi[c][m][l], nn);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = encode_pieces(&S->bmap[c][m][l], S->phi[c][m][l], n[m], n[m],
-                          kVariants[S->variant].cta2 ? bn / 2 : bn, sw);
+                          kVariants[S->variant].cta2 ? bn / 2 : bn, sw, S->fmt);
         if (e != cudaSuccess) return e;
       }
   for (int b = 0; b < 2; ++b)
     for (int c = 0; c < 2; ++c) {
-      e = alloc((void**)&S->buf[b][c], (size_t)kPieces * S->N * 2);
+      e = alloc((void**)&S->buf[b][c], (S->fmt == kFmtTF32 ? 8 : (size_t)kPieces * 2) * S->N);
       if (e != cudaSuccess) return e;
       for (int m = 0; m < d; ++m) {
-        e = encode_pieces(&S->amap[b][c][m], S->buf[b][c], n[m], S->N / n[m], kBM, sw);
+        e = encode_pieces(&S->amap[b][c][m], S->buf[b][c], n[m], S->N / n[m], kBM, sw, S->fmt);
         if (e != cudaSuccess) return e;
       }
     }
@@ -2091,6 +2216,7 @@ cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v) {
 // batch), following the plan's operation list.
 struct GroupStep {
   int d, variant, num_sms, nsolves;  // num_sms: resident CTAs or CTA pairs of the TC kernel
+  int fmt;                           // operand format of the pieces
   int np, nops;
   TcOp ops[16];
   const TcPassDesc* desc;   // [np][nsolves]
@@ -2116,6 +2242,11 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
     switch (op.kind) {
       case kOpRhs:
         e = timed_kernel(ctl, KC_RHS, N * 2.0 * (6.0 * G.d + 10.0), N * (8.0 + 12.0), [&] {
+          if (G.fmt == kFmtTF32)
+            return G.d == 3 ? launch_k(rhs_pieces_kernel<true, kZB3, kFmtTF32>, dim3(G.rhs_blocks),
+                                       dim3(kPwThreads), 0, st, G.rhs)
+                            : launch_k(rhs_pieces_kernel<false, kZB2, kFmtTF32>, dim3(G.rhs_blocks),
+                                       dim3(kPwThreads), 0, st, G.rhs);
           if (G.d == 3)
             return launch_k(rhs_pieces_kernel<true, kZB3>, dim3(G.rhs_blocks), dim3(kPwThreads), 0,
                             st, G.rhs);
@@ -2125,12 +2256,18 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
         break;
       case kOpRdiff:
         e = timed_kernel(ctl, KC_RDIFF, N * 2.0 * 12.0, N * (16.0 + 12.0), [&] {
-          return launch_k(rdiff_pieces_kernel, dim3(G.flat_blocks), dim3(kPwThreads), 0, st, G.flat);
+          if (G.fmt == kFmtTF32)
+            return launch_k(rdiff_pieces_kernel<kFmtTF32>, dim3(G.flat_blocks), dim3(kPwThreads), 0,
+                            st, G.flat);
+          return launch_k(rdiff_pieces_kernel<>, dim3(G.flat_blocks), dim3(kPwThreads), 0, st, G.flat);
         });
         break;
       case kOpLawsonPre:
         e = timed_kernel(ctl, KC_LAWSON_PW, N * 2.0 * 12.0, N * (8.0 + 12.0), [&] {
-          return launch_k(lawson_pre_pieces_kernel, dim3(G.flat_blocks), dim3(kPwThreads), 0, st,
+          if (G.fmt == kFmtTF32)
+            return launch_k(lawson_pre_pieces_kernel<kFmtTF32>, dim3(G.flat_blocks), dim3(kPwThreads),
+                            0, st, G.flat, op.factor);
+          return launch_k(lawson_pre_pieces_kernel<>, dim3(G.flat_blocks), dim3(kPwThreads), 0, st,
                           G.flat, op.factor);
         });
         break;
@@ -2158,6 +2295,11 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
         e = timed_kernel(ctl, KC_MODE_TC, G.flops[p], G.bytes[p],
                          [&] {
                            if (G.xchg[p]) return launch_xchg(G.variant, G.xslots, st, L);
+                           if (G.fmt == kFmtTF32) {
+                             dim3 grid((unsigned)(L.nunits < G.num_sms ? L.nunits : G.num_sms));
+                             return launch_k(tc_mode_kernel<128, 128, false, false, kFmtTF32>, grid,
+                                             dim3(kThreads), TcCfg<128, 128, kFmtTF32>::SMEM, st, L);
+                           }
                            return launch_tc(G.variant, G.num_sms, st, L, G.pair[p] != 0);
                          });
       } break;
@@ -2171,11 +2313,12 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
 
 static void pass_work(const TcState* S, const TcPass& ps, double& flops, double& bytes) {
   const double N = (double)S->N, nmu = (double)S->n[ps.mu];
+  const double pb = S->fmt == kFmtTF32 ? 8.0 : 6.0;  // piece bytes per value
   flops = 2.0 * 2.0 * nmu * N;
-  bytes = 2.0 * (6.0 * N + 6.0 * nmu * nmu);
-  if (ps.mode == kPieces3) bytes += 2.0 * 6.0 * N;
+  bytes = 2.0 * (pb * N + pb * nmu * nmu);
+  if (ps.mode == kPieces3) bytes += 2.0 * pb * N;
   if (ps.mode == kAxpy) bytes += 2.0 * 8.0 * N;
-  if (ps.mode == kStage1 || ps.mode == kStage1X) bytes += 2.0 * (8.0 + 6.0) * N;
+  if (ps.mode == kStage1 || ps.mode == kStage1X) bytes += 2.0 * (8.0 + pb) * N;
 }
 
 static void fill_ops(GroupStep& G, const TcState* S) {
@@ -2187,6 +2330,7 @@ static void fill_ops(GroupStep& G, const TcState* S) {
     G.xchg[p] = S->passes[p].mode == kStage1X;
   }
   G.xslots = S->xslots;
+  G.fmt = S->fmt;
 }
 
 cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
@@ -2387,8 +2531,9 @@ static void batch_free(adr_batch B) {
 static bool same_sequence(const adr_plan_s* a, const adr_plan_s* b) {
   const TcState* A = (const TcState*)a->tc.work[0];
   const TcState* S = (const TcState*)b->tc.work[0];
-  if (a->prec != ADR_BF16X3 || b->prec != ADR_BF16X3 || !A || !S) return false;
-  if (S->d != A->d || S->variant != A->variant || S->scheme != A->scheme ||
+  if (a->prec != b->prec || (a->prec != ADR_BF16X3 && a->prec != ADR_TF32X3) || !A || !S)
+    return false;
+  if (S->d != A->d || S->variant != A->variant || S->fmt != A->fmt || S->scheme != A->scheme ||
       S->passes.size() != A->passes.size() || S->ops.size() != A->ops.size())
     return false;
   for (size_t p = 0; p < S->passes.size(); ++p)

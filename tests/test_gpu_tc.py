@@ -171,3 +171,44 @@ def test_largest_direction_bf16x3(adr):
     Ur, Vr = schemes.etd2rkds_solve(plan, u0, v0, p.nsteps)
     U, V, _ = run(adr, p, u0, v0, p.nsteps)
     assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+@pytest.mark.parametrize("n,model", [((200, 136), wl.FHN), ((40, 24, 56), wl.BRUSSELATOR),
+                                     ((128, 256), wl.SCHNAKENBERG)])
+def test_tf32x3_ragged_shapes(adr, n, model):
+    """TF32 hi + lo tensor-core products (kind::tf32, three MMAs) on grids
+    that are not multiples of the tile sizes, against the oracle."""
+    d = len(n)
+    params = {wl.SCHNAKENBERG: (200.0, 0.1, 0.9), wl.FHN: (0.05, 2.0, -0.03),
+              wl.BRUSSELATOR: (1.0, 3.0)}[model]
+    p = wl.Problem(d=d, n=n, lo=(0.0,) * d, hi=(1.0,) * d, diff=(0.05, 0.3),
+                   adv=((0.2, -0.1, 0.3)[:d], (-0.2, 0.1, 0.05)[:d]), model=model,
+                   params=params, tau=2e-3, nsteps=10, seed=13)
+    u0, v0 = inputs(p, kind="uniform")
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, p.nsteps)
+    U, V, st = run(adr, p, u0, v0, p.nsteps, wl.TF32X3)
+    assert st["kernels"]["mode_product_tc"]["count"] == 2 * d * p.nsteps
+    assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+def test_tf32x3_fhn_1024_full_size_steps(adr):
+    p = wl.fhn_1024(precision=wl.TF32X3)
+    u0, v0 = inputs(p)
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, 3)
+    U, V, _ = run(adr, p, u0, v0, 3, wl.TF32X3)
+    assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+def test_split_precisions_ordered_by_accuracy(adr):
+    """On a 256^2 FHN run of 100 steps: BF16x3 (about 24 bits per operand)
+    is at least as accurate as TF32x3 (about 22 bits), and both stay within
+    a small factor of plain FP32."""
+    p = wl.fhn_1024(n=256, nsteps=100)
+    u0, v0 = inputs(p)
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, p.nsteps)
+    errs = {}
+    for prec in (wl.BF16X3, wl.TF32X3, wl.FP32):
+        U, V, _ = run(adr, p, u0, v0, p.nsteps, prec)
+        errs[prec] = oracle.max_rel_err(U, V, Ur, Vr)
+    assert errs[wl.BF16X3] <= 1.5 * errs[wl.TF32X3], errs
+    assert errs[wl.TF32X3] <= 20.0 * errs[wl.FP32], errs
