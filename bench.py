@@ -267,6 +267,11 @@ def run_batch(args):
     t0 = time.perf_counter()
     plans = [adr.Plan(p) for p in probs]
     plan_ms = 1e3 * (time.perf_counter() - t0)
+    # one kernel for the whole batch, chosen by timing the batch's grouped
+    # launches with each kernel (the plans keep their matrix functions)
+    t0 = time.perf_counter()
+    kernel, tune_ms = adr.autotune_batch(plans)
+    tune_s = time.perf_counter() - t0
     dt = adr.state_dtype(prec)
     init = []
     for p in probs:
@@ -385,7 +390,10 @@ def run_batch(args):
                            "points": npts, "time_steps_per_bench_step": nts,
                            "precision": args.precision, "grouped": batch.grouped,
                            "l2": "flushed between timed solves (256 MB write)",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}",
+                           "kernel": {"chosen": kernel, "by": "autotune_batch (whole batch)",
+                                      "ms_per_step": {str(k): round(t, 4) for k, t in tune_ms.items()},
+                                      "tuning_s": round(tune_s, 2)}},
                 "max_rel_err_vs_fp64": max_rel, "max_rel_err_sample": "every 32nd solve",
                 "plan_ms": plan_ms, "e2e": e2e, "gpu_launches": launches,
                 "kernel_timing": "second pass of the same solves; the graph chunks are replayed "
@@ -558,8 +566,13 @@ def main():
     v = torch.empty_like(v0)
     stream = torch.cuda.current_stream()
 
+    # kernel choice by the library's autotuner (times each tensor-core kernel
+    # on this grid), then the plan
     t0 = time.perf_counter()
-    plan = adr.Plan(p)
+    kernel, tune_ms = adr.autotune(p) if prec in (wl.BF16X3, wl.TF32X3) else (-1, {})
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plan = adr.Plan(p, kernel=kernel)
     plan_ms = 1e3 * (time.perf_counter() - t0)
 
     # accuracy of this precision against an FP64 GPU solve of the same data
@@ -717,7 +730,10 @@ def main():
                 "config": {"workload": p.name, "grid": list(p.n[: p.d]), "tau": p.tau,
                            "time_steps_per_bench_step": nts, "precision": args.precision,
                            "l2": "flushed between timed solves (256 MB write)",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}",
+                           "kernel": {"chosen": kernel, "by": "adr_autotune",
+                                      "ms_per_step": {str(k): round(t, 4) for k, t in tune_ms.items()},
+                                      "tuning_s": round(tune_s, 2)}},
                 "max_rel_err_vs_fp64": max_rel, "plan_ms": plan_ms,
                 "e2e": e2e, "gpu_launches": launches,
                 "kernel_timing": "second pass of the same solves; the graph chunks are replayed "

@@ -135,6 +135,43 @@ typedef struct adr_plan_s* adr_plan;
  *   out     : receives the plan; untouched on failure. */
 adr_status adr_plan_create(const adr_problem* problem, void* stream, adr_plan* out);
 
+/* Kernel choice of a tensor-core plan (ADR_BF16X3 / ADR_TF32X3), as chosen
+ * by adr_autotune.  The paper has no counterpart: it concerns only how the
+ * mode products of Eq. 11 are tiled on the GPU, not what they compute.
+ *   kernel : -1 = the library's choice from the grid size;
+ *            0 = one CTA per 128 x 128 tile, 64-byte swizzle, 4 stages;
+ *            1 = one CTA per 128 x 128 tile, 128-byte swizzle, 2 stages;
+ *            2 = one CTA per 128 x 64 tile, 64-byte swizzle;
+ *            3 / 4 = two-SM (cta_group::2) 256 x 128 tiles, 64- / 128-byte
+ *            swizzle.  TF32X3 plans always use 1.
+ * Every kernel computes the same products in the same order per output. */
+typedef struct {
+  int32_t kernel;
+  int32_t reserved[7];
+} adr_tuning;
+
+/* adr_plan_create with an explicit kernel choice (tuning may be NULL: the
+ * library's choice).  Other precisions ignore it. */
+adr_status adr_plan_create_tuned(const adr_problem* problem, const adr_tuning* tuning,
+                                 void* stream, adr_plan* out);
+
+/* Switch an existing tensor-core plan to another kernel (adr_tuning.kernel)
+ * without recomputing its FP64 matrix functions: synchronises the plan's
+ * stream and rebuilds only the kernel operands, tensor maps and graphs.
+ * Destroy any batch that contains the plan first.  FP32 / FP64 plans: no-op.
+ * On failure the plan cannot step until a later call succeeds. */
+adr_status adr_plan_set_kernel(adr_plan plan, int32_t kernel);
+
+/* Autotuner: for a tensor-core problem, builds a plan with each candidate
+ * kernel, advances scratch state (allocated here, zero-filled) by 2 + nsteps
+ * steps on `stream` and times the last nsteps with CUDA events.  best
+ * receives the fastest kernel; ms_per_step[k] the time per step of kernel k
+ * (-1 when k is not a candidate or failed).  For FP32 / FP64 problems there
+ * is nothing to tune: best->kernel = -1 and every entry is -1.  Synchronous;
+ * allocates and frees device memory.  nsteps in [1, 1024]. */
+adr_status adr_autotune(const adr_problem* problem, void* stream, int32_t nsteps,
+                        adr_tuning* best, float ms_per_step[8]);
+
 /* Move a plan to another CUDA stream (as void*, 0 = default stream): later
  * calls enqueue there.  Synchronises the old stream first, so work already
  * enqueued is complete.  Lets a plan be built on one stream (for instance

@@ -69,16 +69,25 @@ def _stream_handle(stream) -> int:
 class Plan:
     """An adr_plan: FP64 matrix functions on the GPU, operands, workspace."""
 
-    def __init__(self, problem, stream=None):
+    def __init__(self, problem, stream=None, kernel: int = -1):
+        """kernel: tensor-core kernel variant (adr_tuning.kernel; -1 = the
+        library's choice from the grid size, see autotune)."""
         self.problem = problem
         self.precision = int(problem.precision)
         self.shape = tuple(reversed([int(x) for x in problem.n[: problem.d]]))
         self._stream = stream
         self._p = _abi.AdrPlan()
         self._cprob = make_problem(problem)
-        _abi.check(lib().adr_plan_create(ctypes.byref(self._cprob),
-                                         ctypes.c_void_p(_stream_handle(stream)),
-                                         ctypes.byref(self._p)))
+        tuning = _abi.AdrTuning()
+        tuning.kernel = int(kernel)
+        _abi.check(lib().adr_plan_create_tuned(ctypes.byref(self._cprob), ctypes.byref(tuning),
+                                               ctypes.c_void_p(_stream_handle(stream)),
+                                               ctypes.byref(self._p)))
+
+    def set_kernel(self, kernel: int):
+        """adr_plan_set_kernel: switch the tensor-core kernel (see autotune)
+        keeping the plan's matrix functions."""
+        _abi.check(lib().adr_plan_set_kernel(self._p, int(kernel)))
 
     def set_stream(self, stream=None):
         """adr_plan_set_stream: later calls enqueue on `stream` (default: current)."""
@@ -165,6 +174,63 @@ def _stats_dict(st) -> dict:
             "flops": float(st.flops[k]), "bytes": float(st.bytes[k])}
     return {"launches": int(st.launches), "steps": int(st.steps), "timing": bool(st.timing),
             "device_error": int(st.device_error), "kernels": kernels}
+
+
+_tuned = {}
+
+
+def autotune(problem, nsteps: int = 32, stream=None, cache: bool = True):
+    """adr_autotune: time every tensor-core kernel variant on this problem's
+    grid (scratch state, nsteps steps each) and return (best kernel, {kernel:
+    ms per step}).  Results are cached per (d, grid, precision, scheme) in
+    this process.  FP32 / FP64 problems return (-1, {})."""
+    key = (int(problem.d), tuple(int(x) for x in problem.n[: problem.d]),
+           int(problem.precision), int(getattr(problem, "scheme", 0)))
+    if cache and key in _tuned:
+        return _tuned[key]
+    cp = make_problem(problem)
+    best = _abi.AdrTuning()
+    ms = (ctypes.c_float * 8)()
+    _abi.check(lib().adr_autotune(ctypes.byref(cp), ctypes.c_void_p(_stream_handle(stream)),
+                                  int(nsteps), ctypes.byref(best), ms))
+    out = (int(best.kernel), {k: float(ms[k]) for k in range(8) if ms[k] >= 0})
+    if cache:
+        _tuned[key] = out
+    return out
+
+
+def autotune_batch(plans, nsteps: int = 8, stream=None):
+    """Kernel choice for a batch: every tensor-core kernel is timed on the
+    grouped launches of the whole batch (its plans switched with
+    adr_plan_set_kernel, zero-filled scratch states, two warm-up steps, then
+    nsteps timed with CUDA events); the plans are left on the fastest kernel,
+    which is returned with {kernel: ms per step}."""
+    import torch
+    plans = list(plans)
+    if not plans or plans[0].precision not in (BF16X3, TF32X3):
+        return -1, {}
+    cands = [1] if plans[0].precision == TF32X3 else [0, 1, 2, 3, 4]
+    st = torch.cuda.current_stream() if stream is None else stream
+    us = [torch.zeros(pl.shape, dtype=torch.float32, device="cuda") for pl in plans]
+    vs = [torch.zeros(pl.shape, dtype=torch.float32, device="cuda") for pl in plans]
+    times = {}
+    for k in cands:
+        for pl in plans:
+            pl.set_kernel(k)
+        b = Batch(plans, stream=st)
+        b.step(us, vs, 2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        b.step(us, vs, nsteps)
+        e1.record(st)
+        e1.synchronize()
+        times[k] = e0.elapsed_time(e1) / nsteps
+        b.close()
+    best = min(times, key=times.get)
+    for pl in plans:
+        pl.set_kernel(best)
+    return best, times
 
 
 class Batch:

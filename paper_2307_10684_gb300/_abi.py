@@ -32,6 +32,10 @@ class AdrStats(ctypes.Structure):
                 ("bytes", c_double * 16)]
 
 
+class AdrTuning(ctypes.Structure):
+    _fields_ = [("kernel", c_int32), ("reserved", c_int32 * 7)]
+
+
 class AdrPlan(ctypes.c_void_p):
     pass
 
@@ -39,6 +43,11 @@ class AdrPlan(ctypes.c_void_p):
 # name -> (restype, argtypes); every symbol include/adr.h declares
 SIGNATURES = {
     "adr_plan_create": (c_int32, [ctypes.POINTER(AdrProblem), c_void_p, ctypes.POINTER(AdrPlan)]),
+    "adr_plan_create_tuned": (c_int32, [ctypes.POINTER(AdrProblem), ctypes.POINTER(AdrTuning),
+                                        c_void_p, ctypes.POINTER(AdrPlan)]),
+    "adr_autotune": (c_int32, [ctypes.POINTER(AdrProblem), c_void_p, c_int32,
+                               ctypes.POINTER(AdrTuning), ctypes.POINTER(ctypes.c_float)]),
+    "adr_plan_set_kernel": (c_int32, [AdrPlan, c_int32]),
     "adr_plan_destroy": (c_int32, [AdrPlan]),
     "adr_plan_set_stream": (c_int32, [AdrPlan, c_void_p]),
     "adr_step": (c_int32, [AdrPlan, c_void_p, c_void_p, c_int64]),

@@ -185,6 +185,7 @@ struct adr_plan_s {
   void* g_u;
   void* g_v;
   int64_t g_launches;        // kernels per replay
+  int tc_variant;            // requested tensor-core kernel (-1: the library's choice)
   // timing mode: the same chunk captured with an event-record node before and
   // after every kernel, so that per-kernel times exclude host launch gaps
   cudaGraphExec_t gexec_timed;
@@ -199,8 +200,9 @@ static const char* const kClassNames[KC_COUNT] = {"rhs_stencil_reaction", "react
                                                   "lawson_pointwise"};
 void tc_init(TcOperands* t);
 void tc_free(TcOperands* t);
+// variant_req: -1 = the library's choice, else a kernel variant (adr_tuning)
 cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t n[3],
-                       double* const master[2][3][4], cudaStream_t s);
+                       double* const master[2][3][4], cudaStream_t s, int variant_req = -1);
 cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v);
 cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v);
 int* tc_error_word(TcOperands* t);

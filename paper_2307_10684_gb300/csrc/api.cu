@@ -240,7 +240,14 @@ static void plan_free(adr_plan P) {
 }
 
 extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, adr_plan* out) {
+  return adr_plan_create_tuned(problem, nullptr, stream, out);
+}
+
+extern "C" adr_status adr_plan_create_tuned(const adr_problem* problem, const adr_tuning* tuning,
+                                            void* stream, adr_plan* out) {
   if (!out) return fail(ADR_EINVAL, "out is NULL");
+  if (tuning && (tuning->kernel < -1 || tuning->kernel > 4))
+    return fail(ADR_EINVAL, "adr_tuning.kernel must be -1 or 0..4");
   adr_status st = validate(problem);
   if (st != ADR_OK) return st;
   adr_plan P = new adr_plan_s();
@@ -273,6 +280,7 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
   memset(P->acc_bytes, 0, sizeof(P->acc_bytes));
   memset(P->acc_count, 0, sizeof(P->acc_count));
   P->g_launches = 0;
+  P->tc_variant = tuning ? tuning->kernel : -1;
   P->cap_stream = nullptr;
   P->use_graphs = 1;
   if (const char* ev = getenv("ADR_GRAPHS")) P->use_graphs = atoi(ev) != 0;
@@ -343,7 +351,7 @@ extern "C" adr_status adr_plan_create(const adr_problem* problem, void* stream, 
     PLAN_TRY(plan_alloc(P, &P->bufB[c], sb));
   }
   if (P->prec == ADR_TF32X3 || P->prec == ADR_BF16X3) {
-    e = tc_prepare(&P->tc, P->prec, P->scheme, P->d, P->n, P->master, P->stream);
+    e = tc_prepare(&P->tc, P->prec, P->scheme, P->d, P->n, P->master, P->stream, P->tc_variant);
     if (e != cudaSuccess) {
       const bool unsup = (e == cudaErrorNotSupported);
       set_error(std::string("adr_plan_create: tensor-core operands: ") + cudaGetErrorString(e));
@@ -672,3 +680,88 @@ extern "C" const char* adr_status_str(adr_status s) {
 }
 
 extern "C" const char* adr_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" adr_status adr_plan_set_kernel(adr_plan P, int32_t kernel) {
+  if (!P) return fail(ADR_EINVAL, "plan is NULL");
+  if (kernel < -1 || kernel > 4) return fail(ADR_EINVAL, "kernel must be -1 or 0..4");
+  if (P->prec != ADR_BF16X3 && P->prec != ADR_TF32X3) return ADR_OK;
+  ADR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->gexec_timed) cudaGraphExecDestroy(P->gexec_timed);
+  P->gexec = P->gexec_timed = nullptr;
+  P->g_u = P->g_v = P->gt_u = P->gt_v = nullptr;
+  tc_free(&P->tc);
+  tc_init(&P->tc);
+  P->tc_variant = kernel;
+  cudaError_t e = tc_prepare(&P->tc, P->prec, P->scheme, P->d, P->n, P->master, P->stream, kernel);
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorNotSupported ? ADR_EUNSUPPORTED : ADR_ECUDA,
+                std::string("adr_plan_set_kernel: ") + cudaGetErrorString(e));
+  return ADR_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+extern "C" adr_status adr_autotune(const adr_problem* problem, void* stream, int32_t nsteps,
+                                   adr_tuning* best, float ms_per_step[8]) {
+  if (!problem || !best || !ms_per_step) return fail(ADR_EINVAL, "NULL argument");
+  if (nsteps < 1 || nsteps > 1024) return fail(ADR_EINVAL, "adr_autotune: nsteps must be in [1, 1024]");
+  adr_status st = validate(problem);
+  if (st != ADR_OK) return st;
+  memset(best, 0, sizeof(*best));
+  best->kernel = -1;
+  for (int k = 0; k < 8; ++k) ms_per_step[k] = -1.f;
+  const int prec = problem->precision;
+  if (prec != ADR_BF16X3 && prec != ADR_TF32X3) return ADR_OK;  // nothing to tune
+  size_t N = 1;
+  for (int m = 0; m < problem->d; ++m) N *= (size_t)problem->n[m];
+  cudaStream_t s = (cudaStream_t)stream;
+  void* u = nullptr;
+  void* v = nullptr;
+  ADR_CUDA_TRY(cudaMalloc(&u, N * sizeof(float)));
+  if (cudaMalloc(&v, N * sizeof(float)) != cudaSuccess) {
+    cudaFree(u);
+    return fail(ADR_ENOMEM, "adr_autotune: scratch state");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = -1.f;
+  const int candidates[5] = {0, 1, 2, 3, 4};
+  const int ncand = prec == ADR_TF32X3 ? 1 : 5;
+  for (int c = 0; c < ncand; ++c) {
+    const int k = prec == ADR_TF32X3 ? 1 : candidates[c];
+    adr_tuning t;
+    memset(&t, 0, sizeof(t));
+    t.kernel = k;
+    adr_plan P = nullptr;
+    if (adr_plan_create_tuned(problem, &t, stream, &P) != ADR_OK) continue;
+    bool ok = cudaMemsetAsync(u, 0, N * sizeof(float), s) == cudaSuccess &&
+              cudaMemsetAsync(v, 0, N * sizeof(float), s) == cudaSuccess &&
+              adr_step(P, u, v, 2) == ADR_OK && cudaEventRecord(e0, s) == cudaSuccess &&
+              adr_step(P, u, v, nsteps) == ADR_OK && cudaEventRecord(e1, s) == cudaSuccess &&
+              cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0.f;
+    if (ok) ok = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    if (ok && tc_error_word(&P->tc)) {
+      int h = 0;
+      ok = cudaMemcpy(&h, tc_error_word(&P->tc), sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
+           h == 0;
+    }
+    adr_plan_destroy(P);
+    if (!ok) {
+      cudaGetLastError();
+      continue;
+    }
+    ms_per_step[k] = ms / (float)nsteps;
+    if (best_ms < 0.f || ms_per_step[k] < best_ms) {
+      best_ms = ms_per_step[k];
+      best->kernel = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(u);
+  cudaFree(v);
+  if (best->kernel < 0) return fail(ADR_EUNSUPPORTED, "adr_autotune: no kernel ran");
+  return ADR_OK;
+}

@@ -2027,7 +2027,7 @@ void tc_free(TcOperands* t) {
 }
 
 cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t n[3],
-                       double* const master[2][3][4], cudaStream_t s) {
+                       double* const master[2][3][4], cudaStream_t s, int variant_req) {
   if (prec != ADR_BF16X3 && prec != ADR_TF32X3) return cudaErrorNotSupported;
   for (int m = 0; m < d; ++m)
     if (n[m] % 8 != 0) return cudaErrorNotSupported;  // TMA row strides: 16-byte multiples
@@ -2062,6 +2062,7 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     for (int m = 0; m < d; ++m) npts *= n[m];
     S->variant = npts >= 1000000 ? 4 : 0;
   }
+  if (variant_req >= 0 && variant_req < kNumVariants) S->variant = variant_req;
   if (const char* ev = getenv("ADR_TC_VARIANT")) {
     const int v = atoi(ev);
     if (v >= 0 && v < kNumVariants) S->variant = v;

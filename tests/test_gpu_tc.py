@@ -212,3 +212,92 @@ def test_split_precisions_ordered_by_accuracy(adr):
         errs[prec] = oracle.max_rel_err(U, V, Ur, Vr)
     assert errs[wl.BF16X3] <= 1.5 * errs[wl.TF32X3], errs
     assert errs[wl.TF32X3] <= 20.0 * errs[wl.FP32], errs
+
+
+@pytest.mark.parametrize("n", [(256, 384), (40, 24, 56)])
+def test_every_kernel_choice_gives_the_same_result(adr, n):
+    """Plans created with each tensor-core kernel (adr_plan_create_tuned)
+    accumulate every output's products in the same K order, so their results
+    are bitwise identical."""
+    import torch
+    d = len(n)
+    p = wl.Problem(d=d, n=n, lo=(0.0,) * d, hi=(1.0,) * d, diff=(0.05, 0.3),
+                   adv=((0.2, -0.1, 0.3)[:d], (-0.2, 0.1, 0.05)[:d]), model=wl.FHN,
+                   params=(0.05, 2.0, -0.03), tau=2e-3, nsteps=5, precision=wl.BF16X3, seed=29)
+    u0, v0 = inputs(p, kind="uniform")
+    outs = []
+    for k in range(5):
+        u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+        with adr.Plan(p, kernel=k) as plan:
+            plan.step(u, v, p.nsteps)
+        torch.cuda.synchronize()
+        outs.append((u.cpu(), v.cpu()))
+    for k in range(1, 5):
+        assert torch.equal(outs[k][0], outs[0][0]) and torch.equal(outs[k][1], outs[0][1]), k
+
+
+def test_autotune_times_every_candidate(adr):
+    """adr_autotune times each tensor-core kernel on the problem's grid and
+    returns the fastest; FP32 problems have nothing to tune."""
+    p = wl.fhn_1024(precision=wl.BF16X3, n=512)
+    best, ms = adr.autotune(p, nsteps=8, cache=False)
+    assert set(ms) == {0, 1, 2, 3, 4} and all(t > 0 for t in ms.values())
+    assert best == min(ms, key=ms.get)
+    bt, mt = adr.autotune(p.replace(precision=wl.TF32X3), nsteps=8, cache=False)
+    assert bt == 1 and set(mt) == {1}
+    assert adr.autotune(p.replace(precision=wl.FP32), nsteps=8, cache=False) == (-1, {})
+
+
+@pytest.mark.gpu
+def test_set_kernel_keeps_the_plan_and_its_results(adr):
+    """adr_plan_set_kernel swaps the tensor-core kernel of a live plan; its
+    steps stay bitwise equal to a plan created with that kernel."""
+    import torch
+    p = wl.fhn_1024(precision=wl.BF16X3, n=256, nsteps=20)
+    u0, v0 = wl.initial_data(p)
+
+    def run(plan):
+        u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+        plan.step(u, v, p.nsteps)
+        torch.cuda.synchronize()
+        return u.cpu(), v.cpu()
+
+    with adr.Plan(p, kernel=4) as ref_plan:
+        ref = run(ref_plan)
+    with adr.Plan(p, kernel=0) as plan:
+        run(plan)
+        for k in (4, 2, 3):
+            plan.set_kernel(k)
+            got = run(plan)
+            assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), k
+
+
+@pytest.mark.gpu
+def test_autotune_batch_times_the_whole_batch(adr):
+    """autotune_batch times every kernel on the batch itself and leaves its
+    plans on the fastest one, which then steps like any batch."""
+    import torch
+    probs = [wl.fhn_1024(precision=wl.BF16X3, n=n, nsteps=6) for n in (64, 128, 96, 64)]
+    plans = [adr.Plan(p) for p in probs]
+    best, ms = adr.autotune_batch(plans, nsteps=2)
+    assert set(ms) == {0, 1, 2, 3, 4} and best == min(ms, key=ms.get)
+    us, vs = [], []
+    for p in probs:
+        u0, v0 = wl.initial_data(p)
+        us.append(torch.tensor(u0, dtype=torch.float32, device="cuda"))
+        vs.append(torch.tensor(v0, dtype=torch.float32, device="cuda"))
+    with adr.Batch(plans) as b:
+        b.step(us, vs, 6)
+    torch.cuda.synchronize()
+    for p, u, v in zip(probs, us, vs):
+        with adr.Plan(p, kernel=best) as one:
+            u0, v0 = wl.initial_data(p)
+            u1 = torch.tensor(u0, dtype=torch.float32, device="cuda")
+            v1 = torch.tensor(v0, dtype=torch.float32, device="cuda")
+            one.step(u1, v1, 6)
+        torch.cuda.synchronize()
+        assert torch.equal(u1, u) and torch.equal(v1, v)
+    for pl in plans:
+        pl.close()
