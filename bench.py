@@ -270,7 +270,12 @@ def run_batch(args):
     # one kernel for the whole batch, chosen by timing the batch's grouped
     # launches with each kernel (the plans keep their matrix functions)
     t0 = time.perf_counter()
-    kernel, tune_ms = adr.autotune_batch(plans)
+    if args.kernel == -2:
+        kernel, tune_ms = adr.autotune_batch(plans)
+    else:
+        kernel, tune_ms = args.kernel, {}
+        for pl in plans:
+            pl.set_kernel(kernel)
     tune_s = time.perf_counter() - t0
     dt = adr.state_dtype(prec)
     init = []
@@ -391,7 +396,7 @@ def run_batch(args):
                            "precision": args.precision, "grouped": batch.grouped,
                            "l2": "flushed between timed solves (256 MB write)",
                            "parallelism": f"replicas x{world}",
-                           "kernel": {"chosen": kernel, "by": "autotune_batch (whole batch)",
+                           "kernel": {"chosen": kernel, "by": "autotune_batch (whole batch)" if tune_ms else "--kernel",
                                       "ms_per_step": {str(k): round(t, 4) for k, t in tune_ms.items()},
                                       "tuning_s": round(tune_s, 2)}},
                 "max_rel_err_vs_fp64": max_rel, "max_rel_err_sample": "every 32nd solve",
@@ -525,6 +530,8 @@ def main():
     ap.add_argument("--time-steps", type=int, default=None,
                     help="ETD2RKds steps per bench step (default: the workload's)")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy solve")
+    ap.add_argument("--kernel", type=int, default=-2, choices=[-2, -1, 0, 1, 2, 3, 4],
+                    help="tensor-core kernel: -2 autotune (default), -1 plan default, 0..4 fixed")
     ap.add_argument("--cpu-sample", type=int, default=40)
     ap.add_argument("--ref-sample", type=int, default=20)
     ap.add_argument("--requests", type=int, default=400, help="serving workload: request count")
@@ -569,7 +576,10 @@ def main():
     # kernel choice by the library's autotuner (times each tensor-core kernel
     # on this grid), then the plan
     t0 = time.perf_counter()
-    kernel, tune_ms = adr.autotune(p) if prec in (wl.BF16X3, wl.TF32X3) else (-1, {})
+    if args.kernel == -2 and prec in (wl.BF16X3, wl.TF32X3):
+        kernel, tune_ms = adr.autotune(p)
+    else:
+        kernel, tune_ms = max(args.kernel, -1), {}
     tune_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     plan = adr.Plan(p, kernel=kernel)
@@ -731,7 +741,7 @@ def main():
                            "time_steps_per_bench_step": nts, "precision": args.precision,
                            "l2": "flushed between timed solves (256 MB write)",
                            "parallelism": f"replicas x{world}",
-                           "kernel": {"chosen": kernel, "by": "adr_autotune",
+                           "kernel": {"chosen": kernel, "by": "adr_autotune" if tune_ms else "--kernel",
                                       "ms_per_step": {str(k): round(t, 4) for k, t in tune_ms.items()},
                                       "tuning_s": round(tune_s, 2)}},
                 "max_rel_err_vs_fp64": max_rel, "plan_ms": plan_ms,
