@@ -179,6 +179,71 @@ def cpu_baseline(p, sample_steps: int):
                       f"(plan time {plan_s:.1f} s excluded)"}
 
 
+class Replicas:
+    """The ranks of a torchrun launch, each running its own replica of the
+    workload (independent solves, nothing exchanged on the data path).  The
+    timed region is bracketed by barriers, its length is the max over ranks
+    (the job ends with its slowest replica) and the work is summed over
+    ranks.  One process: every reduction returns its argument."""
+
+    def __init__(self, backend: str = "nccl"):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        self.device = "cpu"
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            if backend == "nccl":
+                self.device = torch.device("cuda", self.local)
+                dist.init_process_group(backend, device_id=self.device)
+            else:
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def _reduce(self, x: float, op) -> float:
+        if not self.dist:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x: float) -> float:
+        return self._reduce(x, self.dist.ReduceOp.MAX if self.dist else None)
+
+    def sum(self, x: float) -> float:
+        return self._reduce(x, self.dist.ReduceOp.SUM if self.dist else None)
+
+    def gather(self, items: list) -> list:
+        """Every rank's list, concatenated in rank order."""
+        if not self.dist:
+            return list(items)
+        out = [None] * self.world
+        self.dist.all_gather_object(out, list(items))
+        return [x for part in out for x in part]
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def whole_job_rate(units_per_replica: float, world: int, seconds: float) -> float:
+    """Units all replicas processed per second of the slowest replica."""
+    return world * units_per_replica / seconds
+
+
+def percentile(sorted_vals: list, q: float) -> float:
+    i = min(len(sorted_vals) - 1, max(0, int(round(q * (len(sorted_vals) - 1)))))
+    return sorted_vals[i]
+
+
 def reference_arm(args):
     """--impl reference: the FP64 CPU oracle on this workload (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -252,14 +317,9 @@ def run_batch(args):
     import torch
     import paper_2307_10684_gb300 as adr
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    R = Replicas()
+    world, rank, local = R.world, R.rank, R.local
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     prec = PREC[args.precision]
     probs = wl.batched_512(precision=prec)
     nts = args.time_steps or probs[0].nsteps
@@ -322,21 +382,15 @@ def run_batch(args):
     sampler.start()
     time.sleep(0.3)
     batch.set_timing(False)
-    if dist:
-        dist.barrier()
+    R.barrier()
     torch.cuda.synchronize()
     evs = [one_solve() for _ in range(args.steps)]
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    R.barrier()
     launches = batch.stats()["launches"]
     clocks = sampler.stop()
-    tot_ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * npts * nts * args.steps / (tot_ms / 1e3)
+    tot_ms = R.max(sum(a.elapsed_time(b) for a, b in evs))
+    value = whole_job_rate(npts * nts * args.steps, world, tot_ms / 1e3)
     batch.set_timing(True)
     for _ in range(args.steps):
         one_solve()
@@ -348,6 +402,7 @@ def run_batch(args):
     hout = [(torch.empty_like(a), torch.empty_like(b)) for a, b in hin]
     hout = [(a.pin_memory(), b.pin_memory()) for a, b in hout]
     torch.cuda.synchronize()
+    R.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         for (ha, hb), u, v in zip(hin, us, vs):
@@ -358,9 +413,9 @@ def run_batch(args):
             oa.copy_(u, non_blocking=True)
             ob.copy_(v, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = R.max(time.perf_counter() - t0)
     nbytes = sum(a.numel() * a.element_size() * 2 for a, _ in hin)
-    e2e = {"value": world * npts * nts * args.steps / e2e_s, "unit": "point-steps/s",
+    e2e = {"value": whole_job_rate(npts * nts * args.steps, world, e2e_s), "unit": "point-steps/s",
            "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes)}
     peaks, peak_src = load_peaks()
     kern = {k: d for k, d in stats["kernels"].items() if d["count"] > 0}
@@ -411,8 +466,7 @@ def run_batch(args):
     batch.close()
     for pl in plans:
         pl.close()
-    if dist:
-        dist.destroy_process_group()
+    R.close()
 
 
 def run_serve(args):
@@ -421,11 +475,10 @@ def run_serve(args):
     served throughput beside the offered load."""
     import torch
     import paper_2307_10684_gb300 as adr
-    from paper_2307_10684_gb300.serve import Request, Server, latency_summary
+    from paper_2307_10684_gb300.serve import Request, Server
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    R = Replicas()
+    world, rank, local = R.world, R.rank, R.local
     torch.cuda.set_device(local)
     prec = PREC[args.precision]
     stream_reqs = wl.serving_stream(count=args.requests, precision=prec, seed=5 + rank)
@@ -449,14 +502,24 @@ def run_serve(args):
     sampler = ClockSampler(local)
     sampler.start()
     srv = Server(budget_bytes=int(args.budget_gb * 2**30), keep_ids=sample)
+    R.barrier()
     t0 = time.perf_counter()
     res = srv.run(reqs)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clocks = sampler.stop()
-    summ = latency_summary(res, wall)
-    offered = sum(r.problem.npoints * r.nsteps for r in reqs)
-    span = max(r.arrival for r in reqs)
+    # whole job: every rank serves its own request stream; the served rate is
+    # the work of all ranks over the slowest rank's wall time, and the
+    # latency percentiles are over all ranks' requests
+    served = R.sum(sum(r.npoints * r.nsteps for r in res))
+    wall_all = R.max(wall)
+    lat = sorted(R.gather([r.latency for r in res if r.nsteps > 0]))
+    summ = {"p50_s": percentile(lat, 0.50), "p99_s": percentile(lat, 0.99),
+            "mean_s": sum(lat) / len(lat), "max_s": lat[-1],
+            "served_point_steps_per_s": served / wall_all}
+    offered = R.sum(sum(r.problem.npoints * r.nsteps for r in reqs))
+    span = R.max(max(r.arrival for r in reqs))
+    wall = wall_all
     # accuracy of the sampled requests against FP64 GPU solves of the same data
     # and the conditioning floor: an FP64 solve from data perturbed by 2^-24
     errs, floors, fp32_errs = [], [], []
@@ -487,14 +550,16 @@ def run_serve(args):
         fu, _ = adr.max_abs_diff(up, ur)
         fv, _ = adr.max_abs_diff(vp, vr)
         floors.append(max(fu / mu, fv / mv))
+    errs, floors, fp32_errs = R.gather(errs), R.gather(floors), R.gather(fp32_errs)
     if rank == 0:
         line = {"metric": "served point-steps/s; p50/p99 solve latency",
                 "value": summ["served_point_steps_per_s"], "unit": "point-steps/s",
                 "n_gpus": world, "steps": len(reqs), "warmup": len(warm),
                 "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[prec],
-                "data": "synthetic Poisson request stream (seed 5), seeded initial data",
-                "config": {"workload": f"serving, {len(reqs)} requests at 200/s, 2D sides "
+                "data": "synthetic Poisson request stream per rank (seed 5 + rank), "
+                        "seeded initial data",
+                "config": {"workload": f"serving, {len(reqs)} requests per GPU at 200/s, 2D sides "
                                        "128-1024, 3D sides 64-192, 3 models, horizons 50-1000",
                            "budget_gb": args.budget_gb, "chunk_steps": srv.chunk,
                            "planner_threads": srv.planners},
@@ -514,6 +579,7 @@ def run_serve(args):
                 "e2e": {"value": summ["served_point_steps_per_s"], "unit": "point-steps/s",
                         "note": "requests enter and leave through host memory"}}
         print(json.dumps(line), flush=True)
+    R.close()
 
 
 def main():
@@ -553,14 +619,9 @@ def main():
     import torch
     import paper_2307_10684_gb300 as adr
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    R = Replicas()
+    world, rank, local = R.world, R.rank, R.local
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     prec = PREC[args.precision]
     p = workload(args.workload, prec)
@@ -622,21 +683,15 @@ def main():
     sampler.start()
     time.sleep(0.3)
     plan.set_timing(False)  # resets the counters; steps replay captured CUDA graphs
-    if dist:
-        dist.barrier()
+    R.barrier()
     torch.cuda.synchronize()
     evs = [one_solve() for _ in range(args.steps)]
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    R.barrier()
     launches = plan.stats()["launches"]
     clocks = sampler.stop()
     ms = [a.elapsed_time(b) for a, b in evs]
-    tot_ms = sum(ms)
-    if dist:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = R.max(sum(ms))
     # per-kernel timing: the same solves again, each launch bracketed by CUDA
     # events on the plan's stream; the library replays its graph chunks with
     # the events as event-record nodes (so no host launch gap is timed), which
@@ -648,7 +703,7 @@ def main():
     stats = plan.stats()
     plan.set_timing(False)
     npts = p.npoints
-    value = world * npts * nts * args.steps / (tot_ms / 1e3)
+    value = whole_job_rate(npts * nts * args.steps, world, tot_ms / 1e3)
 
     # end to end through adr_solve with pinned host buffers
     hu0 = u0.cpu().pin_memory()
@@ -657,17 +712,12 @@ def main():
     hvT = torch.empty_like(hv0).pin_memory()
     plan.solve(hu0, hv0, huT, hvT, nts)  # warm
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    R.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         plan.solve(hu0, hv0, huT, hvT, nts)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * npts * nts * args.steps / e2e_s, "unit": "point-steps/s",
+    e2e_s = R.max(time.perf_counter() - t0)
+    e2e = {"value": whole_job_rate(npts * nts * args.steps, world, e2e_s), "unit": "point-steps/s",
            "h2d_bytes_per_step": int(2 * hu0.numel() * hu0.element_size()),
            "d2h_bytes_per_step": int(2 * huT.numel() * huT.element_size())}
 
@@ -755,8 +805,7 @@ def main():
                             for k, d in kern.items()}}
         print(json.dumps(line), flush=True)
     plan.close()
-    if dist:
-        dist.destroy_process_group()
+    R.close()
 
 
 if __name__ == "__main__":
