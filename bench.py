@@ -600,7 +600,7 @@ def main():
                     help="tensor-core kernel: -2 autotune (default), -1 plan default, 0..4 fixed")
     ap.add_argument("--cpu-sample", type=int, default=40)
     ap.add_argument("--ref-sample", type=int, default=20)
-    ap.add_argument("--requests", type=int, default=400, help="serving workload: request count")
+    ap.add_argument("--requests", type=int, default=2000, help="serving workload: requests per GPU")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device-memory budget")
     args = ap.parse_args()
     if args.precision is None:
