@@ -1264,6 +1264,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
 // loads are float4 and stores of four BF16 values 8 bytes) on one y row and
 // marches `zlen` consecutive z planes, keeping the z neighbours in registers.
 struct PwDesc {
+  CUtensorMap tu, tv;  // 3D grids: u and v as [nz][ny][nx] FP32, box {kRingBoxX, kRingBoxY, 1}
   PointwiseArgsT<float> a;
   const float* u;
   const float* v;
@@ -1273,7 +1274,8 @@ struct PwDesc {
   __nv_bfloat16* wv;
   float tau;
   int nx, ny, nz;      // stencil axes (ny = 1 in 2D)
-  int xsegs, zlen, zsegs;
+  int xsegs, zlen, zsegs;  // 2D: warp x segments; 3D: block x tiles.  z runs
+  int ytiles;          // 3D: block y tiles
   int64_t sy, sz;      // element strides of y and z
 };
 
@@ -1284,6 +1286,7 @@ struct PwLaunch {
   const PwDesc* desc;  // [nsolves] in device memory, or null
   const int* bstart;   // [nsolves + 1] prefix sums of this kernel's blocks (desc non-null)
   int nsolves;
+  int* err;            // device error word (bounded waits)
 };
 
 constexpr int kPwThreads = 256;
@@ -1296,14 +1299,19 @@ constexpr int kFlatPerBlock = kPwThreads * 4 * kFlatVec;
 // once in shared memory.  lb = the block's index within its solve.  Waits
 // for the previous kernel of the step before returning (the descriptor is
 // static; the data it points to is not).
-__device__ __forceinline__ const PwDesc* block_desc(const PwLaunch& L, PwDesc* sd, int& lb) {
+// home = the descriptor where it lives (launch parameter or device memory),
+// from where tensor maps must be read.
+__device__ __forceinline__ const PwDesc* block_desc(const PwLaunch& L, PwDesc* sd, int& lb,
+                                                    const PwDesc** home = nullptr) {
   pdl_trigger();
   if (L.desc == nullptr) {
     lb = blockIdx.x;
+    if (home) *home = &L.one;
     pdl_wait();
     return &L.one;
   }
   const int s = find_segment(L.bstart, L.nsolves, blockIdx.x);
+  if (home) *home = L.desc + s;
   static_assert(sizeof(PwDesc) % 4 == 0, "PwDesc is copied in 32-bit words");
   const uint32_t* src = reinterpret_cast<const uint32_t*>(L.desc + s);
   uint32_t* dst = reinterpret_cast<uint32_t*>(sd);
@@ -1314,11 +1322,26 @@ __device__ __forceinline__ const PwDesc* block_desc(const PwLaunch& L, PwDesc* s
   return sd;
 }
 
+// One direction of the stencil of Eq. 6 at an interior point, and at any
+// point (the Neumann rows at i = 0 and i = n - 1 take one neighbour).
+__device__ __forceinline__ float tri_in(float xm, float xc, float xp, float lo, float up) {
+  return lo * (xm - xc) + up * (xp - xc);
+}
 __device__ __forceinline__ float tri_dir(float xm, float xc, float xp, int i, int n, float lo,
                                          float up, float b0, float bn) {
   if (i == 0) return b0 * (xp - xc);
   if (i == n - 1) return bn * (xm - xc);
-  return lo * (xm - xc) + up * (xp - xc);
+  return tri_in(xm, xc, xp, lo, up);
+}
+// The x direction at point j of a group of four starting at a multiple of
+// 4, on a row whose length n is a multiple of 4: only j = 0 can be the
+// row's first point and only j = 3 its last (j is a constant once the
+// loop over the group is unrolled).
+__device__ __forceinline__ float tri_x4(int j, float xm, float xc, float xp, int i, int n,
+                                        float lo, float up, float b0, float bn) {
+  if (j == 0 && i == 0) return b0 * (xp - xc);
+  if (j == 3 && i == n - 1) return bn * (xm - xc);
+  return tri_in(xm, xc, xp, lo, up);
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -1328,17 +1351,25 @@ __device__ __forceinline__ float el(const float4& q, int j) {
 
 // Split four values into BF16 pieces and store piece k of all four at
 // out + k * N + idx (idx a multiple of 4: 8-byte stores).
+// The pieces are those of split3, two values per conversion instruction.
 __device__ __forceinline__ void store_pieces4(__nv_bfloat16* out, int64_t N, int64_t idx,
                                               const float (&w)[4]) {
-  __nv_bfloat16 p[3][4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) split3(w[j], p[0][j], p[1][j], p[2][j]);
+  float r[4] = {w[0], w[1], w[2], w[3]};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(r[0], r[1]);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(r[2], r[3]);
     uint2 q;
-    q.x = (uint32_t)__bfloat16_as_ushort(p[k][0]) | ((uint32_t)__bfloat16_as_ushort(p[k][1]) << 16);
-    q.y = (uint32_t)__bfloat16_as_ushort(p[k][2]) | ((uint32_t)__bfloat16_as_ushort(p[k][3]) << 16);
+    q.x = *reinterpret_cast<const uint32_t*>(&lo);
+    q.y = *reinterpret_cast<const uint32_t*>(&hi);
     *reinterpret_cast<uint2*>(out + k * N + idx) = q;
+    if (k < 2) {
+      const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+      r[0] -= a.x;
+      r[1] -= a.y;
+      r[2] -= b.x;
+      r[3] -= b.y;
+    }
   }
 }
 
@@ -1366,42 +1397,35 @@ struct Coef {
 __device__ __forceinline__ Coef coef(const TridiagT<float>& A) { return Coef{A.lo, A.up, A.b0, A.bn}; }
 
 // W^c = K^c U^c + G^c(U, V) as BF16 pieces [3][N] in the natural layout
-// (Eq. 11, first stage: the stencil of Eq. 6 plus the reaction).  Each
-// iteration of a warp covers ZB consecutive z planes and issues all their
-// loads (the planes, the y neighbours in 3D, the x values beyond the warp's
-// run) before any arithmetic, so that a warp keeps several planes of
-// loads in flight; the planes z - 1 and z + ZB carry over.
-template <bool D3, int ZB, int F = kFmtBF16>
+// (Eq. 11, first stage: the stencil of Eq. 6 plus the reaction), 2D grids
+// (x = x1, z = x2).  Each iteration of a warp covers ZB consecutive z planes
+// and issues all their loads (the planes and the x values beyond the warp's
+// run) before any arithmetic, so that a warp keeps several planes of loads
+// in flight; the planes z - 1 and z + ZB carry over.
+template <int ZB, int F = kFmtBF16>
 __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_constant__ PwLaunch L) {
   __shared__ PwDesc sd;
   int lb;
   const PwDesc* dp = block_desc(L, &sd, lb);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nx = dp->nx, ny = dp->ny, nz = dp->nz, xsegs = dp->xsegs;
+  const int nx = dp->nx, nz = dp->nz, xsegs = dp->xsegs;
   int64_t unit = (int64_t)lb * kPwWarps + warp;
-  if (unit >= (int64_t)xsegs * ny * dp->zsegs) return;  // whole warps only
-  const int y = (int)(unit % ny);
-  unit /= ny;
+  if (unit >= (int64_t)xsegs * dp->zsegs) return;  // whole warps only
   const int xs = (int)(unit % xsegs);
   const int z0 = (int)(unit / xsegs) * dp->zlen;
   const int z1 = min(z0 + dp->zlen, nz);
   const int x0 = xs * kSegX + 4 * lane;
   const bool act = x0 < nx;
-  const int64_t sy = dp->sy, sz = dp->sz, N = dp->a.N;
+  const int64_t sz = dp->sz, N = dp->a.N;
   const float* __restrict__ u = dp->u;
   const float* __restrict__ v = dp->v;
   __nv_bfloat16* wu = dp->wu;
   __nv_bfloat16* wv = dp->wv;
-  // axis coefficients: x = mu 1, y = mu 2 (3D), z = mu 3 (3D) or mu 2 (2D)
+  // axis coefficients: x = mu 1, z = mu 2
   const Coef cxu = coef(dp->a.A[0][0]), cxv = coef(dp->a.A[1][0]);
-  const Coef czu = coef(dp->a.A[0][D3 ? 2 : 1]), czv = coef(dp->a.A[1][D3 ? 2 : 1]);
-  Coef cyu = cxu, cyv = cxv;
-  if (D3) {
-    cyu = coef(dp->a.A[0][1]);
-    cyv = coef(dp->a.A[1][1]);
-  }
+  const Coef czu = coef(dp->a.A[0][1]), czv = coef(dp->a.A[1][1]);
   const ReactionT<float> rx = dp->a.rx;
-  const int64_t col = (int64_t)y * sy + x0;
+  const int64_t col = x0;
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   // run ends: lane 0 needs x0 - 1, lane 31 needs x0 + 4 (others come by shuffle)
   const int64_t eoff = lane == 0 ? -1 : 4;
@@ -1412,7 +1436,6 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_
   pu[1] = act ? ld4(u + z0 * sz + col) : zero4;
   pv[1] = act ? ld4(v + z0 * sz + col) : zero4;
   for (int z = z0; z < z1; z += ZB) {  // trip counts uniform over the warp
-    float4 yum[ZB], yup[ZB], yvm[ZB], yvp[ZB];
     float eu[ZB], ev[ZB];
 #pragma unroll
     for (int j = 2; j < ZB + 2; ++j) {
@@ -1427,12 +1450,6 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_
       const bool ok = act && z + q < z1;
       eu[q] = (ok && eok) ? u[idx + eoff] : 0.f;
       ev[q] = (ok && eok) ? v[idx + eoff] : 0.f;
-      if (D3) {
-        yum[q] = (ok && y > 0) ? ld4(u + idx - sy) : zero4;
-        yvm[q] = (ok && y > 0) ? ld4(v + idx - sy) : zero4;
-        yup[q] = (ok && y + 1 < ny) ? ld4(u + idx + sy) : zero4;
-        yvp[q] = (ok && y + 1 < ny) ? ld4(v + idx + sy) : zero4;
-      }
     }
 #pragma unroll
     for (int q = 0; q < ZB; ++q) {
@@ -1456,12 +1473,8 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_
         const float cu = el(uc, j), cv = el(vc, j);
         const float lu = j == 0 ? ul : el(uc, j - 1), lv = j == 0 ? vl : el(vc, j - 1);
         const float ru = j == 3 ? ur : el(uc, j + 1), rv = j == 3 ? vr : el(vc, j + 1);
-        float ku = tri_dir(lu, cu, ru, xi, nx, cxu.lo, cxu.up, cxu.b0, cxu.bn);
-        float kv = tri_dir(lv, cv, rv, xi, nx, cxv.lo, cxv.up, cxv.b0, cxv.bn);
-        if (D3) {
-          ku += tri_dir(el(yum[q], j), cu, el(yup[q], j), y, ny, cyu.lo, cyu.up, cyu.b0, cyu.bn);
-          kv += tri_dir(el(yvm[q], j), cv, el(yvp[q], j), y, ny, cyv.lo, cyv.up, cyv.b0, cyv.bn);
-        }
+        float ku = tri_x4(j, lu, cu, ru, xi, nx, cxu.lo, cxu.up, cxu.b0, cxu.bn);
+        float kv = tri_x4(j, lv, cv, rv, xi, nx, cxv.lo, cxv.up, cxv.b0, cxv.bn);
         ku += tri_dir(el(pu[q], j), cu, el(pu[q + 2], j), zq, nz, czu.lo, czu.up, czu.b0, czu.bn);
         kv += tri_dir(el(pv[q], j), cv, el(pv[q + 2], j), zq, nz, czv.lo, czv.up, czv.b0, czv.bn);
         float gu, gv;
@@ -1481,7 +1494,161 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_
     pv[1] = pv[ZB + 1];
   }
 }
-constexpr int kZB2 = 4, kZB3 = 1;  // planes per iteration: 2D, 3D
+// The same for 3D grids (x = x1, y = x2, z = x3).  A block owns a
+// kRingX x kRingY tile of the (x, y) plane and marches a run of z planes.
+// Each plane of u and v arrives with its x and y halo by one TMA copy per
+// field (out-of-range points read as zero and are never used: the boundary
+// rows of Eq. 6 take no outer neighbour) into a ring of kRingSlots
+// shared-memory slots.  The copy of plane z + 3 is issued before plane z is
+// computed, so every block keeps about two planes of loads in flight and
+// every value is read from HBM once per tile.  Warp w computes tile rows w
+// and w + 8; the arithmetic is that of the 2D kernel plus the y term.
+constexpr int kRingX = 128, kRingY = 16;
+constexpr int kRingBoxX = kRingX + 8;   // x0 - 4 .. x0 + 131: 16-byte aligned start
+constexpr int kRingBoxY = kRingY + 2;   // y0 - 1 .. y0 + 16
+constexpr int kRingPlane = kRingBoxX * kRingBoxY;        // floats per field and plane copy
+constexpr int kRingField = (kRingPlane + 31) / 32 * 32;  // its slot part: 128-byte multiple
+constexpr int kRingTx = 2 * kRingPlane * 4;              // bytes per plane (u and v)
+constexpr int kRingSlots = 5;
+constexpr int kRingSmem = kRingSlots * 2 * kRingField * 4 + 128 + kRingSlots * 8;
+static_assert(kRingField * 4 % 128 == 0, "copy destinations keep 128-byte alignment");
+
+template <int F = kFmtBF16>
+__global__ void __launch_bounds__(kPwThreads, 2) rhs3_ring_kernel(const __grid_constant__ PwLaunch L) {
+  extern __shared__ uint8_t smem_raw[];
+  float* ring = (float*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  uint64_t* full = (uint64_t*)(ring + kRingSlots * 2 * kRingField);
+  __shared__ PwDesc sd;
+  __shared__ int abort_s;
+  int lb;
+  const PwDesc* src = nullptr;
+  const PwDesc* dp = block_desc(L, &sd, lb, &src);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nx = dp->nx, ny = dp->ny, nz = dp->nz;
+  int b = lb;
+  const int x0 = (b % dp->xsegs) * kRingX;
+  b /= dp->xsegs;
+  const int y0 = (b % dp->ytiles) * kRingY;
+  const int z0 = (b / dp->ytiles) * dp->zlen;
+  if (z0 >= nz) return;  // whole block
+  const int z1 = min(z0 + dp->zlen, nz);
+  const int plo = max(z0 - 1, 0), phi = min(z1, nz - 1);  // planes read: plo .. phi
+  const int np = phi - plo + 1;
+  const CUtensorMap* mu = &src->tu;
+  const CUtensorMap* mv = &src->tv;
+  auto issue = [&](int q) {  // plane plo + q into slot q % kRingSlots
+    const int sl = q % kRingSlots;
+    float* dst = ring + sl * 2 * kRingField;
+    mbar_arrive_expect_tx(&full[sl], kRingTx);
+    tma_load_3d(dst, mu, &full[sl], x0 - 4, y0 - 1, plo + q);
+    tma_load_3d(dst + kRingField, mv, &full[sl], x0 - 4, y0 - 1, plo + q);
+  };
+  int issued = 0, ready = 0;  // planes requested / known landed (thread 0)
+  if (threadIdx.x == 0) {
+    abort_s = 0;
+    for (int sl = 0; sl < kRingSlots; ++sl) mbar_init(&full[sl], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mu) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mv) : "memory");
+    for (; issued < np && issued < kRingSlots; ++issued) issue(issued);
+  }
+  const Coef cxu = coef(dp->a.A[0][0]), cxv = coef(dp->a.A[1][0]);
+  const Coef cyu = coef(dp->a.A[0][1]), cyv = coef(dp->a.A[1][1]);
+  const Coef czu = coef(dp->a.A[0][2]), czv = coef(dp->a.A[1][2]);
+  const ReactionT<float> rx = dp->a.rx;
+  const int64_t sy = dp->sy, sz = dp->sz, N = dp->a.N;
+  __nv_bfloat16* wu = dp->wu;
+  __nv_bfloat16* wv = dp->wv;
+  const int xl = x0 + 4 * lane;
+  const bool act = xl < nx;
+  for (int z = z0; z < z1; ++z) {
+    if (threadIdx.x == 0) {
+      // planes z - 1 .. z + 1 must have landed
+      const int need = min(z + 1, phi) - plo + 1;
+      for (; ready < need; ++ready) {
+        if (!mbar_wait(&full[ready % kRingSlots], (uint32_t)(ready / kRingSlots) & 1u)) {
+          atomicCAS(L.err, 0, kErrTimeoutFull);
+          abort_s = 1;
+          break;
+        }
+      }
+    }
+    __syncthreads();  // data visible; every warp is done with plane z - 2
+    if (abort_s) break;
+    if (threadIdx.x == 0) {
+      const int qfree = z - 2 - plo;  // plane z - 2's slot takes plane z + 3
+      if (qfree >= 0 && qfree + kRingSlots < np && issued == qfree + kRingSlots) issue(issued++);
+    }
+    const float* pc = ring + ((z - plo) % kRingSlots) * 2 * kRingField;
+    const float* pm = z > 0 ? ring + ((z - 1 - plo) % kRingSlots) * 2 * kRingField : nullptr;
+    const float* pp = z + 1 < nz ? ring + ((z + 1 - plo) % kRingSlots) * 2 * kRingField : nullptr;
+#pragma unroll 1
+    for (int rr = 0; rr < 2; ++rr) {
+      const int r = warp + 8 * rr;
+      const int y = y0 + r;
+      if (y >= ny) break;  // uniform over the warp
+      const bool yzin = y > 0 && y + 1 < ny && z > 0 && z + 1 < nz;  // uniform over the warp
+      const int o = (r + 1) * kRingBoxX + 4 + 4 * lane;
+      const float4 uc = *reinterpret_cast<const float4*>(pc + o);
+      const float4 vc = *reinterpret_cast<const float4*>(pc + kRingField + o);
+      const float4 uym = *reinterpret_cast<const float4*>(pc + o - kRingBoxX);
+      const float4 vym = *reinterpret_cast<const float4*>(pc + kRingField + o - kRingBoxX);
+      const float4 uyp = *reinterpret_cast<const float4*>(pc + o + kRingBoxX);
+      const float4 vyp = *reinterpret_cast<const float4*>(pc + kRingField + o + kRingBoxX);
+      const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 uzm = pm ? *reinterpret_cast<const float4*>(pm + o) : zero4;
+      const float4 vzm = pm ? *reinterpret_cast<const float4*>(pm + kRingField + o) : zero4;
+      const float4 uzp = pp ? *reinterpret_cast<const float4*>(pp + o) : zero4;
+      const float4 vzp = pp ? *reinterpret_cast<const float4*>(pp + kRingField + o) : zero4;
+      float ul = __shfl_up_sync(0xffffffffu, uc.w, 1), vl = __shfl_up_sync(0xffffffffu, vc.w, 1);
+      float ur = __shfl_down_sync(0xffffffffu, uc.x, 1), vr = __shfl_down_sync(0xffffffffu, vc.x, 1);
+      if (lane == 0) {
+        ul = pc[o - 1];
+        vl = pc[kRingField + o - 1];
+      }
+      if (lane == 31) {
+        ur = pc[o + 4];
+        vr = pc[kRingField + o + 4];
+      }
+      float ou[4], ov[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int xi = xl + j;
+        const float cu = el(uc, j), cv = el(vc, j);
+        const float lu = j == 0 ? ul : el(uc, j - 1), lv = j == 0 ? vl : el(vc, j - 1);
+        const float ru = j == 3 ? ur : el(uc, j + 1), rv = j == 3 ? vr : el(vc, j + 1);
+        float ku = tri_x4(j, lu, cu, ru, xi, nx, cxu.lo, cxu.up, cxu.b0, cxu.bn);
+        float kv = tri_x4(j, lv, cv, rv, xi, nx, cxv.lo, cxv.up, cxv.b0, cxv.bn);
+        if (yzin) {
+          ku += tri_in(el(uym, j), cu, el(uyp, j), cyu.lo, cyu.up);
+          kv += tri_in(el(vym, j), cv, el(vyp, j), cyv.lo, cyv.up);
+          ku += tri_in(el(uzm, j), cu, el(uzp, j), czu.lo, czu.up);
+          kv += tri_in(el(vzm, j), cv, el(vzp, j), czv.lo, czv.up);
+        } else {
+          ku += tri_dir(el(uym, j), cu, el(uyp, j), y, ny, cyu.lo, cyu.up, cyu.b0, cyu.bn);
+          kv += tri_dir(el(vym, j), cv, el(vyp, j), y, ny, cyv.lo, cyv.up, cyv.b0, cyv.bn);
+          ku += tri_dir(el(uzm, j), cu, el(uzp, j), z, nz, czu.lo, czu.up, czu.b0, czu.bn);
+          kv += tri_dir(el(vzm, j), cv, el(vzp, j), z, nz, czv.lo, czv.up, czv.b0, czv.bn);
+        }
+        float gu, gv;
+        react<float>(rx, cu, cv, gu, gv);
+        ou[j] = ku + gu;
+        ov[j] = kv + gv;
+      }
+      if (act) {
+        const int64_t idx = (int64_t)z * sz + (int64_t)y * sy + xl;
+        store_pieces_fmt<F>(wu, N, idx, ou);
+        store_pieces_fmt<F>(wv, N, idx, ov);
+      }
+    }
+  }
+  if (threadIdx.x == 0 && abort_s) {
+    // copies still in flight land before the block's shared memory is released
+    for (int q = ready; q < issued; ++q) mbar_wait(&full[q % kRingSlots], (uint32_t)(q / kRingSlots) & 1u);
+  }
+}
+
+constexpr int kZB2 = 4;  // planes per iteration of the 2D stencil kernel
 
 // Elementwise kernels: thread t of a block handles float4 groups
 // base + k * kPwThreads + t, k < kFlatVec; loads are issued before any store.
@@ -1953,10 +2120,14 @@ static TcPassDesc make_desc(const TcState* S, const adr_plan_s* P, const TcPass&
   return D;
 }
 
-// Stencil geometry of a solve (see PwDesc): z runs are long enough to reuse
-// the z neighbours, short enough to leave several warps per SM.
+// Stencil geometry of a solve (see PwDesc).
+// 2D: one warp per 128 x-points and z run; the runs are long enough to
+// reuse the z neighbours and short enough to leave several warps per SM.
+// 3D: one block per kRingX x kRingY tile and z run; the runs are cut so that
+// the blocks fill about two waves of two blocks per SM, and hold at least
+// four planes (each run reads two planes beyond its own).
 struct PwGeom {
-  int nx, ny, nz, xsegs, zlen, zsegs;
+  int nx, ny, nz, xsegs, ytiles, zlen, zsegs;
   int64_t sy, sz;
 };
 static PwGeom pw_geom(const TcState* S, int num_sms) {
@@ -1967,12 +2138,26 @@ static PwGeom pw_geom(const TcState* S, int num_sms) {
   g.nz = d3 ? (int)S->n[2] : (int)S->n[1];
   g.sy = S->n[0];
   g.sz = d3 ? S->n[0] * S->n[1] : S->n[0];
+  if (d3) {
+    g.xsegs = (g.nx + kRingX - 1) / kRingX;
+    g.ytiles = (g.ny + kRingY - 1) / kRingY;
+    const int64_t cols = (int64_t)g.xsegs * g.ytiles;
+    const int64_t want = (int64_t)num_sms * 2 * 2;
+    int64_t segs = (want + cols - 1) / cols;
+    if (segs > g.nz) segs = g.nz;
+    int64_t zl = (g.nz + segs - 1) / segs;
+    if (zl < 4) zl = 4;
+    g.zlen = (int)zl;
+    g.zsegs = (g.nz + g.zlen - 1) / g.zlen;
+    return g;
+  }
+  g.ytiles = 1;
   g.xsegs = (g.nx + kSegX - 1) / kSegX;
   // z runs: a multiple of the planes per iteration, as long as leaves about
   // four waves of 16 warps per SM (whole waves balance the SMs; each warp
   // keeps several planes of loads in flight), at most 64 planes
-  const int zb = d3 ? kZB3 : kZB2;
-  const int64_t cols = (int64_t)g.xsegs * g.ny;
+  const int zb = kZB2;
+  const int64_t cols = g.xsegs;
   const int64_t want = (int64_t)num_sms * 16 * 4;
   int64_t zl = (cols * g.nz + want - 1) / want;
   zl = ((zl + zb - 1) / zb) * zb;
@@ -1983,8 +2168,21 @@ static PwGeom pw_geom(const TcState* S, int num_sms) {
   return g;
 }
 
-static PwDesc make_pw(const TcState* S, const adr_plan_s* P, float* u, float* v) {
-  PwDesc W;
+// 3D state field [nz][ny][nx] FP32 for the stencil's plane copies: box
+// {kRingBoxX, kRingBoxY, 1}, zero fill outside the grid.
+static cudaError_t encode_field(CUtensorMap* map, const float* base, const PwGeom& g) {
+  cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  cuuint64_t strides[2] = {(cuuint64_t)g.sy * 4, (cuuint64_t)g.sz * 4};
+  cuuint32_t box[3] = {(cuuint32_t)kRingBoxX, (cuuint32_t)kRingBoxY, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static cudaError_t make_pw(const TcState* S, const adr_plan_s* P, float* u, float* v, PwDesc* out) {
+  PwDesc& W = *out;
   memset(&W, 0, sizeof(W));
   W.a = P->pwf;
   W.u = u;
@@ -1999,16 +2197,23 @@ static PwDesc make_pw(const TcState* S, const adr_plan_s* P, float* u, float* v)
   W.ny = g.ny;
   W.nz = g.nz;
   W.xsegs = g.xsegs;
+  W.ytiles = g.ytiles;
   W.zlen = g.zlen;
   W.zsegs = g.zsegs;
   W.sy = g.sy;
   W.sz = g.sz;
-  return W;
+  if (S->d == 3) {
+    cudaError_t e = encode_field(&W.tu, u, g);
+    if (e == cudaSuccess) e = encode_field(&W.tv, v, g);
+    return e;
+  }
+  return cudaSuccess;
 }
 
 static int rhs_blocks_of(const TcState* S) {
   const PwGeom g = pw_geom(S, S->num_sms);
-  const int64_t warps = (int64_t)g.xsegs * g.ny * g.zsegs;
+  if (S->d == 3) return g.xsegs * g.ytiles * g.zsegs;
+  const int64_t warps = (int64_t)g.xsegs * g.zsegs;
   return (int)((warps + kPwWarps - 1) / kPwWarps);
 }
 static int rdiff_blocks_of(const TcState* S) {
@@ -2043,6 +2248,12 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     if ((e = cudaFuncSetAttribute(tc_mode_kernel<128, 128, false, false, kFmtTF32>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   TcCfg<128, 128, kFmtTF32>::SMEM)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(rhs3_ring_kernel<kFmtBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kRingSmem)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(rhs3_ring_kernel<kFmtTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kRingSmem)) != cudaSuccess)
       return e;
     attr_set = true;
   }
@@ -2207,7 +2418,8 @@ cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   const int np = (int)S->passes.size();
   S->h_desc.resize(np);
   for (int p = 0; p < np; ++p) S->h_desc[p] = make_desc(S, P, S->passes[p], (float*)u, (float*)v);
-  S->h_pw = make_pw(S, P, (float*)u, (float*)v);
+  cudaError_t e = make_pw(S, P, (float*)u, (float*)v, &S->h_pw);
+  if (e != cudaSuccess) return e;
   S->bound_u = u;
   S->bound_v = v;
   return cudaSuccess;
@@ -2243,16 +2455,16 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
     switch (op.kind) {
       case kOpRhs:
         e = timed_kernel(ctl, KC_RHS, N * 2.0 * (6.0 * G.d + 10.0), N * (8.0 + 12.0), [&] {
+          PwLaunch R = G.rhs;
+          R.err = G.err;
           if (G.fmt == kFmtTF32)
-            return G.d == 3 ? launch_k(rhs_pieces_kernel<true, kZB3, kFmtTF32>, dim3(G.rhs_blocks),
-                                       dim3(kPwThreads), 0, st, G.rhs)
-                            : launch_k(rhs_pieces_kernel<false, kZB2, kFmtTF32>, dim3(G.rhs_blocks),
-                                       dim3(kPwThreads), 0, st, G.rhs);
+            return G.d == 3 ? launch_k(rhs3_ring_kernel<kFmtTF32>, dim3(G.rhs_blocks),
+                                       dim3(kPwThreads), kRingSmem, st, R)
+                            : launch_k(rhs_pieces_kernel<kZB2, kFmtTF32>, dim3(G.rhs_blocks),
+                                       dim3(kPwThreads), 0, st, R);
           if (G.d == 3)
-            return launch_k(rhs_pieces_kernel<true, kZB3>, dim3(G.rhs_blocks), dim3(kPwThreads), 0,
-                            st, G.rhs);
-          return launch_k(rhs_pieces_kernel<false, kZB2>, dim3(G.rhs_blocks), dim3(kPwThreads), 0,
-                          st, G.rhs);
+            return launch_k(rhs3_ring_kernel<>, dim3(G.rhs_blocks), dim3(kPwThreads), kRingSmem, st, R);
+          return launch_k(rhs_pieces_kernel<kZB2>, dim3(G.rhs_blocks), dim3(kPwThreads), 0, st, R);
         });
         break;
       case kOpRdiff:
@@ -2701,7 +2913,8 @@ static cudaError_t batch_bind(adr_batch B, void* const* u, void* const* v) {
     const TcState* S = (const TcState*)P->tc.work[0];
     for (int p = 0; p < B->np; ++p)
       hd[(size_t)p * S_ + i] = make_desc(S, P, S->passes[p], (float*)u[i], (float*)v[i]);
-    hp[i] = make_pw(S, P, (float*)u[i], (float*)v[i]);
+    cudaError_t e = make_pw(S, P, (float*)u[i], (float*)v[i], &hp[i]);
+    if (e != cudaSuccess) return e;
   }
   cudaError_t e = g_upload_ring.upload(B->d_desc, hd.data(), sizeof(TcPassDesc) * hd.size(),
                                        B->ctl->stream);

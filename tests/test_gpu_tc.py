@@ -45,7 +45,7 @@ def inputs(p, kind="auto", amp=None):
     return wl.round_to(u0, wl.FP32), wl.round_to(v0, wl.FP32)
 
 
-@pytest.mark.parametrize("n", [(64, 64), (200, 136), (24, 40, 56)])
+@pytest.mark.parametrize("n", [(64, 64), (200, 136), (24, 40, 56), (264, 40, 24)])
 def test_linear_stage_one(adr, n):
     """g = 0: the step is U + tau (K U) x_mu phi_1 (stage 2 adds zero), which
     isolates the stencil kernel and the stage-1 tensor-core products."""
@@ -61,7 +61,8 @@ def test_linear_stage_one(adr, n):
 
 
 @pytest.mark.parametrize("n,model", [((200, 136), wl.FHN), ((128, 256), wl.SCHNAKENBERG),
-                                     ((40, 24, 56), wl.BRUSSELATOR), ((8, 16, 8), wl.FHN)])
+                                     ((40, 24, 56), wl.BRUSSELATOR), ((8, 16, 8), wl.FHN),
+                                     ((136, 24, 40), wl.BRUSSELATOR)])
 def test_ragged_shapes_bf16x3(adr, n, model):
     d = len(n)
     params = {wl.SCHNAKENBERG: (200.0, 0.1, 0.9), wl.FHN: (0.05, 2.0, -0.03),
