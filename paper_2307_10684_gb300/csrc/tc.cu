@@ -29,6 +29,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include <mutex>
 
 #include "adr_internal.h"
@@ -2120,29 +2122,31 @@ static TcPassDesc make_desc(const TcState* S, const adr_plan_s* P, const TcPass&
   return D;
 }
 
-// Stencil geometry of a solve (see PwDesc).
-// 2D: one warp per 128 x-points and z run; the runs are long enough to
-// reuse the z neighbours and short enough to leave several warps per SM.
+// Stencil geometry of a solve (see PwDesc).  share = the solve's fraction
+// of the points of its launch (1 for a single solve), so that a batch's
+// blocks together fill the GPU about as one large solve does.
 // 3D: one block per kRingX x kRingY tile and z run; the runs are cut so that
 // the blocks fill about two waves of two blocks per SM, and hold at least
 // four planes (each run reads two planes beyond its own).
+// 2D: one warp per 128 x-points and z run; the runs are long enough to
+// reuse the z neighbours and short enough to leave several warps per SM.
 struct PwGeom {
   int nx, ny, nz, xsegs, ytiles, zlen, zsegs;
   int64_t sy, sz;
 };
-static PwGeom pw_geom(const TcState* S, int num_sms) {
+static PwGeom pw_geom(const TcState* S, int num_sms, double share) {
   PwGeom g;
   const bool d3 = S->d == 3;
   g.nx = (int)S->n[0];
-  g.ny = d3 ? (int)S->n[1] : 1;
-  g.nz = d3 ? (int)S->n[2] : (int)S->n[1];
   g.sy = S->n[0];
-  g.sz = d3 ? S->n[0] * S->n[1] : S->n[0];
   if (d3) {
+    g.ny = (int)S->n[1];
+    g.nz = (int)S->n[2];
+    g.sz = S->n[0] * S->n[1];
     g.xsegs = (g.nx + kRingX - 1) / kRingX;
     g.ytiles = (g.ny + kRingY - 1) / kRingY;
     const int64_t cols = (int64_t)g.xsegs * g.ytiles;
-    const int64_t want = (int64_t)num_sms * 2 * 2;
+    const int64_t want = std::max<int64_t>(1, (int64_t)(num_sms * 2 * 2 * share + 0.5));
     int64_t segs = (want + cols - 1) / cols;
     if (segs > g.nz) segs = g.nz;
     int64_t zl = (g.nz + segs - 1) / segs;
@@ -2151,6 +2155,9 @@ static PwGeom pw_geom(const TcState* S, int num_sms) {
     g.zsegs = (g.nz + g.zlen - 1) / g.zlen;
     return g;
   }
+  g.ny = 1;
+  g.nz = (int)S->n[1];
+  g.sz = S->n[0];
   g.ytiles = 1;
   g.xsegs = (g.nx + kSegX - 1) / kSegX;
   // z runs: a multiple of the planes per iteration, as long as leaves about
@@ -2158,7 +2165,7 @@ static PwGeom pw_geom(const TcState* S, int num_sms) {
   // keeps several planes of loads in flight), at most 64 planes
   const int zb = kZB2;
   const int64_t cols = g.xsegs;
-  const int64_t want = (int64_t)num_sms * 16 * 4;
+  const int64_t want = std::max<int64_t>(1, (int64_t)(num_sms * 16 * 4 * share + 0.5));
   int64_t zl = (cols * g.nz + want - 1) / want;
   zl = ((zl + zb - 1) / zb) * zb;
   if (zl < zb) zl = zb;
@@ -2181,7 +2188,8 @@ static cudaError_t encode_field(CUtensorMap* map, const float* base, const PwGeo
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-static cudaError_t make_pw(const TcState* S, const adr_plan_s* P, float* u, float* v, PwDesc* out) {
+static cudaError_t make_pw(const TcState* S, const adr_plan_s* P, float* u, float* v, PwDesc* out,
+                           double share = 1.0) {
   PwDesc& W = *out;
   memset(&W, 0, sizeof(W));
   W.a = P->pwf;
@@ -2192,7 +2200,7 @@ static cudaError_t make_pw(const TcState* S, const adr_plan_s* P, float* u, floa
   W.wu = S->buf[0][0];
   W.wv = S->buf[0][1];
   W.tau = (float)P->prob.tau;
-  const PwGeom g = pw_geom(S, S->num_sms);
+  const PwGeom g = pw_geom(S, S->num_sms, share);
   W.nx = g.nx;
   W.ny = g.ny;
   W.nz = g.nz;
@@ -2210,8 +2218,8 @@ static cudaError_t make_pw(const TcState* S, const adr_plan_s* P, float* u, floa
   return cudaSuccess;
 }
 
-static int rhs_blocks_of(const TcState* S) {
-  const PwGeom g = pw_geom(S, S->num_sms);
+static int rhs_blocks_of(const TcState* S, double share = 1.0) {
+  const PwGeom g = pw_geom(S, S->num_sms, share);
   if (S->d == 3) return g.xsegs * g.ytiles * g.zsegs;
   const int64_t warps = (int64_t)g.xsegs * g.zsegs;
   return (int)((warps + kPwWarps - 1) / kPwWarps);
@@ -2457,11 +2465,13 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
         e = timed_kernel(ctl, KC_RHS, N * 2.0 * (6.0 * G.d + 10.0), N * (8.0 + 12.0), [&] {
           PwLaunch R = G.rhs;
           R.err = G.err;
-          if (G.fmt == kFmtTF32)
-            return G.d == 3 ? launch_k(rhs3_ring_kernel<kFmtTF32>, dim3(G.rhs_blocks),
-                                       dim3(kPwThreads), kRingSmem, st, R)
-                            : launch_k(rhs_pieces_kernel<kZB2, kFmtTF32>, dim3(G.rhs_blocks),
-                                       dim3(kPwThreads), 0, st, R);
+          if (G.fmt == kFmtTF32) {
+            if (G.d == 3)
+              return launch_k(rhs3_ring_kernel<kFmtTF32>, dim3(G.rhs_blocks), dim3(kPwThreads),
+                              kRingSmem, st, R);
+            return launch_k(rhs_pieces_kernel<kZB2, kFmtTF32>, dim3(G.rhs_blocks), dim3(kPwThreads),
+                            0, st, R);
+          }
           if (G.d == 3)
             return launch_k(rhs3_ring_kernel<>, dim3(G.rhs_blocks), dim3(kPwThreads), kRingSmem, st, R);
           return launch_k(rhs_pieces_kernel<kZB2>, dim3(G.rhs_blocks), dim3(kPwThreads), 0, st, R);
@@ -2864,13 +2874,13 @@ static adr_status batch_create_one(const adr_plan* plans, int count, void* strea
       B->units[p] = acc;
     }
     int ra = 0, rd = 0;
+    for (int i = 0; i < S_; ++i) B->pw_n += (double)((const TcState*)plans[i]->tc.work[0])->N;
     for (int i = 0; i < S_; ++i) {
       const TcState* S = (const TcState*)plans[i]->tc.work[0];
       bs[i] = ra;
       bs[(S_ + 1) + i] = rd;
-      ra += rhs_blocks_of(S);
+      ra += rhs_blocks_of(S, (double)S->N / B->pw_n);
       rd += rdiff_blocks_of(S);
-      B->pw_n += (double)S->N;
     }
     bs[S_] = ra;
     bs[(S_ + 1) + S_] = rd;
@@ -2913,7 +2923,7 @@ static cudaError_t batch_bind(adr_batch B, void* const* u, void* const* v) {
     const TcState* S = (const TcState*)P->tc.work[0];
     for (int p = 0; p < B->np; ++p)
       hd[(size_t)p * S_ + i] = make_desc(S, P, S->passes[p], (float*)u[i], (float*)v[i]);
-    cudaError_t e = make_pw(S, P, (float*)u[i], (float*)v[i], &hp[i]);
+    cudaError_t e = make_pw(S, P, (float*)u[i], (float*)v[i], &hp[i], (double)S->N / B->pw_n);
     if (e != cudaSuccess) return e;
   }
   cudaError_t e = g_upload_ring.upload(B->d_desc, hd.data(), sizeof(TcPassDesc) * hd.size(),
