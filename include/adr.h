@@ -162,6 +162,19 @@ adr_status adr_plan_create_tuned(const adr_problem* problem, const adr_tuning* t
  * On failure the plan cannot step until a later call succeeds. */
 adr_status adr_plan_set_kernel(adr_plan plan, int32_t kernel);
 
+/* Self-test of the bounded waits that every tensor-core and staging kernel
+ * uses (no counterpart in the paper: it checks this library's failure
+ * detection).  One kernel on `stream` waits on a shared-memory mbarrier
+ * that a thread of another warp arrives on (arrive != 0) or that nothing
+ * arrives on (arrive == 0), gives up after limit_ns nanoseconds of
+ * %globaltimer (1e6 <= limit_ns <= 2e9), and records the timeout code in a
+ * device error word, as a kernel of a step does.  Synchronises the stream;
+ * *code = the error word (0, or 1 = a wait gave up), *waited_ns = the wait's
+ * length measured on the device.  ADR_OK when the kernel ran, whatever the
+ * code; the CUDA context stays usable either way. */
+adr_status adr_selftest_bounded_wait(void* stream, int32_t arrive, int64_t limit_ns, int32_t* code,
+                                     int64_t* waited_ns);
+
 /* Autotuner: for a tensor-core problem, builds a plan with each candidate
  * kernel, advances scratch state (allocated here, zero-filled) by 2 + nsteps
  * steps on `stream` and times the last nsteps with CUDA events.  best

@@ -199,6 +199,17 @@ def autotune(problem, nsteps: int = 32, stream=None, cache: bool = True):
     return out
 
 
+def selftest_bounded_wait(arrive: bool, limit_ns: int = 20_000_000, stream=None):
+    """adr_selftest_bounded_wait: (device error code, ns waited) of one
+    bounded mbarrier wait that is (arrive=True) or is not satisfied."""
+    code = ctypes.c_int32()
+    waited = ctypes.c_int64()
+    _abi.check(lib().adr_selftest_bounded_wait(ctypes.c_void_p(_stream_handle(stream)),
+                                               1 if arrive else 0, ctypes.c_int64(int(limit_ns)),
+                                               ctypes.byref(code), ctypes.byref(waited)))
+    return int(code.value), int(waited.value)
+
+
 def autotune_batch(plans, nsteps: int = 8, stream=None):
     """Kernel choice for a batch: every tensor-core kernel is timed on the
     grouped launches of the whole batch (its plans switched with

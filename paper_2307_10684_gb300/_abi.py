@@ -48,6 +48,8 @@ SIGNATURES = {
     "adr_autotune": (c_int32, [ctypes.POINTER(AdrProblem), c_void_p, c_int32,
                                ctypes.POINTER(AdrTuning), ctypes.POINTER(ctypes.c_float)]),
     "adr_plan_set_kernel": (c_int32, [AdrPlan, c_int32]),
+    "adr_selftest_bounded_wait": (c_int32, [c_void_p, c_int32, c_int64, ctypes.POINTER(c_int32),
+                                            ctypes.POINTER(c_int64)]),
     "adr_plan_destroy": (c_int32, [AdrPlan]),
     "adr_plan_set_stream": (c_int32, [AdrPlan, c_void_p]),
     "adr_step": (c_int32, [AdrPlan, c_void_p, c_void_p, c_int64]),

@@ -134,12 +134,12 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
   }
   return true;
 }
-// Wait for the phase with the given parity; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase with the given parity; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
   return true;
 }
@@ -3135,3 +3135,56 @@ extern "C" adr_status adr_batch_stats(adr_batch batch, adr_stats* out) {
 }
 
 extern "C" int adr_batch_is_grouped(adr_batch batch) { return batch ? batch->grouped : 0; }
+
+// ---------------------------------------------------------------- self-test
+// The bounded wait of the kernels above, exercised on its own: thread 0
+// waits on an mbarrier that a thread of another warp arrives on (arrive != 0)
+// or that nothing arrives on, gives up after limit_ns, and records the
+// timeout code in the error word as a kernel of a step does.
+__global__ void bounded_wait_selftest_kernel(int arrive, uint64_t limit_ns, int* err,
+                                             unsigned long long* waited_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 32)
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  if (threadIdx.x == 0) {
+    const uint64_t t0 = globaltimer();
+    const bool ok = mbar_wait(&bar, 0, limit_ns);
+    *waited_ns = globaltimer() - t0;
+    if (!ok) atomicCAS(err, 0, kErrTimeoutFull);
+  }
+}
+
+extern "C" adr_status adr_selftest_bounded_wait(void* stream, int32_t arrive, int64_t limit_ns,
+                                                int32_t* code, int64_t* waited_ns) {
+  if (!code || !waited_ns || limit_ns < 1000000 || limit_ns > 2000000000) {
+    set_error("adr_selftest_bounded_wait: need code, waited_ns and 1e6 <= limit_ns <= 2e9");
+    return ADR_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, 16);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, 16, st);
+  if (e == cudaSuccess) {
+    bounded_wait_selftest_kernel<<<1, 64, 0, st>>>(arrive, (uint64_t)limit_ns, (int*)buf,
+                                                   (unsigned long long*)((char*)buf + 8));
+    e = cudaGetLastError();
+  }
+  int32_t h[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, buf, 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (buf) cudaFree(buf);
+  if (e != cudaSuccess) {
+    set_error(std::string("adr_selftest_bounded_wait: ") + cudaGetErrorString(e));
+    return ADR_ECUDA;
+  }
+  *code = h[0];
+  int64_t w;
+  memcpy(&w, &h[2], 8);
+  *waited_ns = w;
+  return ADR_OK;
+}

@@ -92,3 +92,14 @@ def test_plan_bytes_host_only(adr):
     assert cb > sb
     sb64, _ = adr.plan_bytes(wl.schnakenberg_64())
     assert sb64 == 2 * 64 * 64 * 8
+
+
+def test_selftest_limits_checked_on_the_host(adr):
+    """The bounded-wait self-test rejects limits outside [1 ms, 2 s] before
+    touching the GPU."""
+    c, w = ctypes.c_int32(), ctypes.c_int64()
+    L = adr.lib()
+    assert L.adr_selftest_bounded_wait(None, 0, 10, ctypes.byref(c), ctypes.byref(w)) == adr.ADR_EINVAL
+    assert L.adr_selftest_bounded_wait(None, 0, 3_000_000_000, ctypes.byref(c),
+                                       ctypes.byref(w)) == adr.ADR_EINVAL
+    assert L.adr_selftest_bounded_wait(None, 0, 20_000_000, None, ctypes.byref(w)) == adr.ADR_EINVAL
