@@ -158,7 +158,8 @@ adr_status adr_plan_create_tuned(const adr_problem* problem, const adr_tuning* t
 /* Switch an existing tensor-core plan to another kernel (adr_tuning.kernel)
  * without recomputing its FP64 matrix functions: synchronises the plan's
  * stream and rebuilds only the kernel operands, tensor maps and graphs.
- * Destroy any batch that contains the plan first.  FP32 / FP64 plans: no-op.
+ * ADR_EBUSY (nothing changed) while a batch created over the plan is alive.
+ * FP32 / FP64 plans: no-op.
  * On failure the plan cannot step until a later call succeeds. */
 adr_status adr_plan_set_kernel(adr_plan plan, int32_t kernel);
 
@@ -191,7 +192,8 @@ adr_status adr_autotune(const adr_problem* problem, void* stream, int32_t nsteps
  * on a planner thread) and stepped on another. */
 adr_status adr_plan_set_stream(adr_plan plan, void* stream);
 
-/* Free a plan (synchronises its stream first).  NULL is accepted. */
+/* Free a plan (synchronises its stream first).  NULL is accepted.
+ * ADR_EBUSY (nothing freed) while a batch created over the plan is alive. */
 adr_status adr_plan_destroy(adr_plan plan);
 
 /* Advance (u, v) by nsteps ETD2RKds steps in place (Eq. 11):
@@ -250,7 +252,9 @@ adr_status adr_plan_stats(adr_plan plan, adr_stats* out);
  * per-solve descriptors), one reaction-difference launch; runs of 16 steps
  * replay a captured CUDA graph.  Other batches step their plans in turn.
  * The batch uses the plans' matrices and workspaces: while a batch steps, do
- * not step its plans on their own.  The plans must outlive the batch. */
+ * not step its plans on their own.  The plans must outlive the batch:
+ * adr_plan_destroy and adr_plan_set_kernel return ADR_EBUSY for a plan that
+ * a live batch uses. */
 typedef struct adr_batch_s* adr_batch;
 
 /* Build a batch of `count` plans (host array, copied); launches go to

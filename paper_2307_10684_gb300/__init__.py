@@ -95,8 +95,10 @@ class Plan:
         _abi.check(lib().adr_plan_set_stream(self._p, ctypes.c_void_p(_stream_handle(stream))))
 
     def close(self):
+        """adr_plan_destroy; raises (and keeps the plan) while a live Batch
+        uses it."""
         if self._p:
-            lib().adr_plan_destroy(self._p)
+            _abi.check(lib().adr_plan_destroy(self._p))
             self._p = _abi.AdrPlan()
 
     def __del__(self):

@@ -186,6 +186,8 @@ struct adr_plan_s {
   void* g_v;
   int64_t g_launches;        // kernels per replay
   int tc_variant;            // requested tensor-core kernel (-1: the library's choice)
+  int batch_refs;            // live batches over this plan (atomic; destroy and
+                             // kernel changes are refused while non-zero)
   // timing mode: the same chunk captured with an event-record node before and
   // after every kernel, so that per-kernel times exclude host launch gaps
   cudaGraphExec_t gexec_timed;

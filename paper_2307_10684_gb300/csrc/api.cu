@@ -376,6 +376,8 @@ extern "C" adr_status adr_plan_set_stream(adr_plan plan, void* stream) {
 }
 
 extern "C" adr_status adr_plan_destroy(adr_plan plan) {
+  if (plan && __atomic_load_n(&plan->batch_refs, __ATOMIC_ACQUIRE) > 0)
+    return fail(ADR_EBUSY, "adr_plan_destroy: a live batch uses this plan; destroy the batch first");
   plan_free(plan);
   return ADR_OK;
 }
@@ -684,6 +686,8 @@ extern "C" const char* adr_last_error(void) { return g_last_error.c_str(); }
 extern "C" adr_status adr_plan_set_kernel(adr_plan P, int32_t kernel) {
   if (!P) return fail(ADR_EINVAL, "plan is NULL");
   if (kernel < -1 || kernel > 4) return fail(ADR_EINVAL, "kernel must be -1 or 0..4");
+  if (__atomic_load_n(&P->batch_refs, __ATOMIC_ACQUIRE) > 0)
+    return fail(ADR_EBUSY, "adr_plan_set_kernel: a live batch uses this plan; destroy the batch first");
   if (P->prec != ADR_BF16X3 && P->prec != ADR_TF32X3) return ADR_OK;
   ADR_CUDA_TRY(cudaStreamSynchronize(P->stream));
   if (P->gexec) cudaGraphExecDestroy(P->gexec);

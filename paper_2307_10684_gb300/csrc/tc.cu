@@ -2768,8 +2768,20 @@ static bool same_sequence(const adr_plan_s* a, const adr_plan_s* b) {
 
 static adr_status batch_create_one(const adr_plan* plans, int count, void* stream, adr_batch* out);
 
+static adr_status batch_create_any(const adr_plan* plans, int count, void* stream, adr_batch* out);
+
+// A live batch holds a reference on each of its plans: destroying a plan or
+// changing its kernel would leave the batch's descriptors pointing at freed
+// memory, so both are refused while the count is non-zero.
 extern "C" adr_status adr_batch_create(const adr_plan* plans, int count, void* stream,
                                        adr_batch* out) {
+  const adr_status st = batch_create_any(plans, count, stream, out);
+  if (st == ADR_OK)
+    for (int i = 0; i < count; ++i) __atomic_add_fetch(&plans[i]->batch_refs, 1, __ATOMIC_ACQ_REL);
+  return st;
+}
+
+static adr_status batch_create_any(const adr_plan* plans, int count, void* stream, adr_batch* out) {
   if (!plans || count < 1 || !out) {
     set_error("adr_batch_create: need count >= 1 plans and an output pointer");
     return ADR_EINVAL;
@@ -2907,6 +2919,8 @@ static adr_status batch_create_one(const adr_plan* plans, int count, void* strea
 }
 
 extern "C" adr_status adr_batch_destroy(adr_batch batch) {
+  if (batch)
+    for (adr_plan p : batch->plans) __atomic_sub_fetch(&p->batch_refs, 1, __ATOMIC_ACQ_REL);
   batch_free(batch);
   return ADR_OK;
 }

@@ -210,3 +210,32 @@ def test_batch_mixing_kernels_is_split_and_equals_alone(adr):
     b.close()
     for pl in plans:
         pl.close()
+
+
+def test_plans_of_a_live_batch_are_protected(adr):
+    """While a batch uses a plan, destroying the plan or changing its kernel
+    is refused (ADR_EBUSY) and leaves both usable; after the batch is
+    destroyed both succeed."""
+    import torch
+    probs = mixed_problems(d=2, count=2)
+    plans = [adr.Plan(p) for p in probs]
+    us, vs, _ = states(adr, probs)
+    b = adr.Batch(plans)
+    b2 = adr.Batch(plans[:1])  # a second batch over the first plan
+    for pl in plans:
+        with pytest.raises(adr.AdrError) as ei:
+            pl.close()
+        assert ei.value.status == adr.ADR_EBUSY
+        with pytest.raises(adr.AdrError) as ei:
+            pl.set_kernel(2)
+        assert ei.value.status == adr.ADR_EBUSY
+    b.step(us, vs, 3)  # still steps: nothing was freed or changed
+    b.close()
+    with pytest.raises(adr.AdrError):
+        plans[0].close()  # b2 still holds it
+    plans[1].set_kernel(2)
+    plans[1].close()
+    b2.close()
+    plans[0].set_kernel(2)
+    plans[0].close()
+    torch.cuda.synchronize()
