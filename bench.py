@@ -75,10 +75,10 @@ def measured_gemm_peak(dtype) -> float:
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
-def profiled_traffic(workload_name: str):
+def profiled_traffic(workload_name: str, kernel: int):
     """DRAM bytes per launch of the tensor-core mode-product kernel from the
     committed ncu summary, or None when the kernel source has changed since
-    that capture."""
+    that capture or the capture is of another kernel than `kernel`."""
     import hashlib
     import re
     prof = os.path.join(ROOT, "profiles", f"tc_mode_{workload_name}.md")
@@ -88,7 +88,8 @@ def profiled_traffic(workload_name: str):
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         m_sha = re.search(r"source_sha256\([^)]*\): ([0-9a-f]+)", txt)
         m_b = re.search(r"dram_bytes_per_launch: (\d+)", txt)
-        if m_sha and m_b and m_sha.group(1) == sha:
+        m_k = re.search(r"captured_kernel: (-?\d+)", txt)
+        if m_sha and m_b and m_k and m_sha.group(1) == sha and int(m_k.group(1)) == kernel:
             return int(m_b.group(1))
     except OSError:
         pass
@@ -742,7 +743,8 @@ def main():
                 "frac": achieved / peak, "traffic": None, "kernel": dom,
                 "peak_source": peak_note, "share_of_kernel_time": kd["ms"] / total_kernel_ms}
     elif dom == "mode_product_tc":
-        roof = tc_roofline(kd, prec, peaks, peak_src, profiled_traffic(args.workload))
+        used = kernel if kernel >= 0 else (4 if npts >= 1000000 else 0)  # the plan default
+        roof = tc_roofline(kd, prec, peaks, peak_src, profiled_traffic(args.workload, used))
         roof["share_of_kernel_time"] = kd["ms"] / total_kernel_ms
     else:
         bytes_ = kd["bytes"] / kd["count"]
