@@ -160,10 +160,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+SCHEMES = {"etd2rkds": wl.ETD2RKDS, "lawson2b": wl.LAWSON2B}
+SCHEME_NAMES = {wl.ETD2RKDS: "ETD2RKds", wl.LAWSON2B: "Lawson2b"}
+
+
+def oracle_solve(plan, p, u0, v0, nsteps: int):
+    """nsteps steps of the oracle in the problem's scheme."""
+    from oracle import schemes
+    if p.scheme == wl.LAWSON2B:
+        for _ in range(nsteps):
+            u0, v0 = schemes.lawson2b_step(plan, u0, v0)
+        return u0, v0
+    return schemes.etd2rkds_solve(plan, u0, v0, nsteps)
+
+
 def cpu_baseline(p, sample_steps: int):
     """The FP64 oracle (as it stands) timed on the host cores on a bounded
-    sample: `sample_steps` ETD2RKds steps of the same workload."""
-    import oracle
+    sample: `sample_steps` steps of the same workload."""
     from oracle import schemes
     cores = len(os.sched_getaffinity(0))
     u0, v0 = wl.initial_data(p)
@@ -172,12 +185,12 @@ def cpu_baseline(p, sample_steps: int):
     plan = schemes.make_plan(p)
     plan_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    schemes.etd2rkds_solve(plan, u0, v0, sample_steps)
+    oracle_solve(plan, p, u0, v0, sample_steps)
     dt = time.perf_counter() - t0
     return {"value": p.npoints * sample_steps / dt, "unit": "point-steps/s", "cores": cores,
             "kind": "oracle",
-            "sample": f"{sample_steps} ETD2RKds steps of the same {p.name} grid, FP64 numpy "
-                      f"(plan time {plan_s:.1f} s excluded)"}
+            "sample": f"{sample_steps} {SCHEME_NAMES[p.scheme]} steps of the same {p.name} grid, "
+                      f"FP64 numpy (plan time {plan_s:.1f} s excluded)"}
 
 
 class Replicas:
@@ -250,19 +263,18 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    p = workload(args.workload, PREC[args.precision])
+    p = workload(args.workload, PREC[args.precision]).replace(scheme=SCHEMES[args.scheme])
     sample = args.ref_sample
-    import oracle
     from oracle import schemes
     u0, v0 = wl.initial_data(p)
     u0, v0 = wl.round_to(u0, p.precision), wl.round_to(v0, p.precision)
     plan = schemes.make_plan(p)
     for _ in range(args.warmup):
-        schemes.etd2rkds_solve(plan, u0, v0, 1)
+        oracle_solve(plan, p, u0, v0, 1)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        schemes.etd2rkds_solve(plan, u0, v0, sample)
+        oracle_solve(plan, p, u0, v0, sample)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = p.npoints * sample * args.steps / tot
@@ -273,10 +285,11 @@ def reference_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64)",
             "config": {"workload": p.name, "grid": list(p.n[: p.d]), "tau": p.tau,
-                       "time_steps_per_bench_step": sample},
+                       "scheme": SCHEME_NAMES[p.scheme], "time_steps_per_bench_step": sample},
             "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": cores,
                              "kind": "oracle",
-                             "sample": f"each bench step = {sample} ETD2RKds steps of {p.name}"},
+                             "sample": f"each bench step = {sample} {SCHEME_NAMES[p.scheme]} "
+                                       f"steps of {p.name}"},
             "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -597,6 +610,9 @@ def main():
     ap.add_argument("--time-steps", type=int, default=None,
                     help="ETD2RKds steps per bench step (default: the workload's)")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy solve")
+    ap.add_argument("--scheme", default="etd2rkds", choices=sorted(SCHEMES),
+                    help="time-stepping scheme of the single-solve workloads (fhn1024, "
+                         "bruss256, schnak64)")
     ap.add_argument("--kernel", type=int, default=-2, choices=[-2, -1, 0, 1, 2, 3, 4],
                     help="tensor-core kernel: -2 autotune (default), -1 plan default, 0..4 fixed")
     ap.add_argument("--cpu-sample", type=int, default=40)
@@ -625,7 +641,7 @@ def main():
     torch.cuda.set_device(local)
 
     prec = PREC[args.precision]
-    p = workload(args.workload, prec)
+    p = workload(args.workload, prec).replace(scheme=SCHEMES[args.scheme])
     nts = args.time_steps or p.nsteps
     dt = adr.state_dtype(prec)
     u0n, v0n = wl.initial_data(p)
@@ -744,7 +760,8 @@ def main():
                 "peak_source": peak_note, "share_of_kernel_time": kd["ms"] / total_kernel_ms}
     elif dom == "mode_product_tc":
         used = kernel if kernel >= 0 else (4 if npts >= 1000000 else 0)  # the plan default
-        roof = tc_roofline(kd, prec, peaks, peak_src, profiled_traffic(args.workload, used))
+        traffic = profiled_traffic(args.workload, used) if p.scheme == wl.ETD2RKDS else None
+        roof = tc_roofline(kd, prec, peaks, peak_src, traffic)
         roof["share_of_kernel_time"] = kd["ms"] / total_kernel_ms
     else:
         bytes_ = kd["bytes"] / kd["count"]
@@ -790,6 +807,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[prec],
                 "data": "synthetic (seeded SplitMix64 N(0,0.05^2) data)",
                 "config": {"workload": p.name, "grid": list(p.n[: p.d]), "tau": p.tau,
+                           "scheme": SCHEME_NAMES[p.scheme],
                            "time_steps_per_bench_step": nts, "precision": args.precision,
                            "l2": "flushed between timed solves (256 MB write)",
                            "parallelism": f"replicas x{world}",
