@@ -1,0 +1,58 @@
+"""bench.py's host-side logic (no GPU): the roofline arithmetic, the use of
+the committed ncu captures, and the oracle baseline's scheme dispatch."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import workloads as wl  # noqa: E402
+from oracle import schemes  # noqa: E402
+
+
+def test_tensor_roofline_arithmetic():
+    peaks = {"bf16_tflops": 2000.0, "hbm_gbs": 8000.0}
+    # 10 launches of 1 GFLOP (algorithmic) and 1 MB in 1 ms in all
+    kd = {"ms": 1.0, "count": 10, "flops": 10e9, "bytes": 10e6}
+    r = bench.tc_roofline(kd, wl.BF16X3, peaks, "test", None)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(6 * 1e9 / 1e-4 / 1e12)  # six MMAs per product
+    assert r["frac"] == pytest.approx(r["achieved"] / 2000.0)
+    r32 = bench.tc_roofline(kd, wl.TF32X3, peaks, "test", None)
+    assert r32["peak"] == pytest.approx(1000.0)  # tf32 at half the bf16 rate, 3 MMAs
+    assert r32["achieved"] == pytest.approx(3 * 1e9 / 1e-4 / 1e12)
+
+
+def test_hbm_roofline_arithmetic():
+    peaks = {"bf16_tflops": 2000.0, "hbm_gbs": 8000.0}
+    kd = {"ms": 1.0, "count": 10, "flops": 10e6, "bytes": 10e9}
+    r = bench.tc_roofline(kd, wl.BF16X3, peaks, "test", 123)
+    assert r["bound"] == "hbm" and r["traffic"] == 123
+    assert r["achieved"] == pytest.approx(1e9 / 1e-4 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 8000.0)
+
+
+def test_traffic_only_for_the_captured_source_and_kernel():
+    t = bench.profiled_traffic("fhn1024", 4)
+    assert isinstance(t, int) and t > 0
+    assert bench.profiled_traffic("fhn1024", 0) is None
+    assert bench.profiled_traffic("no_such_workload", 4) is None
+
+
+@pytest.mark.parametrize("scheme", [wl.ETD2RKDS, wl.LAWSON2B])
+def test_oracle_solve_follows_the_scheme(scheme):
+    p = wl.fhn_1024(precision=wl.FP64, n=16, nsteps=3).replace(scheme=scheme)
+    u0, v0 = wl.initial_data(p)
+    plan = schemes.make_plan(p)
+    U, V = bench.oracle_solve(plan, p, u0, v0, 3)
+    if scheme == wl.LAWSON2B:
+        Ur, Vr = u0, v0
+        for _ in range(3):
+            Ur, Vr = schemes.lawson2b_step(plan, Ur, Vr)
+    else:
+        Ur, Vr = schemes.etd2rkds_solve(plan, u0, v0, 3)
+    assert np.array_equal(U, Ur) and np.array_equal(V, Vr)
