@@ -245,11 +245,12 @@ adr_status adr_plan_set_timing(adr_plan plan, int enable);
 adr_status adr_plan_stats(adr_plan plan, adr_stats* out);
 
 /* ---------------------------------------------------------------- batches
- * Many independent solves (SURVEY config "batched") advanced together.  When
- * every plan is ADR_BF16X3 with the same d, one step of the whole batch is a
- * fixed set of grouped launches: one stencil launch, one launch per mode
- * product covering every solve's tiles (a persistent tcgen05 kernel reading
- * per-solve descriptors), one reaction-difference launch; runs of 16 steps
+ * Many independent solves (say hundreds of grids of different sizes)
+ * advanced together.  When every plan is ADR_BF16X3 with the same d, one
+ * step of the whole batch is a fixed set of grouped launches: one stencil
+ * launch, one launch per mode product covering every solve's tiles (a
+ * persistent tcgen05 kernel reading per-solve descriptors), one
+ * reaction-difference launch; runs of 16 steps
  * replay a captured CUDA graph.  Other batches step their plans in turn.
  * The batch uses the plans' matrices and workspaces: while a batch steps, do
  * not step its plans on their own.  The plans must outlive the batch:
