@@ -36,6 +36,7 @@ import numpy as np  # noqa: E402
 import workloads as wl  # noqa: E402
 
 PREC = {"fp64": wl.FP64, "fp32": wl.FP32, "tf32x3": wl.TF32X3, "bf16x3": wl.BF16X3}
+PREC_NAME = {v: k for k, v in PREC.items()}
 DTYPE_NAME = {wl.FP64: "f64", wl.FP32: "f32", wl.TF32X3: "f32 (tf32x3 tensor-core products)",
               wl.BF16X3: "f32 (bf16x3 tensor-core products)"}
 
@@ -75,13 +76,13 @@ def measured_gemm_peak(dtype) -> float:
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
-def profiled_traffic(workload_name: str, kernel: int):
+def profiled_traffic(workload_name: str, kernel: int, profiles: str = None):
     """DRAM bytes per launch of the tensor-core mode-product kernel from the
     committed ncu summary, or None when the kernel source has changed since
     that capture or the capture is of another kernel than `kernel`."""
     import hashlib
     import re
-    prof = os.path.join(ROOT, "profiles", f"tc_mode_{workload_name}.md")
+    prof = os.path.join(profiles or os.path.join(ROOT, "profiles"), f"tc_mode_{workload_name}.md")
     src = os.path.join(ROOT, "paper_2307_10684_gb300", "csrc", "tc.cu")
     try:
         txt = open(prof).read()
@@ -323,6 +324,309 @@ def tc_roofline(kd, prec, peaks, peak_src, traffic):
             "algorithmic_bytes_per_launch": nbytes, "algorithmic_flops_per_launch": flops,
             "tensor_frac": t_tensor / avg_s,
             "peak_source": f"{peak_src} HBM copy bandwidth"}
+
+
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _oracle_final(p, nsteps: int):
+    """Worker (spawned process): the oracle's final state of the workload
+    from the same rounded initial data the GPU solve starts from."""
+    from oracle import schemes
+    u0, v0 = wl.initial_data(p)
+    u0, v0 = wl.round_to(u0, p.precision), wl.round_to(v0, p.precision)
+    plan = schemes.make_plan(p)
+    t0 = time.perf_counter()
+    U, V = oracle_solve(plan, p, u0, v0, nsteps)
+    return U, V, time.perf_counter() - t0
+
+
+class OracleJobs:
+    """Whole-horizon oracle solves in one spawned worker process, started
+    before any GPU call, with `threads` BLAS threads (the rest of the host
+    cores stay with the GPU process)."""
+
+    def __init__(self, jobs, threads: int):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        saved = {k: os.environ.get(k) for k in THREAD_VARS}
+        for k in THREAD_VARS:
+            os.environ[k] = str(threads)
+        try:
+            self.ex = cf.ProcessPoolExecutor(max_workers=1, mp_context=mp.get_context("spawn"))
+            self.futs = [self.ex.submit(_oracle_final, p, n) for p, n in jobs]
+            # the worker is spawned now, with the thread counts above
+            self.ex.submit(int, 0).result()
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.threads = threads
+
+    def result(self, i: int):
+        return self.futs[i].result()
+
+    def close(self):
+        self.ex.shutdown(wait=True)
+
+
+def mode_product_roofline(p, prec, ms_launch: float, per_step: int, peaks, peak_src, traffic):
+    """Roofline of the tensor-core mode-product launch, timed as it runs
+    inside a step (adr_plan_time_mode_products), on the algorithmic work of
+    the method per launch:
+      flops: 2 flops x n_mu per output x 2 components  = 4 n_mu N (mean over mu)
+      bytes: FP32 operand in + out for both components = 16 B per point, plus
+             the base (U or U2) read by the last product of each ETD2RKds
+             Tucker operator: 16 + 8/d B per point on average.
+    The bound is the slower of the two at the measured peaks (dense BF16
+    burst, HBM copy); `frac` is the algorithmic fraction.  The split-precision
+    form issues 6 (BF16x3) or 3 TF32 (= 6 BF16-rate) MMAs per algorithmic
+    product: `issued_tensor_frac` counts them."""
+    d = p.d
+    N = float(p.npoints)
+    nmu = float(sum(p.n[:d])) / d
+    flops = 4.0 * nmu * N
+    per_pt = 16.0 + (8.0 / d if p.scheme == wl.ETD2RKDS else 0.0)
+    nbytes = per_pt * N + 2.0 * 4.0 * nmu * nmu
+    issue = 3.0 if prec == wl.TF32X3 else 6.0
+    ratio = 0.5 if prec == wl.TF32X3 else 1.0
+    tc_peak = peaks["bf16_tflops"] * 1e12 * ratio
+    bw = peaks["hbm_gbs"] * 1e9
+    avg_s = ms_launch / 1e3
+    t_tc, t_hbm = flops / tc_peak, nbytes / bw
+    common = {"kernel": "mode_product_tc", "traffic": traffic,
+              "duration_us": 1e6 * avg_s,
+              "duration_source": "adr_plan_time_mode_products: the mode-product launches of 64 "
+                                 "steps replayed back to back in one CUDA graph (programmatic "
+                                 "dependent launch, no timing node between launches)",
+              "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+              "tensor_frac_algorithmic": t_tc / avg_s, "hbm_frac_algorithmic": t_hbm / avg_s,
+              "issued_tensor_frac": issue * t_tc / avg_s,
+              "issued_mmas_per_product": int(issue),
+              "launches_per_time_step": per_step}
+    if t_tc >= t_hbm:
+        return dict(common, bound="tensor", achieved=flops / avg_s / 1e12, peak=tc_peak / 1e12,
+                    unit="TFLOP/s", frac=t_tc / avg_s,
+                    peak_source=f"{peak_src} dense bf16 burst (x{ratio})")
+    return dict(common, bound="hbm", achieved=nbytes / avg_s / 1e9, peak=bw / 1e9, unit="GB/s",
+                frac=t_hbm / avg_s, peak_source=f"{peak_src} HBM copy bandwidth")
+
+
+def run_single(args, p, nts: int, R, with_compare: bool, oracle):
+    """One single-solve workload: timed solves from resident data, e2e
+    through adr_solve, roofline, accuracy; returns the JSON fields (rank 0)."""
+    import torch
+    import paper_2307_10684_gb300 as adr
+
+    world, rank, local = R.world, R.rank, R.local
+    prec = p.precision
+    dt = adr.state_dtype(prec)
+    u0n, v0n = wl.initial_data(p)
+    u0 = torch.tensor(wl.round_to(u0n, prec), dtype=dt, device="cuda")
+    v0 = torch.tensor(wl.round_to(v0n, prec), dtype=dt, device="cuda")
+    u = torch.empty_like(u0)
+    v = torch.empty_like(v0)
+    stream = torch.cuda.current_stream()
+
+    # kernel choice by the library's autotuner (times each tensor-core kernel
+    # on this grid), then the plan
+    t0 = time.perf_counter()
+    if args.kernel == -2 and prec in (wl.BF16X3, wl.TF32X3):
+        kernel, tune_ms = adr.autotune(p)
+    else:
+        kernel, tune_ms = max(args.kernel, -1), {}
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plan = adr.Plan(p, kernel=kernel)
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def one_solve():
+        u.copy_(u0)
+        v.copy_(v0)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.step(u, v, nts)
+        e1.record(stream)
+        return e0, e1
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    plan.set_timing(False)  # resets the counters; steps replay captured CUDA graphs
+    R.barrier()
+    torch.cuda.synchronize()
+    evs = [one_solve() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    R.barrier()
+    launches = plan.stats()["launches"]
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = R.max(sum(ms))
+    npts = p.npoints
+    value = whole_job_rate(npts * nts * args.steps, world, tot_ms / 1e3)
+    # the timed state after one solve, for the accuracy fields below
+    one_solve()
+    torch.cuda.synchronize()
+    uf, vf = u.clone(), v.clone()
+
+    # per-kernel shares: the same solves again with each launch bracketed by
+    # CUDA events (graph chunks replayed with event-record nodes: no host
+    # launch gap is timed, but the kernels are serialised)
+    plan.set_timing(True)
+    for _ in range(args.steps):
+        one_solve()
+    torch.cuda.synchronize()
+    stats = plan.stats()
+    plan.set_timing(False)
+    kern = {k: d for k, d in stats["kernels"].items() if d["count"] > 0}
+    total_kernel_ms = sum(d["ms"] for d in kern.values())
+
+    # end to end through adr_solve with pinned host buffers
+    hu0 = u0.cpu().pin_memory()
+    hv0 = v0.cpu().pin_memory()
+    huT = torch.empty_like(hu0).pin_memory()
+    hvT = torch.empty_like(hv0).pin_memory()
+    plan.solve(hu0, hv0, huT, hvT, nts)  # warm
+    torch.cuda.synchronize()
+    R.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.solve(hu0, hv0, huT, hvT, nts)
+    e2e_s = R.max(time.perf_counter() - t0)
+    e2e = {"value": whole_job_rate(npts * nts * args.steps, world, e2e_s), "unit": "point-steps/s",
+           "h2d_bytes_per_step": int(2 * hu0.numel() * hu0.element_size()),
+           "d2h_bytes_per_step": int(2 * huT.numel() * huT.element_size())}
+
+    # roofline of the dominant kernel class
+    peaks, peak_src = load_peaks()
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    kd = kern[dom]
+    in_step = None
+    if dom == "mode_product_tc":
+        used = kernel if kernel >= 0 else (4 if npts >= 1000000 else 0)  # the plan default
+        traffic = profiled_traffic(p.name, used) if p.scheme == wl.ETD2RKDS else None
+        ms_launch, per_step = plan.time_mode_products(u, v, reps=64)
+        roof = mode_product_roofline(p, prec, ms_launch, per_step, peaks, peak_src, traffic)
+        roof["share_of_kernel_time"] = kd["ms"] / total_kernel_ms
+        step_ms = tot_ms / args.steps / nts
+        in_step = {"mode_product_ms_per_time_step": per_step * ms_launch,
+                   "time_step_ms": step_ms, "fits": per_step * ms_launch <= step_ms}
+    elif dom == "mode_product_simt":
+        avg_s = kd["ms"] / kd["count"] / 1e3
+        flops = kd["flops"] / kd["count"]
+        # the dense GEMM rate in the kernel's type, measured here (the peaks
+        # file holds only HBM and BF16): best of 5 torch.matmul at 4096^2
+        gdt = torch.float64 if prec == wl.FP64 else torch.float32
+        peak = measured_gemm_peak(gdt)
+        achieved = flops / avg_s
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "peak_source": f"measured {'FP64' if prec == wl.FP64 else 'FP32'} dense GEMM "
+                               "(torch.matmul 4096^2, best of 5)",
+                "duration_source": "event-bracketed launches (serialised)",
+                "share_of_kernel_time": kd["ms"] / total_kernel_ms}
+    else:
+        avg_s = kd["ms"] / kd["count"] / 1e3
+        bytes_ = kd["bytes"] / kd["count"]
+        achieved = bytes_ / avg_s
+        peak = peaks["hbm_gbs"] * 1e9
+        roof = {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom}
+
+    # accuracy: against the oracle's whole-horizon solve (rank 0), and
+    # against an FP64 GPU solve of the same data
+    acc = {}
+    if not args.no_check:
+        p64 = p.replace(precision=wl.FP64)
+        ur = u0.double().clone()
+        vr = v0.double().clone()
+        with adr.Plan(p64) as plan64:
+            plan64.step(ur, vr, nts)
+        torch.cuda.synchronize()
+        du, mu = adr.max_abs_diff(uf, ur)
+        dv, mv = adr.max_abs_diff(vf, vr)
+        acc["max_rel_err_vs_fp64_gpu"] = max(du / mu, dv / mv)
+        if oracle is not None:
+            oj, idx = oracle
+            Uo, Vo, osec = oj.result(idx)
+            uo = torch.tensor(Uo, dtype=torch.float64, device="cuda")
+            vo = torch.tensor(Vo, dtype=torch.float64, device="cuda")
+            du, mu = adr.max_abs_diff(uf, uo)
+            dv, mv = adr.max_abs_diff(vf, vo)
+            acc["max_rel_err_vs_oracle"] = max(du / mu, dv / mv)
+            du, mu = adr.max_abs_diff(ur, uo)
+            dv, mv = adr.max_abs_diff(vr, vo)
+            acc["fp64_gpu_vs_oracle"] = max(du / mu, dv / mv)
+            acc["oracle_solve"] = {"steps": nts, "seconds": round(osec, 1),
+                                   "threads": oj.threads}
+
+    compare = None
+    if with_compare and args.compare and args.compare not in ("none", args.precision):
+        cp = PREC[args.compare]
+        pc = p.replace(precision=cp)
+        cdt = adr.state_dtype(cp)
+        cu0 = torch.tensor(wl.round_to(u0n, cp), dtype=cdt, device="cuda")
+        cv0 = torch.tensor(wl.round_to(v0n, cp), dtype=cdt, device="cuda")
+        cu, cv = torch.empty_like(cu0), torch.empty_like(cv0)
+        with adr.Plan(pc) as cplan:
+            cms = []
+            for k in range(1 + max(1, args.steps // 2)):
+                cu.copy_(cu0)
+                cv.copy_(cv0)
+                flush.fill_(1.0)
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                cplan.step(cu, cv, nts)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                if k > 0:
+                    cms.append(a0.elapsed_time(a1))
+        compare = {"precision": args.compare, "ms_per_step": float(np.mean(cms)),
+                   "value": npts * nts / (float(np.mean(cms)) / 1e3),
+                   "speedup_of_headline": (float(np.mean(cms)) / (tot_ms / args.steps))}
+        if oracle is not None:
+            Uo, Vo, _ = oracle[0].result(oracle[1])
+            du, mu = adr.max_abs_diff(cu, torch.tensor(Uo, dtype=torch.float64, device="cuda"))
+            dv, mv = adr.max_abs_diff(cv, torch.tensor(Vo, dtype=torch.float64, device="cuda"))
+            compare["max_rel_err_vs_oracle"] = max(du / mu, dv / mv)
+
+    plan.close()
+    if rank != 0:
+        return None
+    state = {0: "auto", 1: "plain", 2: "compensated"}[int(getattr(p, "state", 0))]
+    return {"metric": "point-steps/s", "value": value, "unit": "point-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[prec],
+            "data": "synthetic (seeded SplitMix64 data)",
+            "config": {"workload": p.name, "grid": list(p.n[: p.d]), "tau": p.tau,
+                       "scheme": SCHEME_NAMES[p.scheme], "state": state,
+                       "time_steps_per_bench_step": nts, "precision": PREC_NAME[prec],
+                       "l2": "flushed between timed solves (256 MB write)",
+                       "parallelism": f"replicas x{world}",
+                       "kernel": {"chosen": kernel, "by": "adr_autotune" if tune_ms else "--kernel",
+                                  "ms_per_step": {str(k): round(t, 4) for k, t in tune_ms.items()},
+                                  "tuning_s": round(tune_s, 2)}},
+            **acc, "plan_ms": plan_ms,
+            "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "in_step_check": in_step, "clocks": clocks,
+            "same_gpu_comparison": compare,
+            "kernel_timing": "per-kernel shares from a second pass of the same solves; graph "
+                             "chunks replayed with an event-record node before and after every "
+                             "kernel (no host launch gaps; kernels serialised)",
+            "kernels": {k: {"count": d["count"], "avg_us": 1e3 * d["ms"] / d["count"],
+                            "share": d["ms"] / total_kernel_ms} for k, d in kern.items()}}
 
 
 def run_batch(args):
@@ -609,7 +913,14 @@ def main():
                     help="also time this precision on the same workload ('none' to skip)")
     ap.add_argument("--time-steps", type=int, default=None,
                     help="ETD2RKds steps per bench step (default: the workload's)")
-    ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy solve")
+    ap.add_argument("--no-check", action="store_true", help="skip the accuracy solves")
+    ap.add_argument("--oracle-check", type=int, default=1,
+                    help="1: accuracy against the oracle's whole-horizon solve (spawned process)")
+    ap.add_argument("--oracle-threads", type=int, default=12,
+                    help="BLAS threads of the oracle process (the rest stay with the GPU process)")
+    ap.add_argument("--secondary", default="bruss256",
+                    help="with the default fhn1024 workload, also measure this single-solve "
+                         "workload and report it under secondary_workload ('none' to skip)")
     ap.add_argument("--scheme", default="etd2rkds", choices=sorted(SCHEMES),
                     help="time-stepping scheme of the single-solve workloads (fhn1024, "
                          "bruss256, schnak64)")
@@ -634,197 +945,39 @@ def main():
         return
 
     import torch
-    import paper_2307_10684_gb300 as adr
 
     R = Replicas()
     world, rank, local = R.world, R.rank, R.local
-    torch.cuda.set_device(local)
-
     prec = PREC[args.precision]
     p = workload(args.workload, prec).replace(scheme=SCHEMES[args.scheme])
     nts = args.time_steps or p.nsteps
-    dt = adr.state_dtype(prec)
-    u0n, v0n = wl.initial_data(p)
-    u0 = torch.tensor(wl.round_to(u0n, prec), dtype=dt, device="cuda")
-    v0 = torch.tensor(wl.round_to(v0n, prec), dtype=dt, device="cuda")
-    u = torch.empty_like(u0)
-    v = torch.empty_like(v0)
-    stream = torch.cuda.current_stream()
-
-    # kernel choice by the library's autotuner (times each tensor-core kernel
-    # on this grid), then the plan
-    t0 = time.perf_counter()
-    if args.kernel == -2 and prec in (wl.BF16X3, wl.TF32X3):
-        kernel, tune_ms = adr.autotune(p)
-    else:
-        kernel, tune_ms = max(args.kernel, -1), {}
-    tune_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    plan = adr.Plan(p, kernel=kernel)
-    plan_ms = 1e3 * (time.perf_counter() - t0)
-
-    # accuracy of this precision against an FP64 GPU solve of the same data
-    max_rel = None
-    if not args.no_check:
-        u.copy_(u0)
-        v.copy_(v0)
-        plan.step(u, v, nts)
-        p64 = p.replace(precision=wl.FP64)
-        ur = u0.double().clone()
-        vr = v0.double().clone()
-        with adr.Plan(p64) as plan64:
-            plan64.step(ur, vr, nts)
-        torch.cuda.synchronize()
-        du, mu = adr.max_abs_diff(u, ur)
-        dv, mv = adr.max_abs_diff(v, vr)
-        max_rel = max(du / mu, dv / mv)
-
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-
-    def one_solve():
-        u.copy_(u0)
-        v.copy_(v0)
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        plan.step(u, v, nts)
-        e1.record(stream)
-        return e0, e1
-
-    for _ in range(args.warmup):
-        one_solve()
-    torch.cuda.synchronize()
-
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    plan.set_timing(False)  # resets the counters; steps replay captured CUDA graphs
-    R.barrier()
-    torch.cuda.synchronize()
-    evs = [one_solve() for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    R.barrier()
-    launches = plan.stats()["launches"]
-    clocks = sampler.stop()
-    ms = [a.elapsed_time(b) for a, b in evs]
-    tot_ms = R.max(sum(ms))
-    # per-kernel timing: the same solves again, each launch bracketed by CUDA
-    # events on the plan's stream; the library replays its graph chunks with
-    # the events as event-record nodes (so no host launch gap is timed), which
-    # serialises the kernels (no programmatic overlap) during this pass only
-    plan.set_timing(True)
-    for _ in range(args.steps):
-        one_solve()
-    torch.cuda.synchronize()
-    stats = plan.stats()
-    plan.set_timing(False)
-    npts = p.npoints
-    value = whole_job_rate(npts * nts * args.steps, world, tot_ms / 1e3)
-
-    # end to end through adr_solve with pinned host buffers
-    hu0 = u0.cpu().pin_memory()
-    hv0 = v0.cpu().pin_memory()
-    huT = torch.empty_like(hu0).pin_memory()
-    hvT = torch.empty_like(hv0).pin_memory()
-    plan.solve(hu0, hv0, huT, hvT, nts)  # warm
-    torch.cuda.synchronize()
-    R.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        plan.solve(hu0, hv0, huT, hvT, nts)
-    e2e_s = R.max(time.perf_counter() - t0)
-    e2e = {"value": whole_job_rate(npts * nts * args.steps, world, e2e_s), "unit": "point-steps/s",
-           "h2d_bytes_per_step": int(2 * hu0.numel() * hu0.element_size()),
-           "d2h_bytes_per_step": int(2 * huT.numel() * huT.element_size())}
-
-    # roofline of the dominant kernel class (live CUDA-event timing)
-    peaks, peak_src = load_peaks()
-    kern = {k: d for k, d in stats["kernels"].items() if d["count"] > 0}
-    dom = max(kern, key=lambda k: kern[k]["ms"])
-    kd = kern[dom]
-    avg_s = kd["ms"] / kd["count"] / 1e3
-    total_kernel_ms = sum(d["ms"] for d in kern.values())
-    if dom == "mode_product_simt":
-        flops = kd["flops"] / kd["count"]
-        # the dense GEMM rate in the kernel's type, measured here (the peaks
-        # file holds only HBM and BF16): best of 5 torch.matmul at 4096^2
-        dt = torch.float64 if prec == wl.FP64 else torch.float32
-        peak = measured_gemm_peak(dt)
-        bound, unit = "alu", "TFLOP/s"
-        peak_note = (f"measured {'FP64' if prec == wl.FP64 else 'FP32'} dense GEMM "
-                     "(torch.matmul 4096^2, best of 5)")
-        achieved = flops / avg_s
-        roof = {"bound": bound, "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "kernel": dom,
-                "peak_source": peak_note, "share_of_kernel_time": kd["ms"] / total_kernel_ms}
-    elif dom == "mode_product_tc":
-        used = kernel if kernel >= 0 else (4 if npts >= 1000000 else 0)  # the plan default
-        traffic = profiled_traffic(args.workload, used) if p.scheme == wl.ETD2RKDS else None
-        roof = tc_roofline(kd, prec, peaks, peak_src, traffic)
-        roof["share_of_kernel_time"] = kd["ms"] / total_kernel_ms
-    else:
-        bytes_ = kd["bytes"] / kd["count"]
-        achieved = bytes_ / avg_s
-        peak = peaks["hbm_gbs"] * 1e9
-        roof = {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom}
-
-    compare = None
-    if args.compare and args.compare not in ("none", args.precision):
-        cp = PREC[args.compare]
-        pc = workload(args.workload, cp)
-        cdt = adr.state_dtype(cp)
-        cu0 = torch.tensor(wl.round_to(u0n, cp), dtype=cdt, device="cuda")
-        cv0 = torch.tensor(wl.round_to(v0n, cp), dtype=cdt, device="cuda")
-        cu, cv = torch.empty_like(cu0), torch.empty_like(cv0)
-        with adr.Plan(pc) as cplan:
-            cms = []
-            for k in range(1 + max(1, args.steps // 2)):
-                cu.copy_(cu0)
-                cv.copy_(cv0)
-                flush.fill_(1.0)
-                a0 = torch.cuda.Event(enable_timing=True)
-                a1 = torch.cuda.Event(enable_timing=True)
-                a0.record(stream)
-                cplan.step(cu, cv, nts)
-                a1.record(stream)
-                torch.cuda.synchronize()
-                if k > 0:
-                    cms.append(a0.elapsed_time(a1))
-        compare = {"precision": args.compare, "ms_per_step": float(np.mean(cms)),
-                   "value": npts * nts / (float(np.mean(cms)) / 1e3),
-                   "speedup_of_headline": (float(np.mean(cms)) / (tot_ms / args.steps))}
-
-    cpu = None
-    if rank == 0 and world == 1 and args.cpu_sample > 0:
-        cpu = cpu_baseline(p, args.cpu_sample)
-
-    if rank == 0:
-        line = {"metric": "point-steps/s", "value": value, "unit": "point-steps/s",
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[prec],
-                "data": "synthetic (seeded SplitMix64 N(0,0.05^2) data)",
-                "config": {"workload": p.name, "grid": list(p.n[: p.d]), "tau": p.tau,
-                           "scheme": SCHEME_NAMES[p.scheme],
-                           "time_steps_per_bench_step": nts, "precision": args.precision,
-                           "l2": "flushed between timed solves (256 MB write)",
-                           "parallelism": f"replicas x{world}",
-                           "kernel": {"chosen": kernel, "by": "adr_autotune" if tune_ms else "--kernel",
-                                      "ms_per_step": {str(k): round(t, 4) for k, t in tune_ms.items()},
-                                      "tuning_s": round(tune_s, 2)}},
-                "max_rel_err_vs_fp64": max_rel, "plan_ms": plan_ms,
-                "e2e": e2e, "gpu_launches": launches,
-                "kernel_timing": "second pass of the same solves; the graph chunks are replayed "
-                                 "with an event-record node before and after every kernel "
-                                 "(no host launch gaps; kernels serialised)",
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
-                "same_gpu_comparison": compare,
-                "kernels": {k: {"count": d["count"], "avg_us": 1e3 * d["ms"] / d["count"]}
-                            for k, d in kern.items()}}
+    # the oracle's solves of the timed workloads, for the accuracy fields: a
+    # spawned process (rank 0, one replica) running while the GPU works
+    second = None
+    if args.workload == "fhn1024" and args.secondary != "none":
+        second = workload(args.secondary, prec).replace(scheme=SCHEMES[args.scheme])
+    jobs = []
+    if rank == 0 and not args.no_check and args.oracle_check:
+        jobs.append((p, nts))
+        if second is not None:
+            jobs.append((second, second.nsteps))
+    oj = OracleJobs(jobs, threads=args.oracle_threads) if jobs else None
+    torch.cuda.set_device(local)
+    line = run_single(args, p, nts, R, with_compare=True, oracle=(oj, 0) if oj else None)
+    if second is not None:
+        sub = run_single(args, second, second.nsteps, R, with_compare=False,
+                         oracle=(oj, 1) if oj and len(jobs) > 1 else None)
+        if line is not None and sub is not None:
+            for k in ("n_gpus", "steps", "warmup", "higher_is_better", "scaling", "vs_baseline",
+                      "cpu_baseline"):
+                sub.pop(k, None)
+            line["secondary_workload"] = sub
+    if oj:
+        oj.close()
+    if rank == 0 and line is not None and world == 1 and args.cpu_sample > 0:
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_sample)
+    if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
-    plan.close()
     R.close()
 
 

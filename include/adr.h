@@ -108,6 +108,41 @@ typedef enum {
   ADR_LAWSON2B = 1
 } adr_scheme;
 
+/* How a single-precision state is carried from step to step.
+ *  ADR_STATE_PLAIN       : the caller's buffers are the whole state; each
+ *                          stage update U + tau T of Eq. 11 is rounded to
+ *                          FP32.  Over long horizons these roundings
+ *                          accumulate, by ~1e-7 relative per step and more
+ *                          where the dynamics amplify them.
+ *  ADR_STATE_COMPENSATED : the state is hi + lo: hi in the caller's buffer
+ *                          (the FP32 value nearest the state) and lo, a
+ *                          low-order FP32 word per point and component, in
+ *                          plan memory.  The stage updates of Eq. 11 add the
+ *                          increment to hi + lo with its exact rounding
+ *                          error (TwoSum) and renormalise, so the state
+ *                          keeps about 48 bits; the right-hand sides are
+ *                          evaluated from hi.  16 bytes of extra traffic per
+ *                          point and step.  The lo words carry over from one
+ *                          call to the next while the plan (alone or in a
+ *                          batch) steps the same (u, v) pair; they restart
+ *                          at zero when it steps another pair, when
+ *                          adr_solve starts, and on adr_plan_reset_state.
+ *                          A caller that writes new values into buffers the
+ *                          plan has stepped calls adr_plan_reset_state.
+ *  ADR_STATE_AUTO        : the library's choice.  For ADR_BF16X3 and
+ *                          ADR_TF32X3 plans of ADR_ETD2RKDS: compensated
+ *                          within each call (the lo words restart at zero at
+ *                          every adr_step, adr_solve and adr_batch_step
+ *                          call, so reused buffers need nothing extra);
+ *                          plain for every other plan.
+ * Compensation applies to tensor-core ETD2RKds plans only: other plans
+ * asking for ADR_STATE_COMPENSATED get ADR_EUNSUPPORTED. */
+typedef enum {
+  ADR_STATE_AUTO = 0,
+  ADR_STATE_PLAIN = 1,
+  ADR_STATE_COMPENSATED = 2
+} adr_state_mode;
+
 /* One problem.  Direction mu = 0 is x_1 (the contiguous axis). */
 typedef struct {
   int32_t d;            /* 2 or 3                                           */
@@ -120,6 +155,8 @@ typedef struct {
   double adv[2][3];     /* velocity of the term -adv[c] . grad(c)           */
   double params[16];    /* model constants, see adr_model                   */
   double tau;           /* constant time step (> 0)                         */
+  int32_t state;        /* adr_state_mode (0 = the library's choice)        */
+  int32_t reserved;     /* must be 0                                        */
 } adr_problem;
 
 typedef struct adr_plan_s* adr_plan;
@@ -204,6 +241,13 @@ adr_status adr_plan_destroy(adr_plan plan);
  * 16-byte aligned (ADR_EINVAL otherwise).  nsteps >= 0.  Asynchronous. */
 adr_status adr_step(adr_plan plan, void* u, void* v, int64_t nsteps);
 
+/* Restart the compensation of a plan's state (adr_state_mode): the
+ * low-order words are cleared, so the next step continues from the
+ * caller's buffers alone.  Call it after writing new values into buffers
+ * the plan has already stepped under ADR_STATE_COMPENSATED.  Enqueued on
+ * the plan's stream; a no-op for plain plans.  No counterpart in the paper. */
+adr_status adr_plan_reset_state(adr_plan plan);
+
 /* Solve from (u0, v0) for nsteps steps into (uT, vT).  Each pointer may be
  * host or device memory; host inputs are copied to the device, host outputs
  * copied back, and in that case the call returns after the copy-back has
@@ -222,6 +266,20 @@ adr_status adr_plan_bytes(const adr_problem* problem, size_t* state_bytes, size_
  * Synchronous. */
 adr_status adr_plan_matrix(adr_plan plan, int which, int component, int mu, double* out);
 
+/* Measurement aid (no counterpart in the paper): the duration of one
+ * tensor-core mode-product launch as it runs inside a step.  The launches
+ * of `reps` steps' Tucker operators (4 d per ETD2RKds step) are captured
+ * back to back in one CUDA graph, with programmatic dependent launch
+ * between them and no timing node in between, and the graph is replayed
+ * once to warm up and once between two CUDA events on the plan's stream.
+ * *ms_per_launch = that replay's time / (reps x *launches_per_step).
+ * u, v: device scratch state buffers of the plan's shape, 16-byte aligned;
+ * their contents are overwritten (the last product of each Tucker operator
+ * writes the state).  reps in [1, 4096].  Tensor-core plans only
+ * (ADR_EUNSUPPORTED otherwise).  Synchronous. */
+adr_status adr_plan_time_mode_products(adr_plan plan, void* u, void* v, int32_t reps,
+                                       double* ms_per_launch, int32_t* launches_per_step);
+
 /* Counters of a plan since creation (or the last reset). */
 typedef struct {
   int64_t launches;        /* kernels launched by adr_step / adr_solve     */
@@ -229,7 +287,12 @@ typedef struct {
   int32_t timing;          /* 1 if per-kernel event timing is on           */
   int32_t nkernels;        /* entries used in the arrays below             */
   int32_t device_error;    /* 0, or the code a bounded device wait left    */
-  int32_t reserved;
+  int32_t shared_matrices; /* directional matrix sets (A, e^(tau A), phi_1,
+                              phi_2 of one operator) this plan took from the
+                              library's cache instead of computing: plans
+                              whose operators and step coincide share one
+                              refcounted copy (as do their split operand
+                              pieces)                                         */
   char    name[16][32];    /* kernel class names                           */
   int64_t count[16];       /* timed launches per class                     */
   double  ms[16];          /* summed CUDA-event time per class (ms)        */
@@ -262,11 +325,15 @@ typedef struct adr_batch_s* adr_batch;
  * `stream`.  Synchronous. */
 adr_status adr_batch_create(const adr_plan* plans, int count, void* stream, adr_batch* out);
 adr_status adr_batch_destroy(adr_batch batch);
-/* Advance solve i's device state (u[i], v[i]) by nsteps steps, all solves in
- * lock-step; u and v are host arrays of `count` device pointers.  The first
- * call with a new set of pointers uploads the per-solve descriptors
- * (synchronous); later calls are asynchronous. */
-adr_status adr_batch_step(adr_batch batch, void* const* u, void* const* v, int64_t nsteps);
+/* Advance solve i's device state (u[i], v[i]) by nsteps[i] steps (its own
+ * horizon, >= 0); u, v and nsteps are host arrays of `count` entries.  The
+ * solves advance in lock-step while they run: between consecutive distinct
+ * horizons the solves that are still running form one grouped launch
+ * sequence (a batch over that subset, built on first use and kept with the
+ * batch), so a solve that has finished drops out of the work of the rest.
+ * The first call with a new set of pointers (per subset) uploads the
+ * per-solve descriptors; calls are asynchronous. */
+adr_status adr_batch_step(adr_batch batch, void* const* u, void* const* v, const int64_t* nsteps);
 /* Timing and counters of the batch's launches (as for plans). */
 adr_status adr_batch_set_timing(adr_batch batch, int enable);
 adr_status adr_batch_stats(adr_batch batch, adr_stats* out);
@@ -291,7 +358,10 @@ adr_status adr_max_abs_diff(void* stream, const void* x, int x_is_double, const 
  * 67,108,864 (2^26) elements; larger counts return ADR_EINVAL and enqueue
  * nothing.  The first call on a device resolves the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array, so calls that
+ * before any stream capture.  The resolved address is kept for the life of
+ * the process: it belongs to the device's primary context, so after a
+ * cudaDeviceReset of that device in this process it is stale and this entry
+ * point must not be called again.  All calls share the one array, so calls that
  * overlap on the GPU (different streams, or different host threads) race and
  * may return each other's results.  Enqueued on `stream`, synchronised before
  * returning; out: host. */
@@ -307,6 +377,31 @@ adr_status adr_max_abs_diff_noalloc(void* stream, const void* x, int x_is_double
  * synchronous. */
 adr_status adr_indicators(adr_plan plan, const void* u_prev, const void* v_prev, const void* u,
                           const void* v, double out[4]);
+
+/* Indicators of Sec. 4 fused into the step: with them on, the last product
+ * of every ETD2RKds step also accumulates, in FP64, the trapezoid-weighted
+ * spatial means <U_{n+1}>, <V_{n+1}> and the increments ||U_{n+1} - U_n||_F,
+ * ||V_{n+1} - V_n||_F (reading the previous state before overwriting it: 8
+ * bytes more traffic per point and step), into a ring of the last 4096 steps
+ * in plan memory.  Tensor-core ETD2RKds plans only (ADR_EUNSUPPORTED
+ * otherwise), not while a live batch uses the plan (ADR_EBUSY).  Enabling
+ * clears the history; the state results are the same with them on or off.
+ * Synchronises the plan's stream. */
+adr_status adr_plan_set_indicators(adr_plan plan, int enable);
+/* The indicators of the last min(max_steps, steps since enabling, 4096)
+ * steps, oldest first: out[4 k + 0..3] = <U>, <V>, ||dU||_F, ||dV||_F of
+ * step k.  *count = the number of steps written.  Synchronous. */
+adr_status adr_plan_indicator_log(adr_plan plan, double* out, int64_t max_steps, int64_t* count);
+/* Step-count-free run (the pattern and equilibrium runs of Sec. 4): advance
+ * (u, v) in place (device pointers) until the physical time t_end, that is
+ * ceil(t_end / tau) steps, or, when tol > 0, until the increment indicator
+ * of a checked step, max(||U_{n+1} - U_n||_F, ||V_{n+1} - V_n||_F), is at
+ * most tol (a stationary state).  The indicators are checked every
+ * check_every >= 1 steps, each check synchronising the plan's stream.
+ * *steps_done = steps taken; ind_last = the indicators of the last step.
+ * Needs adr_plan_set_indicators(plan, 1).  Synchronous. */
+adr_status adr_run(adr_plan plan, void* u, void* v, double t_end, double tol, int64_t check_every,
+                   int64_t* steps_done, double ind_last[4]);
 
 /* Short name of a status code (static storage). */
 const char* adr_status_str(adr_status s);

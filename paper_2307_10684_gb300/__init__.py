@@ -20,7 +20,7 @@ from . import _abi
 from ._abi import (ADR_OK, ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA, ADR_EUNSUPPORTED,  # noqa: F401
                    ADR_ETIMEOUT, ADR_ENUMERIC, ADR_EBUSY, FP64, FP32, TF32X3, BF16X3,
                    SCHNAKENBERG, FHN, BRUSSELATOR, NO_REACTION, FHN_RHO, DIB, ETD2RKDS,
-                   LAWSON2B, AdrError, lib,
+                   LAWSON2B, STATE_AUTO, STATE_PLAIN, STATE_COMPENSATED, AdrError, lib,
                    library_path)
 
 __all__ = ["Plan", "Batch", "AdrError", "lib", "library_path", "plan_bytes", "max_abs_diff",
@@ -51,6 +51,7 @@ def make_problem(p) -> _abi.AdrProblem:
     for i in range(16):
         s.params[i] = float(p.params[i]) if i < len(p.params) else 0.0
     s.tau = float(p.tau)
+    s.state = int(getattr(p, "state", 0))
     return s
 
 
@@ -131,6 +132,51 @@ class Plan:
         _abi.check(lib().adr_step(self._p, ctypes.c_void_p(u.data_ptr()),
                                   ctypes.c_void_p(v.data_ptr()), ctypes.c_int64(int(nsteps))))
 
+    def time_mode_products(self, u, v, reps: int = 32):
+        """adr_plan_time_mode_products: (ms per mode-product launch inside a
+        step, launches per step); u, v are scratch tensors (overwritten)."""
+        self._check_state(u, True)
+        self._check_state(v, True)
+        ms = ctypes.c_double()
+        n = ctypes.c_int32()
+        _abi.check(lib().adr_plan_time_mode_products(self._p, ctypes.c_void_p(u.data_ptr()),
+                                                     ctypes.c_void_p(v.data_ptr()), int(reps),
+                                                     ctypes.byref(ms), ctypes.byref(n)))
+        return float(ms.value), int(n.value)
+
+    def set_indicators(self, enable: bool = True):
+        """adr_plan_set_indicators: per-step indicators of Sec. 4 fused into
+        the last product of every step."""
+        _abi.check(lib().adr_plan_set_indicators(self._p, 1 if enable else 0))
+
+    def indicator_log(self, max_steps: int = 4096):
+        """adr_plan_indicator_log: numpy [steps, 4] of (<U>, <V>, ||dU||_F,
+        ||dV||_F), oldest step first."""
+        import numpy as np
+        out = np.zeros((max(int(max_steps), 1), 4), dtype=np.float64)
+        n = ctypes.c_int64()
+        _abi.check(lib().adr_plan_indicator_log(
+            self._p, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(max_steps),
+            ctypes.byref(n)))
+        return out[: n.value].copy()
+
+    def run(self, u, v, t_end: float, tol: float = 0.0, check_every: int = 32):
+        """adr_run: step until t_end or until the increment indicator <= tol;
+        returns (steps taken, indicators of the last step)."""
+        self._check_state(u, True)
+        self._check_state(v, True)
+        steps = ctypes.c_int64()
+        last = (ctypes.c_double * 4)()
+        _abi.check(lib().adr_run(self._p, ctypes.c_void_p(u.data_ptr()),
+                                 ctypes.c_void_p(v.data_ptr()), float(t_end), float(tol),
+                                 int(check_every), ctypes.byref(steps), last))
+        return int(steps.value), [float(x) for x in last]
+
+    def reset_state(self):
+        """adr_plan_reset_state: restart the compensated state's low-order
+        words (after writing new values into buffers already stepped)."""
+        _abi.check(lib().adr_plan_reset_state(self._p))
+
     def solve(self, u0, v0, uT, vT, nsteps: int):
         """adr_solve: tensors may live on the host (pinned) or the device."""
         for x in (u0, v0, uT, vT):
@@ -175,7 +221,8 @@ def _stats_dict(st) -> dict:
             "count": int(st.count[k]), "ms": float(st.ms[k]),
             "flops": float(st.flops[k]), "bytes": float(st.bytes[k])}
     return {"launches": int(st.launches), "steps": int(st.steps), "timing": bool(st.timing),
-            "device_error": int(st.device_error), "kernels": kernels}
+            "device_error": int(st.device_error), "shared_matrices": int(st.shared_matrices),
+            "kernels": kernels}
 
 
 _tuned = {}
@@ -261,16 +308,22 @@ class Batch:
     def grouped(self) -> bool:
         return bool(lib().adr_batch_is_grouped(self._b))
 
-    def step(self, us, vs, nsteps: int = 1):
-        """Advance every solve i's CUDA tensors (us[i], vs[i]) in place."""
+    def step(self, us, vs, nsteps=1):
+        """Advance every solve i's CUDA tensors (us[i], vs[i]) in place by
+        nsteps[i] steps (one int: the same for every solve)."""
         if len(us) != len(self.plans) or len(vs) != len(self.plans):
             raise ValueError("one (u, v) pair per plan")
         for p, u, v in zip(self.plans, us, vs):
             p._check_state(u, True)
             p._check_state(v, True)
+        ns = ([int(n) for n in nsteps] if hasattr(nsteps, "__len__")
+              else [int(nsteps)] * len(us))
+        if len(ns) != len(us):
+            raise ValueError("one horizon per plan")
         U = (ctypes.c_void_p * len(us))(*[u.data_ptr() for u in us])
         V = (ctypes.c_void_p * len(vs))(*[v.data_ptr() for v in vs])
-        _abi.check(lib().adr_batch_step(self._b, U, V, ctypes.c_int64(int(nsteps))))
+        H = (ctypes.c_int64 * len(ns))(*ns)
+        _abi.check(lib().adr_batch_step(self._b, U, V, H))
 
     def set_timing(self, enable: bool):
         _abi.check(lib().adr_batch_set_timing(self._b, 1 if enable else 0))

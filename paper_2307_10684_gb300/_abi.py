@@ -12,6 +12,7 @@ ADR_OK, ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA, ADR_EUNSUPPORTED, ADR_ETIMEOUT, ADR_E
     ADR_EBUSY = range(8)
 SCHNAKENBERG, FHN, BRUSSELATOR, NO_REACTION, FHN_RHO, DIB = range(6)
 ETD2RKDS, LAWSON2B = range(2)
+STATE_AUTO, STATE_PLAIN, STATE_COMPENSATED = range(3)
 FP64, FP32, TF32X3, BF16X3 = range(4)
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
@@ -21,12 +22,12 @@ class AdrProblem(ctypes.Structure):
     _fields_ = [("d", c_int32), ("model", c_int32), ("precision", c_int32), ("scheme", c_int32),
                 ("n", c_int64 * 3), ("lo", c_double * 3), ("hi", c_double * 3),
                 ("diff", c_double * 2), ("adv", (c_double * 3) * 2), ("params", c_double * 16),
-                ("tau", c_double)]
+                ("tau", c_double), ("state", c_int32), ("reserved", c_int32)]
 
 
 class AdrStats(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("steps", c_int64), ("timing", c_int32),
-                ("nkernels", c_int32), ("device_error", c_int32), ("reserved", c_int32),
+                ("nkernels", c_int32), ("device_error", c_int32), ("shared_matrices", c_int32),
                 ("name", (ctypes.c_char * 32) * 16),
                 ("count", c_int64 * 16), ("ms", c_double * 16), ("flops", c_double * 16),
                 ("bytes", c_double * 16)]
@@ -53,6 +54,14 @@ SIGNATURES = {
     "adr_plan_destroy": (c_int32, [AdrPlan]),
     "adr_plan_set_stream": (c_int32, [AdrPlan, c_void_p]),
     "adr_step": (c_int32, [AdrPlan, c_void_p, c_void_p, c_int64]),
+    "adr_plan_reset_state": (c_int32, [AdrPlan]),
+    "adr_plan_set_indicators": (c_int32, [AdrPlan, c_int32]),
+    "adr_plan_indicator_log": (c_int32, [AdrPlan, ctypes.POINTER(c_double), c_int64,
+                                         ctypes.POINTER(c_int64)]),
+    "adr_run": (c_int32, [AdrPlan, c_void_p, c_void_p, c_double, c_double, c_int64,
+                          ctypes.POINTER(c_int64), ctypes.POINTER(c_double)]),
+    "adr_plan_time_mode_products": (c_int32, [AdrPlan, c_void_p, c_void_p, c_int32,
+                                              ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
     "adr_solve": (c_int32, [AdrPlan, c_void_p, c_void_p, c_void_p, c_void_p, c_int64]),
     "adr_plan_bytes": (c_int32, [ctypes.POINTER(AdrProblem), ctypes.POINTER(ctypes.c_size_t),
                                  ctypes.POINTER(ctypes.c_size_t)]),
@@ -67,7 +76,7 @@ SIGNATURES = {
                                    ctypes.POINTER(c_void_p)]),
     "adr_batch_destroy": (c_int32, [c_void_p]),
     "adr_batch_step": (c_int32, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
-                                 c_int64]),
+                                ctypes.POINTER(c_int64)]),
     "adr_batch_set_timing": (c_int32, [c_void_p, c_int32]),
     "adr_batch_stats": (c_int32, [c_void_p, ctypes.POINTER(AdrStats)]),
     "adr_batch_is_grouped": (c_int32, [c_void_p]),

@@ -2,7 +2,7 @@
 
 Each .cu file under csrc/ is compiled to an object in parallel, then the
 objects are linked into paper_2307_10684_gb300/_build/libadr_gb300.so.  An
-object is rebuilt when its source or any header is newer than it.
+object is rebuilt when its source or any header (.h, .cuh) is newer than it.
 """
 from __future__ import annotations
 
@@ -32,7 +32,8 @@ def nvcc() -> str:
 
 
 def _headers_mtime() -> float:
-    hs = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    hs = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+          + glob.glob(os.path.join(ROOT, "include", "*.h")))
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 

@@ -3,7 +3,9 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -38,6 +40,8 @@ template <typename T>
 struct ReactionT {
   int model;
   T p[16];
+  T plo[16];  // low-order parts: p + plo is the double-precision parameter
+              // (zero when T is double)
 };
 
 // Stencil + reaction description for one problem, passed by value.  The
@@ -64,7 +68,10 @@ inline PointwiseArgsT<T> cast_args(const PointwiseArgs& a) {
       r.A[c][m] = TridiagT<T>{(T)a.A[c][m].lo, (T)a.A[c][m].di, (T)a.A[c][m].up,
                               (T)a.A[c][m].b0, (T)a.A[c][m].bn};
   r.rx.model = a.rx.model;
-  for (int i = 0; i < 16; ++i) r.rx.p[i] = (T)a.rx.p[i];
+  for (int i = 0; i < 16; ++i) {
+    r.rx.p[i] = (T)a.rx.p[i];
+    r.rx.plo[i] = (T)(a.rx.p[i] - (double)r.rx.p[i]);
+  }
   return r;
 }
 
@@ -114,6 +121,24 @@ cudaError_t launch_indicators(const PointwiseArgs& a, const void* up, const void
 cudaError_t launch_max_abs_diff(const void* x, int x_is_double, const double* ref, int64_t count,
                                 unsigned long long* out2, cudaStream_t s);
 
+
+// Refcounted process-wide cache of device buffer sets (cache.cu): nbuf
+// buffers of `bytes` each, keyed by the values that determine their
+// contents (plus the device).  On a miss the buffers are allocated, filled
+// by fill() on stream s, and inserted once s has completed.  *hit tells
+// whether the set was found.  shared_release takes the first buffer.
+cudaError_t shared_acquire(std::vector<uint64_t> key, int nbuf, size_t bytes,
+                           const std::function<cudaError_t(void* const*)>& fill, cudaStream_t s,
+                           void** out, bool* hit);
+void shared_release(void* first);
+int64_t shared_sets_live();
+
+inline uint64_t key_bits(double x) {
+  uint64_t b;
+  static_assert(sizeof(b) == sizeof(x), "64-bit double");
+  memcpy(&b, &x, sizeof(b));
+  return b;
+}
 
 // Tensor-core operand set of a plan (tc.cu).
 struct TcOperands {
@@ -167,6 +192,8 @@ struct adr_plan_s {
   void* dstate[2];  // device state for adr_solve with host buffers
   double* ind;      // 4 accumulators of adr_indicators
   std::vector<void*> allocs;
+  std::vector<void*> shared;  // matrix sets held in the process-wide cache
+  int32_t shared_hits;        // of them, found there (computed by another plan)
   // counters
   int64_t launches;
   int64_t steps;
@@ -203,11 +230,25 @@ static const char* const kClassNames[KC_COUNT] = {"rhs_stencil_reaction", "react
 void tc_init(TcOperands* t);
 void tc_free(TcOperands* t);
 // variant_req: -1 = the library's choice, else a kernel variant (adr_tuning)
+// comp: carry the state as hi + lo FP32 words; 1 = within each call
+// (ADR_STATE_AUTO), 2 = across calls on the same (u, v) pair
+// (ADR_STATE_COMPENSATED)
 cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t n[3],
-                       double* const master[2][3][4], cudaStream_t s, int variant_req = -1);
+                       double* const master[2][3][4], cudaStream_t s, int variant_req, int comp);
+// Clear the low-order state words (no-op without compensation).
+cudaError_t tc_reset_state(TcOperands* t, cudaStream_t s);
+// Start of a stepping call on (u, v): restarts the low-order words of a
+// compensated state when the call needs it (enqueued on s).
+cudaError_t tc_begin_call(TcOperands* t, void* u, void* v, cudaStream_t s);
 cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v);
 cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v);
 int* tc_error_word(TcOperands* t);
+// Indicators of Sec. 4 accumulated by the last product of every step.
+cudaError_t tc_set_indicators(TcOperands* t, int enable, cudaStream_t s);
+cudaError_t tc_indicator_log(TcOperands* t, cudaStream_t s, double* out, int64_t max_steps,
+                             int64_t* count);
+cudaError_t tc_time_passes(TcOperands* t, adr_plan_s* P, void* u, void* v, int reps, float* ms,
+                           int* passes);
 
 inline cudaEvent_t pool_event(adr_plan_s* P) {
   if (P->event_next < P->event_pool.size()) return P->event_pool[P->event_next++];
@@ -260,3 +301,7 @@ inline void harvest_timing(adr_plan_s* P, const std::vector<TimedLaunch>& v) {
   }
 }
 }  // namespace adr
+
+// Advance a plan's (u, v) by nsteps, continuing its compensated state as it
+// stands (api.cu; the batch path uses it for plans it steps one by one).
+adr_status plan_step_continue(adr_plan plan, void* u, void* v, int64_t nsteps);

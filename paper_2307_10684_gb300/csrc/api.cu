@@ -16,6 +16,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -54,6 +55,11 @@ static adr_status validate(const adr_problem* p) {
   if (p->precision < 0 || p->precision > ADR_BF16X3)
     return fail(ADR_EINVAL, "unknown precision");
   if (!(p->tau > 0.0) || !isfinite(p->tau)) return fail(ADR_EINVAL, "tau must be finite and > 0");
+  if (p->state < ADR_STATE_AUTO || p->state > ADR_STATE_COMPENSATED || p->reserved != 0)
+    return fail(ADR_EINVAL, "unknown state mode (or reserved field not 0)");
+  if (p->state == ADR_STATE_COMPENSATED &&
+      ((p->precision != ADR_BF16X3 && p->precision != ADR_TF32X3) || p->scheme != ADR_ETD2RKDS))
+    return fail(ADR_EUNSUPPORTED, "compensated state: tensor-core ETD2RKds plans only");
   int64_t N = 1;
   for (int m = 0; m < p->d; ++m) {
     if (p->n[m] < 3 || p->n[m] > 4096) return fail(ADR_EINVAL, "n[mu] must be in [3, 4096]");
@@ -84,6 +90,14 @@ static Tridiag fd_coefficients(int64_t n, double lo, double hi, double delta, do
   t.b0 = 2.0 * delta / (h * h);
   t.bn = 2.0 * delta / (h * h);
   return t;
+}
+
+// How a (validated) problem carries its state: 0 = plain FP32, 1 = hi + lo
+// FP32 words within each call, 2 = hi + lo carried across calls.
+static int compensated(const adr_problem* p) {
+  const bool tc = p->precision == ADR_BF16X3 || p->precision == ADR_TF32X3;
+  if (!tc || p->scheme != ADR_ETD2RKDS || p->state == ADR_STATE_PLAIN) return 0;
+  return p->state == ADR_STATE_COMPENSATED ? 2 : 1;
 }
 
 static bool same_operator(const Tridiag& a, const Tridiag& b) {
@@ -231,11 +245,13 @@ static void plan_free(adr_plan P) {
   if (!P) return;
   if (P->stream) cudaStreamSynchronize(P->stream);
   for (void* q : P->allocs) cudaFree(q);
+  // the operand pieces first: they are keyed by the FP64 matrices' addresses
+  tc_free(&P->tc);
+  for (void* q : P->shared) shared_release(q);
   for (cudaEvent_t e : P->event_pool) cudaEventDestroy(e);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->gexec_timed) cudaGraphExecDestroy(P->gexec_timed);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
-  tc_free(&P->tc);
   delete P;
 }
 
@@ -282,6 +298,7 @@ extern "C" adr_status adr_plan_create_tuned(const adr_problem* problem, const ad
   P->g_launches = 0;
   P->tc_variant = tuning ? tuning->kernel : -1;
   P->cap_stream = nullptr;
+  P->shared_hits = 0;
   P->use_graphs = 1;
   if (const char* ev = getenv("ADR_GRAPHS")) P->use_graphs = atoi(ev) != 0;
   tc_init(&P->tc);
@@ -328,10 +345,24 @@ extern "C" adr_status adr_plan_create_tuned(const adr_problem* problem, const ad
         }
       if (found) continue;
       const size_t nn = (size_t)n * n;
-      for (int w = 0; w < 4; ++w) PLAN_TRY(plan_alloc(P, (void**)&P->master[c][m][w], nn * 8));
-      PLAN_TRY(launch_build_dense((int)n, pw.A[c][m], 1.0, P->master[c][m][0], P->stream));
-      PLAN_TRY(matfun_phi((int)n, pw.A[c][m], problem->tau, P->master[c][m][1],
-                          P->master[c][m][2], P->master[c][m][3], P->stream));
+      // A, e^(tau A), phi_1, phi_2 of this operator and step: from the
+      // process-wide cache, computed here on a miss
+      const Tridiag& op = pw.A[c][m];
+      const std::vector<uint64_t> key = {0, (uint64_t)n, key_bits(op.lo), key_bits(op.di),
+                                         key_bits(op.up), key_bits(op.b0), key_bits(op.bn),
+                                         key_bits(problem->tau)};
+      void* mats[4] = {};
+      bool hit = false;
+      PLAN_TRY(shared_acquire(key, 4, nn * 8, [&](void* const* b) {
+        cudaError_t r = launch_build_dense((int)n, op, 1.0, (double*)b[0], P->stream);
+        if (r == cudaSuccess)
+          r = matfun_phi((int)n, op, problem->tau, (double*)b[1], (double*)b[2], (double*)b[3],
+                         P->stream);
+        return r;
+      }, P->stream, mats, &hit));
+      P->shared.push_back(mats[0]);
+      P->shared_hits += hit ? 1 : 0;
+      for (int w = 0; w < 4; ++w) P->master[c][m][w] = (double*)mats[w];
       // SIMT operands (FP32/FP64 plans): e^(tau A), phi_1, phi_2 and transposes
       for (int l = 0; l < 3 && P->prec <= ADR_FP32; ++l) {
         PLAN_TRY(plan_alloc(P, &P->op[c][m][l], nn * P->esize));
@@ -351,7 +382,8 @@ extern "C" adr_status adr_plan_create_tuned(const adr_problem* problem, const ad
     PLAN_TRY(plan_alloc(P, &P->bufB[c], sb));
   }
   if (P->prec == ADR_TF32X3 || P->prec == ADR_BF16X3) {
-    e = tc_prepare(&P->tc, P->prec, P->scheme, P->d, P->n, P->master, P->stream, P->tc_variant);
+    e = tc_prepare(&P->tc, P->prec, P->scheme, P->d, P->n, P->master, P->stream, P->tc_variant,
+                   compensated(problem));
     if (e != cudaSuccess) {
       const bool unsup = (e == cudaErrorNotSupported);
       set_error(std::string("adr_plan_create: tensor-core operands: ") + cudaGetErrorString(e));
@@ -497,13 +529,112 @@ static adr_status step_impl(adr_plan P, void* u, void* v, int64_t nsteps) {
   return ADR_OK;
 }
 
-extern "C" adr_status adr_step(adr_plan plan, void* u, void* v, int64_t nsteps) {
+adr_status plan_step_continue(adr_plan plan, void* u, void* v, int64_t nsteps) {
   if (!plan) return fail(ADR_EINVAL, "plan is NULL");
   if (!u || !v || u == v) return fail(ADR_EINVAL, "u, v must be distinct non-NULL device pointers");
   if (nsteps < 0) return fail(ADR_EINVAL, "nsteps < 0");
   if (!is_device_ptr(u) || !is_device_ptr(v))
     return fail(ADR_EINVAL, "adr_step needs device pointers");
   return step_impl(plan, u, v, nsteps);
+}
+
+extern "C" adr_status adr_step(adr_plan plan, void* u, void* v, int64_t nsteps) {
+  if (plan && u && v && u != v && nsteps > 0) {  // the start of a call (compensated state)
+    cudaError_t e = tc_begin_call(&plan->tc, u, v, plan->stream);
+    if (e != cudaSuccess) return fail(ADR_ECUDA, std::string("adr_step: ") + cudaGetErrorString(e));
+  }
+  return plan_step_continue(plan, u, v, nsteps);
+}
+
+extern "C" adr_status adr_plan_time_mode_products(adr_plan plan, void* u, void* v, int32_t reps,
+                                                  double* ms_per_launch, int32_t* launches_per_step) {
+  if (!plan || !u || !v || u == v || !ms_per_launch || !launches_per_step)
+    return fail(ADR_EINVAL, "adr_plan_time_mode_products: bad argument");
+  if (reps < 1 || reps > 4096) return fail(ADR_EINVAL, "adr_plan_time_mode_products: reps in [1, 4096]");
+  if (plan->prec != ADR_BF16X3 && plan->prec != ADR_TF32X3)
+    return fail(ADR_EUNSUPPORTED, "adr_plan_time_mode_products: tensor-core plans only");
+  if (!is_device_ptr(u) || !is_device_ptr(v) || ((((uintptr_t)u) | ((uintptr_t)v)) & 15))
+    return fail(ADR_EINVAL, "adr_plan_time_mode_products: 16-byte aligned device buffers needed");
+  float ms = 0.f;
+  int passes = 0;
+  cudaError_t e = tc_time_passes(&plan->tc, plan, u, v, reps, &ms, &passes);
+  if (e != cudaSuccess)
+    return fail(ADR_ECUDA, std::string("adr_plan_time_mode_products: ") + cudaGetErrorString(e));
+  *ms_per_launch = ms;
+  *launches_per_step = passes;
+  return ADR_OK;
+}
+
+static bool tc_etd2rkds(adr_plan P) {
+  return (P->prec == ADR_BF16X3 || P->prec == ADR_TF32X3) && P->scheme == ADR_ETD2RKDS;
+}
+
+static void drop_graphs(adr_plan P) {
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->gexec_timed) cudaGraphExecDestroy(P->gexec_timed);
+  P->gexec = P->gexec_timed = nullptr;
+  P->g_u = P->g_v = P->gt_u = P->gt_v = nullptr;
+}
+
+extern "C" adr_status adr_plan_set_indicators(adr_plan plan, int enable) {
+  if (!plan) return fail(ADR_EINVAL, "plan is NULL");
+  if (!tc_etd2rkds(plan))
+    return fail(ADR_EUNSUPPORTED, "fused indicators: tensor-core ETD2RKds plans only");
+  if (__atomic_load_n(&plan->batch_refs, __ATOMIC_ACQUIRE) > 0)
+    return fail(ADR_EBUSY, "adr_plan_set_indicators: a live batch uses this plan");
+  ADR_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+  drop_graphs(plan);  // the captured launches carry the old descriptors
+  ADR_CUDA_TRY(tc_set_indicators(&plan->tc, enable != 0, plan->stream));
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_plan_indicator_log(adr_plan plan, double* out, int64_t max_steps,
+                                             int64_t* count) {
+  if (!plan || !out || !count || max_steps < 0) return fail(ADR_EINVAL, "bad argument");
+  if (!tc_etd2rkds(plan)) return fail(ADR_EUNSUPPORTED, "fused indicators: tensor-core ETD2RKds plans only");
+  cudaError_t e = tc_indicator_log(&plan->tc, plan->stream, out, max_steps, count);
+  if (e == cudaErrorNotSupported) return fail(ADR_EINVAL, "indicators are off (adr_plan_set_indicators)");
+  if (e != cudaSuccess) return fail(ADR_ECUDA, std::string("adr_plan_indicator_log: ") + cudaGetErrorString(e));
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_run(adr_plan plan, void* u, void* v, double t_end, double tol,
+                              int64_t check_every, int64_t* steps_done, double ind_last[4]) {
+  if (!plan || !u || !v || u == v || !steps_done || !ind_last || check_every < 1 ||
+      !(t_end >= 0.0) || !isfinite(t_end) || !(tol >= 0.0))
+    return fail(ADR_EINVAL, "adr_run: bad argument");
+  if (!tc_etd2rkds(plan)) return fail(ADR_EUNSUPPORTED, "adr_run: tensor-core ETD2RKds plans only");
+  *steps_done = 0;
+  const double tau = plan->prob.tau;
+  const int64_t total = (int64_t)ceil(t_end / tau - 1e-9);  // steps to reach t_end
+  if (total > 0) {
+    cudaError_t e = tc_begin_call(&plan->tc, u, v, plan->stream);
+    if (e != cudaSuccess) return fail(ADR_ECUDA, std::string("adr_run: ") + cudaGetErrorString(e));
+  }
+  for (int m = 0; m < 4; ++m) ind_last[m] = 0.0;
+  while (*steps_done < total) {
+    const int64_t n = std::min<int64_t>(check_every, total - *steps_done);
+    adr_status st = plan_step_continue(plan, u, v, n);
+    if (st != ADR_OK) return st;
+    *steps_done += n;
+    int64_t got = 0;
+    cudaError_t e = tc_indicator_log(&plan->tc, plan->stream, ind_last, 1, &got);
+    if (e == cudaErrorNotSupported) return fail(ADR_EINVAL, "adr_run: indicators are off (adr_plan_set_indicators)");
+    if (e != cudaSuccess) return fail(ADR_ECUDA, std::string("adr_run: ") + cudaGetErrorString(e));
+    if (int* ew = tc_error_word(&plan->tc)) {
+      int h = 0;
+      ADR_CUDA_TRY(cudaMemcpy(&h, ew, sizeof(int), cudaMemcpyDeviceToHost));
+      if (h != 0) return fail(ADR_ETIMEOUT, "adr_run: a kernel gave up a bounded wait");
+    }
+    if (tol > 0.0 && std::max(ind_last[2], ind_last[3]) <= tol) break;
+  }
+  return ADR_OK;
+}
+
+extern "C" adr_status adr_plan_reset_state(adr_plan plan) {
+  if (!plan) return fail(ADR_EINVAL, "plan is NULL");
+  ADR_CUDA_TRY(tc_reset_state(&plan->tc, plan->stream));
+  return ADR_OK;
 }
 
 extern "C" adr_status adr_solve(adr_plan plan, const void* u0, const void* v0, void* uT, void* vT,
@@ -530,6 +661,8 @@ extern "C" adr_status adr_solve(adr_plan plan, const void* u0, const void* v0, v
     wu = P->dstate[0];
     wv = P->dstate[1];
   }
+  // a solve starts from (u0, v0) alone
+  ADR_CUDA_TRY(tc_reset_state(&P->tc, P->stream));
   const cudaMemcpyKind kin = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (wu != u0) ADR_CUDA_TRY(cudaMemcpyAsync(wu, u0, sb, kin, P->stream));
   if (wv != v0) ADR_CUDA_TRY(cudaMemcpyAsync(wv, v0, sb, kin, P->stream));
@@ -563,7 +696,7 @@ extern "C" adr_status adr_plan_bytes(const adr_problem* problem, size_t* state_b
     if (problem->precision >= ADR_TF32X3) mats += 2 * 2 * 3 * 4 * nn;
   }
   if (state_bytes) *state_bytes = 2 * N * es;
-  if (cache_bytes) *cache_bytes = mats + 6 * N * es;
+  if (cache_bytes) *cache_bytes = mats + 6 * N * es + (compensated(problem) ? 2 * N * 4 : 0);
   return ADR_OK;
 }
 
@@ -607,6 +740,7 @@ extern "C" adr_status adr_plan_stats(adr_plan plan, adr_stats* out) {
   out->steps = plan->steps;
   out->timing = plan->timing ? 1 : 0;
   out->nkernels = KC_COUNT;
+  out->shared_matrices = plan->shared_hits;
   ADR_CUDA_TRY(cudaStreamSynchronize(plan->stream));
   if (int* ew = tc_error_word(&plan->tc)) {
     int h = 0;
@@ -697,7 +831,8 @@ extern "C" adr_status adr_plan_set_kernel(adr_plan P, int32_t kernel) {
   tc_free(&P->tc);
   tc_init(&P->tc);
   P->tc_variant = kernel;
-  cudaError_t e = tc_prepare(&P->tc, P->prec, P->scheme, P->d, P->n, P->master, P->stream, kernel);
+  cudaError_t e = tc_prepare(&P->tc, P->prec, P->scheme, P->d, P->n, P->master, P->stream, kernel,
+                             compensated(&P->prob));
   if (e != cudaSuccess)
     return fail(e == cudaErrorNotSupported ? ADR_EUNSUPPORTED : ADR_ECUDA,
                 std::string("adr_plan_set_kernel: ") + cudaGetErrorString(e));

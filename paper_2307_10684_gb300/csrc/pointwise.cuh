@@ -51,6 +51,67 @@ __device__ __forceinline__ void react(const ReactionT<T>& rx, T u, T v, T& gu, T
 // One direction of the tridiagonal action at one point, in difference form
 // (the rows sum to zero): interior lo (x_{i-1} - x_i) + up (x_{i+1} - x_i),
 // Neumann rows b0 (x_1 - x_0) and bn (x_{n-2} - x_{n-1}).
+// Double-float numbers: a value is h + l with two FP32 words (about 48
+// significant bits).  Sums use Knuth's TwoSum and products the exact FMA
+// residual (Dekker's TwoProduct with a fused multiply-add), so a reaction
+// polynomial whose terms cancel (the Brusselator's a - (b + 1) u + u^2 v
+// at u, v of a few units, say) keeps the digits an FP32 evaluation loses.
+// The _rn intrinsics keep the compiler from contracting or reordering the
+// error terms.
+struct dfloat {
+  float h, l;
+  __device__ __forceinline__ dfloat() : h(0.f), l(0.f) {}
+  __device__ __forceinline__ dfloat(float x) : h(x), l(0.f) {}
+  __device__ __forceinline__ dfloat(float x, float y) : h(x), l(y) {}
+};
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return dfloat(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+  const dfloat s = df_two_sum(a.h, b.h);
+  return df_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.h, -a.l); }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+  const float p = __fmul_rn(a.h, b.h);
+  const float e = __fmaf_rn(a.h, b.h, -p);  // exact: a.h b.h = p + e
+  return df_two_sum(p, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e)));
+}
+
+// The reaction of Eq. 1 evaluated in double-float from single-precision
+// state values, rounded once to FP32 (parameters as p + plo).
+__device__ __forceinline__ void react_df(const ReactionT<float>& rx, float u, float v, float& gu,
+                                         float& gv) {
+  ReactionT<dfloat> r;
+  r.model = rx.model;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) r.p[i] = dfloat(rx.p[i], rx.plo[i]);
+  dfloat a, b;
+  react<dfloat>(r, dfloat(u), dfloat(v), a, b);
+  gu = __fadd_rn(a.h, a.l);
+  gv = __fadd_rn(b.h, b.l);
+}
+
+// D = G(u2, v2) - G(u0, v0) (the stage-2 reaction difference of Eq. 11),
+// both reactions and the difference in double-float, rounded once.
+__device__ __forceinline__ void react_diff_df(const ReactionT<float>& rx, float u0, float v0,
+                                              float u2, float v2, float& du, float& dv) {
+  ReactionT<dfloat> r;
+  r.model = rx.model;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) r.p[i] = dfloat(rx.p[i], rx.plo[i]);
+  dfloat a0, b0, a2, b2;
+  react<dfloat>(r, dfloat(u0), dfloat(v0), a0, b0);
+  react<dfloat>(r, dfloat(u2), dfloat(v2), a2, b2);
+  const dfloat x = a2 - a0, y = b2 - b0;
+  du = __fadd_rn(x.h, x.l);
+  dv = __fadd_rn(y.h, y.l);
+}
+
 template <typename T>
 __device__ __forceinline__ T stencil_dir(const T* __restrict__ x, int64_t idx, int64_t stride,
                                          int i, int n, const TridiagT<T>& A) {

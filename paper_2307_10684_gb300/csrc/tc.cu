@@ -25,12 +25,14 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 
+#include <map>
 #include <mutex>
 
 #include "adr_internal.h"
@@ -334,6 +336,12 @@ struct alignas(128) TcPassDesc {
   __nv_bfloat16* outp[2];   // [3][N][M] per component (kPieces3, kStage1)
   float* outf[2];           // FP32 output per component (kStage1, kAxpy)
   const float* base[2];     // FP32 base per component (kStage1, kAxpy)
+  float* lo[2];             // kAxpy of a compensated state: low-order words, read and
+                            // rewritten in place (null: plain FP32 update)
+  double* ind;              // last product of a step: indicator ring [ind_k][4] (null: off)
+  const int64_t* ind_ctr;   // the step's slot: *ind_ctr % ind_k
+  int ind_k;
+  int ind_n1, ind_n2;       // n_1 and (3D) n_2, for the trapezoid weights of row m
   int M, N, K;
   int tiles_m, tiles_n;
   int pair;                 // 1: unit = (u, v) tile pair; 0: unit = one tile of one component
@@ -363,6 +371,98 @@ __device__ __forceinline__ void pdl_trigger() {
 }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Stage update of a compensated state.  The state is b + lo_in (two FP32
+// words); (hi, lo) receives b + lo_in + inc with hi the FP32 value nearest
+// the sum and |lo| <= ulp(hi) / 2.  Knuth's TwoSum gives the exact rounding
+// error of b + inc; a second TwoSum renormalises after the low-order words
+// are added.  The _rn intrinsics keep the compiler from contracting or
+// reordering the error terms.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void comp_update(float b, float lo_in, float inc, float& hi, float& lo) {
+  float s, e;
+  two_sum(b, inc, s, e);
+  two_sum(s, __fadd_rn(lo_in, e), hi, lo);
+}
+
+__device__ __forceinline__ double trap_w(int i, int n) { return (i == 0 || i == n - 1) ? 0.5 : 1.0; }
+
+// Epilogue of a kAxpy pass with its options, for one epilogue warp: lane =
+// output row m, NCH chunks of 16 columns from n0; out = base + alpha acc.
+//  lp  : compensated state; the low-order words are read and rewritten in
+//        place and hi + lo takes the exact sum (comp_update).
+//  ind : the step's indicator slot of this component: adds the
+//        trapezoid-weighted sum of the new state and the squared increment
+//        against the value the output buffer held (the previous state), in
+//        FP64, one atomic per warp and sum.
+// Per chunk the base, low-order and previous values are loaded before the
+// TMEM read, so their latency overlaps it.
+template <int NCH>
+__device__ __forceinline__ void axpy_epilogue(uint32_t ta, float* __restrict__ of,
+                                              const float* __restrict__ bsrc, float* lp,
+                                              float alpha, int M, int N, int n0, int m, bool mrow,
+                                              double* ind, int n1, int n2) {
+  double wm = 0.0;  // trapezoid weight of row m (the directions before the last)
+  if (ind && mrow) wm = n2 > 0 ? trap_w(m % n1, n1) * trap_w(m / n1, n2) : trap_w(m, n1);
+  double sw = 0.0, sd = 0.0;
+#pragma unroll 1
+  for (int bt = 0; bt < NCH; ++bt) {
+    float bb[16], lv[16], pv[16];
+    uint32_t r[16];
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      const int col = n0 + bt * 16 + jj;
+      const bool ok = mrow && col < N;
+      const int64_t o = (int64_t)col * M + m;
+      bb[jj] = ok ? __ldg(bsrc + o) : 0.f;
+      lv[jj] = (ok && lp) ? __ldcg(lp + o) : 0.f;
+      pv[jj] = (ok && ind) ? __ldcg(of + o) : 0.f;
+    }
+    tmem_ld16_nw(ta + (uint32_t)(bt * 16), r);
+    tmem_wait_ld();
+    tmem_fence16(r);
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      const int col = n0 + bt * 16 + jj;
+      if (mrow && col < N) {
+        const int64_t o = (int64_t)col * M + m;
+        const float a = __uint_as_float(r[jj]);
+        float hi;
+        if (lp) {
+          float lo;
+          comp_update(bb[jj], lv[jj], __fmul_rn(alpha, a), hi, lo);
+          lp[o] = lo;
+        } else {
+          hi = __fmaf_rn(alpha, a, bb[jj]);
+        }
+        of[o] = hi;
+        if (ind) {
+          sw += wm * trap_w(col, N) * (double)hi;
+          const double dd = (double)hi - (double)pv[jj];
+          sd += dd * dd;
+        }
+      }
+    }
+  }
+  if (ind) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sw += __shfl_xor_sync(0xffffffffu, sw, off);
+      sd += __shfl_xor_sync(0xffffffffu, sd, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(ind, sw);
+      atomicAdd(ind + 2, sd);
+    }
+  }
+}
+
+// The indicator slot of component c for the unit's step (null when off).
+__device__ __forceinline__ double* indicator_slot(const struct TcPassDesc* D, int c);
+
 // Epilogue of one mode-product pass.
 enum TcMode : int {
   kPieces3 = 0,   // out pieces [3][N][M] of acc
@@ -372,6 +472,12 @@ enum TcMode : int {
   kStage1X = 3    // as kStage1 with one component per CTA: the two CTAs of a
                   // cluster hold u and v of the same tile and exchange U2, V2
 };
+
+__device__ __forceinline__ double* indicator_slot(const TcPassDesc* D, int c) {
+  if (D->ind == nullptr) return nullptr;
+  const int64_t s = __ldcg(D->ind_ctr);
+  return D->ind + 4 * (s % D->ind_k) + c;
+}
 
 // The six piece pairs (i, j), A piece i times B piece j, grouped by A piece
 // so that each A piece is read from shared memory once per K step (A
@@ -669,7 +775,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
           for (int jj = 0; jj < 32; ++jj) {
             const int col = n0 + bt * 16 + jj;
             if (mrow && col < N)
-              of[(int64_t)col * M + m] = bv[bt * 16 + jj] + alpha * __uint_as_float(r[jj / 16][jj % 16]);
+              of[(int64_t)col * M + m] = __fmaf_rn(alpha, __uint_as_float(r[jj / 16][jj % 16]), bv[bt * 16 + jj]);
           }
         }
         tc_fence_before();
@@ -734,10 +840,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
         // wait, then write.
         float bv[HC];
         const float* bsrc = D->base[w.c_lo];
+        float* lp = mode == kAxpy ? D->lo[w.c_lo] : nullptr;  // compensated state update
+        double* ind = mode == kAxpy ? indicator_slot(D, w.c_lo) : nullptr;
 #pragma unroll
         for (int j = 0; j < HC; ++j) {
           const int col = n0 + j;
-          bv[j] = (fp32_in && bsrc && mrow && col < N) ? __ldg(bsrc + (int64_t)col * M + m) : 0.f;
+          bv[j] = (fp32_in && !lp && !ind && bsrc && mrow && col < N)
+                      ? __ldg(bsrc + (int64_t)col * M + m) : 0.f;
         }
         if (!mbar_wait_sleep(&acc_full[slot], (i >> 1) & 1)) {
           if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
@@ -748,6 +857,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
         if (*abort_v) break;
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * 2 * BN + half * HC);
         // TMEM columns in batches of two 16-column chunks, one wait per batch
+        if (lp || ind) {
+          axpy_epilogue<NCH>(ta, D->outf[w.c_lo], bsrc, lp, alpha, M, N, n0, m, mrow, ind,
+                             D->ind_n1, D->ind_n2);
+        } else {
 #pragma unroll
         for (int bt = 0; bt < NCH; bt += 2) {
           constexpr int NB = NCH >= 2 ? 2 : 1;
@@ -791,10 +904,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
               for (int jj = 0; jj < 16 * NB; ++jj) {
                 const int col = n0 + bt * 16 + jj;
                 if (col < N)
-                  of[(int64_t)col * M + m] = bv[bt * 16 + jj] + alpha * __uint_as_float(r[jj / 16][jj % 16]);
+                  of[(int64_t)col * M + m] = __fmaf_rn(alpha, __uint_as_float(r[jj / 16][jj % 16]), bv[bt * 16 + jj]);
               }
             }
           }
+        }
         }
         tc_fence_before();
         __syncwarp();
@@ -882,7 +996,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                   if (j >= jm) break;
-                  of[o0 + (int64_t)j * M] = bsv[j] + alpha * a[j];
+                  of[o0 + (int64_t)j * M] = __fmaf_rn(alpha, a[j], bsv[j]);
                 }
               }
             };
@@ -1195,10 +1309,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
       const int64_t plane = (int64_t)N * M;
       float bv[HC];
       const float* bsrc = D->base[w.c];
+      float* lp = mode == kAxpy ? D->lo[w.c] : nullptr;  // compensated state update
+      double* ind = mode == kAxpy ? indicator_slot(D, w.c) : nullptr;
 #pragma unroll
       for (int j = 0; j < HC; ++j) {
         const int col = n0 + j;
-        bv[j] = (fp32_in && bsrc && mrow && col < N) ? __ldg(bsrc + (int64_t)col * M + m) : 0.f;
+        bv[j] = (fp32_in && !lp && !ind && bsrc && mrow && col < N)
+                    ? __ldg(bsrc + (int64_t)col * M + m) : 0.f;
       }
       if (!mbar_wait_sleep(&acc_full[slot], (i >> 1) & 1)) {
         if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
@@ -1208,6 +1325,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
       tc_fence_after();
       if (*abort_v) break;
       const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * BN + half * HC);
+      if (lp || ind) {
+        axpy_epilogue<NCH>(ta, D->outf[w.c], bsrc, lp, alpha, M, N, n0, m, mrow, ind, D->ind_n1,
+                           D->ind_n2);
+      } else {
 #pragma unroll
       for (int bt = 0; bt < NCH; bt += 2) {
         uint32_t r[2][16];
@@ -1237,10 +1358,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
             for (int jj = 0; jj < 32; ++jj) {
               const int col = n0 + bt * 16 + jj;
               if (col < N)
-                of[(int64_t)col * M + m] = bv[bt * 16 + jj] + alpha * __uint_as_float(r[jj / 16][jj % 16]);
+                of[(int64_t)col * M + m] = __fmaf_rn(alpha, __uint_as_float(r[jj / 16][jj % 16]), bv[bt * 16 + jj]);
             }
           }
         }
+      }
       }
       tc_fence_before();
       __syncwarp();
@@ -1274,6 +1396,9 @@ struct PwDesc {
   const float* v2;
   __nv_bfloat16* wu;   // pieces [3][N] of the u output
   __nv_bfloat16* wv;
+  double* ind;         // indicator ring [ind_k][4] and step counter (null: off)
+  int64_t* ind_ctr;
+  int ind_k;
   float tau;
   int nx, ny, nz;      // stencil axes (ny = 1 in 2D)
   int xsegs, zlen, zsegs;  // 2D: warp x segments; 3D: block x tiles.  z runs
@@ -1322,6 +1447,18 @@ __device__ __forceinline__ const PwDesc* block_desc(const PwLaunch& L, PwDesc* s
   __syncthreads();
   pdl_wait();
   return sd;
+}
+
+// Indicators of Sec. 4: the first kernel of a step opens the step's slot in
+// the solve's indicator ring (the counter and slot are written by one thread
+// after the previous step has completed; the last product of the step, which
+// runs after this kernel has completed, accumulates into it).
+__device__ __forceinline__ void indicator_open_step(const PwDesc* dp, int lb) {
+  if (lb != 0 || threadIdx.x != 0 || dp->ind == nullptr) return;
+  const int64_t s = *dp->ind_ctr + 1;
+  *dp->ind_ctr = s;
+  double* slot = dp->ind + 4 * (s % dp->ind_k);
+  slot[0] = slot[1] = slot[2] = slot[3] = 0.0;
 }
 
 // One direction of the stencil of Eq. 6 at an interior point, and at any
@@ -1409,6 +1546,7 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_
   __shared__ PwDesc sd;
   int lb;
   const PwDesc* dp = block_desc(L, &sd, lb);
+  indicator_open_step(dp, lb);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = dp->nx, nz = dp->nz, xsegs = dp->xsegs;
   int64_t unit = (int64_t)lb * kPwWarps + warp;
@@ -1480,7 +1618,7 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_
         ku += tri_dir(el(pu[q], j), cu, el(pu[q + 2], j), zq, nz, czu.lo, czu.up, czu.b0, czu.bn);
         kv += tri_dir(el(pv[q], j), cv, el(pv[q + 2], j), zq, nz, czv.lo, czv.up, czv.b0, czv.bn);
         float gu, gv;
-        react<float>(rx, cu, cv, gu, gv);
+        react_df(rx, cu, cv, gu, gv);
         ou[j] = ku + gu;
         ov[j] = kv + gv;
       }
@@ -1525,6 +1663,7 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs3_ring_kernel(const __grid_c
   int lb;
   const PwDesc* src = nullptr;
   const PwDesc* dp = block_desc(L, &sd, lb, &src);
+  indicator_open_step(dp, lb);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = dp->nx, ny = dp->ny, nz = dp->nz;
   int b = lb;
@@ -1633,7 +1772,7 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs3_ring_kernel(const __grid_c
           kv += tri_dir(el(vzm, j), cv, el(vzp, j), z, nz, czv.lo, czv.up, czv.b0, czv.bn);
         }
         float gu, gv;
-        react<float>(rx, cu, cv, gu, gv);
+        react_df(rx, cu, cv, gu, gv);
         ou[j] = ku + gu;
         ov[j] = kv + gv;
       }
@@ -1685,11 +1824,7 @@ __global__ void __launch_bounds__(kPwThreads) rdiff_pieces_kernel(const __grid_c
     float du[4], dv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      float g0u, g0v, g2u, g2v;
-      react<float>(rx, el(a0[k], j), el(a1[k], j), g0u, g0v);
-      react<float>(rx, el(a2[k], j), el(a3[k], j), g2u, g2v);
-      du[j] = g2u - g0u;
-      dv[j] = g2v - g0v;
+      react_diff_df(rx, el(a0[k], j), el(a1[k], j), el(a2[k], j), el(a3[k], j), du[j], dv[j]);
     }
     store_pieces_fmt<F>(sd.wu, N, 4 * g, du);
     store_pieces_fmt<F>(sd.wv, N, 4 * g, dv);
@@ -2054,6 +2189,8 @@ struct TcOp {
 
 }  // namespace
 
+constexpr int kIndSlots = 4096;  // steps of indicator history a plan keeps
+
 // Host-side state of the tensor-core path of one plan (owned through TcOperands).
 struct TcState {
   int d;
@@ -2067,6 +2204,7 @@ struct TcState {
   int fmt;       // operand format: kFmtBF16 (three BF16 pieces) or kFmtTF32 (two TF32 pieces)
   int fuse;      // 1: fuse the stage-1 combination into the last stage-1 product
   int num_sms;
+  std::vector<void*> shared;  // operand pieces held in the process-wide cache
   int slots;     // resident CTAs (or CTA pairs) of the mode-product kernel
   int xslots;    // resident clusters of the exchanging (kStage1X) kernel
   int* err;
@@ -2083,6 +2221,17 @@ struct TcState {
   int rhs_blocks, rdiff_blocks;
   void* bound_u;
   void* bound_v;
+  // compensated state: low-order words per component [N], valid for the
+  // state pair (comp_u, comp_v); null when the plan carries a plain state.
+  // comp: 0 plain, 1 restarted at every call, 2 carried across calls
+  int comp;
+  float* lo[2];
+  void* comp_u;
+  void* comp_v;
+  // indicators of Sec. 4 per step (null when off): ring [kIndSlots][4] of
+  // sums (w u, w v, |dU|^2, |dV|^2) and the step counter
+  double* ind;
+  int64_t* ind_ctr;
 };
 
 static int units_of(const TcState* S, const TcPass& ps, int bn) {
@@ -2116,6 +2265,19 @@ static TcPassDesc make_desc(const TcState* S, const adr_plan_s* P, const TcPass&
     D.outp[c] = S->buf[1 - ps.b][c];
     D.outf[c] = ps.out == kOutStage ? stage[c] : (ps.out == kOutState ? state[c] : nullptr);
     D.base[c] = ps.base == kBaseStage ? stage[c] : (ps.base == kBaseState ? state[c] : nullptr);
+    // the stage updates U2 = U + tau T and U+ = U2 + 2^(d-1) tau S of a
+    // compensated state carry the low-order words (stage 1 leaves U2's in
+    // place of U's, stage 2 replaces them by U+'s)
+    D.lo[c] = (S->comp && ps.mode == kAxpy && !ps.pair) ? S->lo[c] : nullptr;
+  }
+  // the last product of an ETD2RKds step writes the new state: it adds the
+  // step's indicator sums
+  if (S->ind && S->scheme == ADR_ETD2RKDS && ps.mode == kAxpy && ps.out == kOutState && !ps.pair) {
+    D.ind = S->ind;
+    D.ind_ctr = S->ind_ctr;
+    D.ind_k = kIndSlots;
+    D.ind_n1 = (int)S->n[0];
+    D.ind_n2 = S->d == 3 ? (int)S->n[1] : 0;
   }
   D.alpha = ps.alpha == kAlphaTau ? (float)tau
                                   : (ps.alpha == kAlphaTauD ? (float)ldexp(tau, S->d - 1) : 1.0f);
@@ -2200,6 +2362,9 @@ static cudaError_t make_pw(const TcState* S, const adr_plan_s* P, float* u, floa
   W.wu = S->buf[0][0];
   W.wv = S->buf[0][1];
   W.tau = (float)P->prob.tau;
+  W.ind = S->ind;
+  W.ind_ctr = S->ind_ctr;
+  W.ind_k = kIndSlots;
   const PwGeom g = pw_geom(S, S->num_sms, share);
   W.nx = g.nx;
   W.ny = g.ny;
@@ -2234,13 +2399,14 @@ void tc_free(TcOperands* t) {
   TcState* S = (TcState*)t->work[0];
   if (S) {
     for (void* p : S->allocs) cudaFree(p);
+    for (void* p : S->shared) shared_release(p);
     delete S;
   }
   t->work[0] = nullptr;
 }
 
 cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t n[3],
-                       double* const master[2][3][4], cudaStream_t s, int variant_req) {
+                       double* const master[2][3][4], cudaStream_t s, int variant_req, int comp) {
   if (prec != ADR_BF16X3 && prec != ADR_TF32X3) return cudaErrorNotSupported;
   for (int m = 0; m < d; ++m)
     if (n[m] % 8 != 0) return cudaErrorNotSupported;  // TMA row strides: 16-byte multiples
@@ -2296,6 +2462,8 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     S->fuse = f >= 0 && f <= 2 ? f : 0;
   }
   if (kVariants[S->variant].cta2) S->fuse = 0;  // the CTA-pair kernel has neither epilogue
+  S->comp = scheme == ADR_ETD2RKDS ? comp : 0;
+  if (S->comp) S->fuse = 0;  // the fused stage-1 epilogues keep a plain state
   if (S->fmt == kFmtTF32) {  // TF32 pieces: the one-CTA kernel, 128-byte swizzle, plain epilogues
     S->variant = 1;
     S->fuse = 0;
@@ -2336,19 +2504,38 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
         if ((scheme == ADR_LAWSON2B) != (l == 0)) continue;  // only the matrices the scheme uses
         const int64_t nn = n[m] * n[m];
         const size_t pb = S->fmt == kFmtTF32 ? 2 * 4 : (size_t)kPieces * 2;  // piece bytes per value
-        e = alloc((void**)&S->phi[c][m][l], pb * nn);
+        // the pieces of a cached FP64 matrix are cached with it (keyed by
+        // that matrix and the piece format)
+        const double* src = master[c][m][1 + l];
+        const std::vector<uint64_t> key = {1, (uint64_t)(uintptr_t)src, (uint64_t)S->fmt,
+                                           (uint64_t)nn};
+        void* buf = nullptr;
+        bool hit = false;
+        e = shared_acquire(key, 1, pb * nn, [&](void* const* b) {
+          if (S->fmt == kFmtTF32)
+            split_matrix_tf32_kernel<<<grid_for(nn), 256, 0, s>>>(src, (float*)b[0], nn);
+          else
+            split_matrix_kernel<<<grid_for(nn), 256, 0, s>>>(src, (__nv_bfloat16*)b[0], nn);
+          return cudaGetLastError();
+        }, s, &buf, &hit);
         if (e != cudaSuccess) return e;
-        if (S->fmt == kFmtTF32)
-          split_matrix_tf32_kernel<<<grid_for(nn), 256, 0, s>>>(master[c][m][1 + l],
-                                                                 (float*)S->phi[c][m][l], nn);
-        else
-          split_matrix_kernel<<<grid_for(nn), 256, 0, s>>>(master[c][m][1 + l], S->phi[c][m][l], nn);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        S->shared.push_back(buf);
+        S->phi[c][m][l] = (__nv_bfloat16*)buf;
         e = encode_pieces(&S->bmap[c][m][l], S->phi[c][m][l], n[m], n[m],
                           kVariants[S->variant].cta2 ? bn / 2 : bn, sw, S->fmt);
         if (e != cudaSuccess) return e;
       }
+  S->lo[0] = S->lo[1] = nullptr;
+  S->comp_u = S->comp_v = nullptr;
+  S->ind = nullptr;
+  S->ind_ctr = nullptr;
+  if (S->comp)
+    for (int c = 0; c < 2; ++c) {
+      e = alloc((void**)&S->lo[c], sizeof(float) * S->N);
+      if (e != cudaSuccess) return e;
+      e = cudaMemsetAsync(S->lo[c], 0, sizeof(float) * S->N, s);
+      if (e != cudaSuccess) return e;
+    }
   for (int b = 0; b < 2; ++b)
     for (int c = 0; c < 2; ++c) {
       e = alloc((void**)&S->buf[b][c], (S->fmt == kFmtTF32 ? 8 : (size_t)kPieces * 2) * S->N);
@@ -2419,6 +2606,37 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
 // Point this plan's descriptors at the state buffers (u, v).  The
 // descriptors are host copies passed by value in every launch, so binding
 // neither copies to the device nor synchronises.  A no-op when already bound.
+// Start of a stepping call on (u, v).  The low-order words of a
+// compensated state restart at zero (enqueued on s) at every call (comp 1),
+// or when the call steps another pair than the one they belong to (comp 2).
+static cudaError_t comp_own(TcState* S, void* u, void* v, cudaStream_t s) {
+  if (!S->comp || (S->comp == 2 && S->comp_u == u && S->comp_v == v)) return cudaSuccess;
+  for (int c = 0; c < 2; ++c) {
+    cudaError_t e = cudaMemsetAsync(S->lo[c], 0, sizeof(float) * S->N, s);
+    if (e != cudaSuccess) return e;
+  }
+  S->comp_u = u;
+  S->comp_v = v;
+  return cudaSuccess;
+}
+
+cudaError_t tc_reset_state(TcOperands* t, cudaStream_t s) {
+  TcState* S = (TcState*)t->work[0];
+  if (!S || !t->ready || !S->comp) return cudaSuccess;
+  S->comp_u = S->comp_v = nullptr;  // the words belong to no pair until the next call
+  for (int c = 0; c < 2; ++c) {
+    cudaError_t e = cudaMemsetAsync(S->lo[c], 0, sizeof(float) * S->N, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t tc_begin_call(TcOperands* t, void* u, void* v, cudaStream_t s) {
+  TcState* S = (TcState*)t->work[0];
+  if (!S || !t->ready) return cudaSuccess;
+  return comp_own(S, u, v, s);
+}
+
 cudaError_t tc_bind(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   TcState* S = (TcState*)t->work[0];
   if (!S || !t->ready) return cudaErrorNotSupported;
@@ -2540,7 +2758,7 @@ static void pass_work(const TcState* S, const TcPass& ps, double& flops, double&
   flops = 2.0 * 2.0 * nmu * N;
   bytes = 2.0 * (pb * N + pb * nmu * nmu);
   if (ps.mode == kPieces3) bytes += 2.0 * pb * N;
-  if (ps.mode == kAxpy) bytes += 2.0 * 8.0 * N;
+  if (ps.mode == kAxpy) bytes += 2.0 * (S->comp ? 16.0 : 8.0) * N;  // base, out (+ lo in, out)
   if (ps.mode == kStage1 || ps.mode == kStage1X) bytes += 2.0 * (8.0 + pb) * N;
 }
 
@@ -2581,6 +2799,124 @@ cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   G.err = S->err;
   G.pw_n = (double)S->N;
   return group_step(P, G);
+}
+
+// Duration of the tensor-core mode-product launches as they run inside a
+// step: the passes of `reps` steps are captured back to back in one graph
+// (programmatic dependent launch between consecutive passes, no event node
+// between them), the graph is replayed once to warm up and once between two
+// events.  *ms = the replay's time / (reps x passes per step).  (u, v) are
+// scratch state buffers (the AXPY passes write them).
+cudaError_t tc_time_passes(TcOperands* t, adr_plan_s* P, void* u, void* v, int reps, float* ms,
+                           int* passes) {
+  TcState* S = (TcState*)t->work[0];
+  if (!S || !t->ready) return cudaErrorNotSupported;
+  cudaError_t e = tc_bind(t, P, u, v);
+  if (e != cudaSuccess) return e;
+  GroupStep G;
+  memset(&G, 0, sizeof(G));
+  G.d = S->d;
+  G.variant = S->variant;
+  G.num_sms = S->slots;
+  G.nsolves = 1;
+  fill_ops(G, S);
+  int k = 0;  // keep only the mode-product launches
+  for (int o = 0; o < G.nops; ++o)
+    if (G.ops[o].kind == kOpTc) G.ops[k++] = G.ops[o];
+  G.nops = k;
+  *passes = k;
+  G.hdesc = S->h_desc.data();
+  for (int p = 0; p < G.np; ++p) {
+    G.units[p] = S->units[p];
+    pass_work(S, S->passes[p], G.flops[p], G.bytes[p]);
+  }
+  G.err = S->err;
+  G.pw_n = (double)S->N;
+  const bool timing = P->timing;
+  const int64_t l0 = P->launches;
+  cudaStream_t saved = P->stream;
+  P->timing = false;
+  P->stream = P->cap_stream;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = cudaSuccess;
+    for (int r = 0; r < reps && e1 == cudaSuccess; ++r) e1 = group_step(P, G);
+    cudaError_t e2 = cudaStreamEndCapture(P->cap_stream, &g);
+    e = e1 != cudaSuccess ? e1 : e2;
+  }
+  P->stream = saved;
+  P->timing = timing;
+  P->launches = l0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, P->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, P->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t_ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t_ms, e0, e1);
+  if (e == cudaSuccess) *ms = t_ms / (float)(reps * (k > 0 ? k : 1));
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ge) cudaGraphExecDestroy(ge);
+  return e;
+}
+
+cudaError_t tc_set_indicators(TcOperands* t, int enable, cudaStream_t s) {
+  TcState* S = (TcState*)t->work[0];
+  if (!S || !t->ready) return cudaErrorNotSupported;
+  if (enable && !S->ind) {
+    cudaError_t e = cudaMalloc((void**)&S->ind, sizeof(double) * 4 * kIndSlots);
+    if (e != cudaSuccess) return e;
+    S->allocs.push_back(S->ind);
+    e = cudaMalloc((void**)&S->ind_ctr, sizeof(int64_t));
+    if (e != cudaSuccess) return e;
+    S->allocs.push_back(S->ind_ctr);
+  }
+  if (enable) {  // counter -1: the first step opens slot 0
+    cudaError_t e = cudaMemsetAsync(S->ind_ctr, 0xff, sizeof(int64_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->ind, 0, sizeof(double) * 4 * kIndSlots, s);
+    if (e != cudaSuccess) return e;
+  } else {
+    S->ind = nullptr;  // the buffers stay allocated (freed with the plan)
+    S->ind_ctr = nullptr;
+  }
+  S->bound_u = S->bound_v = nullptr;  // descriptors are rebuilt at the next bind
+  return cudaSuccess;
+}
+
+cudaError_t tc_indicator_log(TcOperands* t, cudaStream_t s, double* out, int64_t max_steps,
+                             int64_t* count) {
+  TcState* S = (TcState*)t->work[0];
+  *count = 0;
+  if (!S || !S->ind) return cudaErrorNotSupported;
+  int64_t ctr = -1;
+  cudaError_t e = cudaMemcpyAsync(&ctr, S->ind_ctr, sizeof(ctr), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  const int64_t have = std::min<int64_t>(ctr + 1, kIndSlots);
+  const int64_t n = std::min<int64_t>(have, max_steps);
+  std::vector<double> ring(4 * kIndSlots);
+  e = cudaMemcpy(ring.data(), S->ind, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  double wsum = 1.0;
+  for (int m = 0; m < S->d; ++m) wsum *= (double)(S->n[m] - 1);
+  for (int64_t k = 0; k < n; ++k) {  // the last n steps, oldest first
+    const int64_t step = ctr - (n - 1) + k;
+    const double* q = ring.data() + 4 * (step % kIndSlots);
+    out[4 * k + 0] = q[0] / wsum;
+    out[4 * k + 1] = q[1] / wsum;
+    out[4 * k + 2] = sqrt(q[2]);
+    out[4 * k + 3] = sqrt(q[3]);
+  }
+  *count = n;
+  return cudaSuccess;
 }
 
 int* tc_error_word(TcOperands* t) {
@@ -2627,6 +2963,10 @@ struct adr_batch_s {
   // parts, each a batch of mutually compatible plans (solve indices in idx)
   std::vector<adr_batch_s*> parts;
   std::vector<std::vector<int>> idx;
+  cudaStream_t stream;   // the stream given at creation
+  // batches over subsets of the solves, for the later phases of a call with
+  // uneven horizons (created on first use, kept until the batch is freed)
+  std::map<std::vector<int>, adr_batch_s*> subs;
 };
 
 static constexpr int64_t kBatchChunk = 16;
@@ -2737,6 +3077,7 @@ static cudaMemPool_t batch_pool() {
 static void batch_free(adr_batch B) {
   if (!B) return;
   for (adr_batch_s* q : B->parts) batch_free(q);
+  for (auto& kv : B->subs) batch_free(kv.second);
   cudaStream_t st = B->ctl ? B->ctl->stream : nullptr;
   if (B->gexec) cudaGraphExecDestroy(B->gexec);
   if (B->gexec_timed) cudaGraphExecDestroy(B->gexec_timed);
@@ -2815,6 +3156,7 @@ static adr_status batch_create_any(const adr_plan* plans, int count, void* strea
   B->plans.assign(plans, plans + count);
   B->nsolves = count;
   B->grouped = loose < 0 ? 1 : 0;
+  B->stream = (cudaStream_t)stream;
   for (const std::vector<int>& c : cls) {
     std::vector<adr_plan> sub;
     for (int i : c) sub.push_back(plans[i]);
@@ -2834,6 +3176,7 @@ static adr_status batch_create_any(const adr_plan* plans, int count, void* strea
 static adr_status batch_create_one(const adr_plan* plans, int count, void* stream, adr_batch* out) {
   adr_batch B = new adr_batch_s();
   B->plans.assign(plans, plans + count);
+  B->stream = (cudaStream_t)stream;
   B->ctl = new adr_plan_s();
   B->ctl->stream = (cudaStream_t)stream;
   B->ctl->prec = plans[0]->prec;
@@ -2991,12 +3334,9 @@ static cudaError_t batch_step_direct(adr_batch B, int64_t nsteps) {
   return cudaSuccess;
 }
 
-extern "C" adr_status adr_batch_step(adr_batch batch, void* const* u, void* const* v,
+// Every solve of B advances by the same nsteps (arguments checked).
+static adr_status batch_step_uniform(adr_batch batch, void* const* u, void* const* v,
                                      int64_t nsteps) {
-  if (!batch || !u || !v || nsteps < 0) {
-    set_error("adr_batch_step: bad argument");
-    return ADR_EINVAL;
-  }
   adr_batch B = batch;
   if (!B->parts.empty()) {  // one grouped launch sequence per part
     for (size_t k = 0; k < B->parts.size(); ++k) {
@@ -3005,24 +3345,14 @@ extern "C" adr_status adr_batch_step(adr_batch batch, void* const* u, void* cons
         pu.push_back(u[i]);
         pv.push_back(v[i]);
       }
-      adr_status st = adr_batch_step(B->parts[k], pu.data(), pv.data(), nsteps);
+      adr_status st = batch_step_uniform(B->parts[k], pu.data(), pv.data(), nsteps);
       if (st != ADR_OK) return st;
     }
     return ADR_OK;
   }
-  for (int i = 0; i < B->nsolves; ++i) {
-    if (!u[i] || !v[i] || u[i] == v[i]) {
-      set_error("adr_batch_step: state pointers must be distinct and non-NULL");
-      return ADR_EINVAL;
-    }
-    if (B->grouped && ((((uintptr_t)u[i]) | ((uintptr_t)v[i])) & 15)) {
-      set_error("adr_batch_step: BF16X3 state buffers must be 16-byte aligned");
-      return ADR_EINVAL;
-    }
-  }
   if (!B->grouped) {
     for (int i = 0; i < B->nsolves; ++i) {
-      adr_status st = adr_step(B->plans[i], u[i], v[i], nsteps);
+      adr_status st = plan_step_continue(B->plans[i], u[i], v[i], nsteps);
       if (st != ADR_OK) return st;
     }
     return ADR_OK;
@@ -3090,6 +3420,83 @@ extern "C" adr_status adr_batch_step(adr_batch batch, void* const* u, void* cons
   if (e != cudaSuccess) {
     set_error(std::string("adr_batch_step: ") + cudaGetErrorString(e));
     return ADR_ECUDA;
+  }
+  return ADR_OK;
+}
+
+// Batch over the solves idx of B (cached; created on first use).
+static adr_batch sub_batch(adr_batch B, const std::vector<int>& idx, adr_status* st) {
+  auto it = B->subs.find(idx);
+  if (it != B->subs.end()) return it->second;
+  std::vector<adr_plan> sp;
+  for (int i : idx) sp.push_back(B->plans[i]);
+  adr_batch sub = nullptr;
+  *st = batch_create_any(sp.data(), (int)sp.size(), B->stream, &sub);
+  if (*st != ADR_OK) return nullptr;
+  B->subs[idx] = sub;
+  return sub;
+}
+
+extern "C" adr_status adr_batch_step(adr_batch batch, void* const* u, void* const* v,
+                                     const int64_t* nsteps) {
+  if (!batch || !u || !v || !nsteps) {
+    set_error("adr_batch_step: bad argument");
+    return ADR_EINVAL;
+  }
+  adr_batch B = batch;
+  const int S_ = B->nsolves;
+  for (int i = 0; i < S_; ++i) {
+    if (nsteps[i] < 0) {
+      set_error("adr_batch_step: nsteps[i] < 0");
+      return ADR_EINVAL;
+    }
+    if (!u[i] || !v[i] || u[i] == v[i]) {
+      set_error("adr_batch_step: state pointers must be distinct and non-NULL");
+      return ADR_EINVAL;
+    }
+    const int prec = B->plans[i]->prec;
+    if ((prec == ADR_BF16X3 || prec == ADR_TF32X3) && ((((uintptr_t)u[i]) | ((uintptr_t)v[i])) & 15)) {
+      set_error("adr_batch_step: tensor-core state buffers must be 16-byte aligned");
+      return ADR_EINVAL;
+    }
+  }
+  // the start of a call for every solve that steps (compensated states)
+  for (int i = 0; i < S_; ++i) {
+    if (nsteps[i] == 0) continue;
+    cudaError_t e = tc_begin_call(&B->plans[i]->tc, u[i], v[i], B->stream);
+    if (e != cudaSuccess) {
+      set_error(std::string("adr_batch_step: ") + cudaGetErrorString(e));
+      return ADR_ECUDA;
+    }
+  }
+  // phases: between consecutive distinct horizons, the solves still running
+  // advance together; the first phase covers every solve that steps at all
+  std::vector<int64_t> hs;
+  for (int i = 0; i < S_; ++i)
+    if (nsteps[i] > 0) hs.push_back(nsteps[i]);
+  std::sort(hs.begin(), hs.end());
+  hs.erase(std::unique(hs.begin(), hs.end()), hs.end());
+  int64_t prev = 0;
+  for (int64_t h : hs) {
+    std::vector<int> idx;
+    for (int i = 0; i < S_; ++i)
+      if (nsteps[i] >= h) idx.push_back(i);
+    adr_status st = ADR_OK;
+    if ((int)idx.size() == S_) {
+      st = batch_step_uniform(B, u, v, h - prev);
+    } else {
+      adr_batch sub = sub_batch(B, idx, &st);
+      if (sub) {
+        std::vector<void*> su, sv;
+        for (int i : idx) {
+          su.push_back(u[i]);
+          sv.push_back(v[i]);
+        }
+        st = batch_step_uniform(sub, su.data(), sv.data(), h - prev);
+      }
+    }
+    if (st != ADR_OK) return st;
+    prev = h;
   }
   return ADR_OK;
 }

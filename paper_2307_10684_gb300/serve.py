@@ -8,9 +8,8 @@ The server:
   functions on the GPU) on a planner thread, so that stepping continues
   meanwhile;
 * keeps every admitted solve's state and matrices resident, and each tick
-  advances all active solves: those with at least ``chunk`` steps left
-  together, one grouped batch per dimension (``adr_batch_step``), the
-  others individually;
+  advances all active solves of a dimension in one grouped batch call
+  (``adr_batch_step``), each by ``chunk`` steps or what it has left;
 * retires finished solves without stalling the stepping loop: the results
   are copied to page-locked host memory asynchronously, and a request is
   complete when its copy event has fired (its latency is that moment minus
@@ -29,7 +28,20 @@ import threading
 import time
 from typing import Callable, Dict, List, Optional, Sequence, Tuple
 
-from . import Batch, Plan, plan_bytes, state_dtype
+from . import BF16X3, ETD2RKDS, STATE_AUTO, STATE_COMPENSATED, TF32X3, Batch, Plan, plan_bytes, \
+    state_dtype
+
+
+def served_problem(p):
+    """The problem as the server plans it.  A solve advances in ticks (one
+    call per tick), so a tensor-core ETD2RKds solve carries its compensated
+    state across calls (ADR_STATE_COMPENSATED): the server owns the state
+    buffers for the solve's whole life and writes nothing into them between
+    ticks, which is the condition that mode asks of its caller."""
+    if (getattr(p, "state", STATE_AUTO) == STATE_AUTO and int(p.precision) in (BF16X3, TF32X3)
+            and int(getattr(p, "scheme", ETD2RKDS)) == ETD2RKDS):
+        return dataclasses.replace(p, state=STATE_COMPENSATED)
+    return p
 
 
 @dataclasses.dataclass
@@ -104,7 +116,7 @@ class Server:
             req, nbytes = item
             try:
                 with torch.cuda.stream(pstream):
-                    plan = Plan(req.problem, stream=pstream)
+                    plan = Plan(served_problem(req.problem), stream=pstream)
                 dt = state_dtype(plan.precision)
                 u0, v0 = req.init()
                 hu = torch.as_tensor(u0, dtype=dt).pin_memory()
@@ -166,7 +178,7 @@ class Server:
             # arrivals join the waiting queue with their memory demand
             while arrivals and arrivals[0].arrival <= t:
                 r = arrivals.popleft()
-                sb, cb = plan_bytes(r.problem)
+                sb, cb = plan_bytes(served_problem(r.problem))
                 waiting.append((r, sb + cb))
             # admission by memory budget, in arrival order
             while waiting and len(self.active) + in_planning < self.max_active:
@@ -202,20 +214,18 @@ class Server:
                 else:
                     time.sleep(0.0005)
                 continue
-            # one tick: full chunks batched per dimension, short tails alone
+            # one tick: every active solve of a dimension in one batch call,
+            # each advancing min(chunk, its steps left); a solve whose horizon
+            # ends inside the tick drops out of the grouped work there
             groups: Dict[int, List[_Slot]] = collections.defaultdict(list)
             for s in self.active:
-                if s.left >= self.chunk:
-                    groups[s.req.problem.d].append(s)
-                else:
-                    s.plan.step(s.u, s.v, s.left)
-                    self.stats["tail_steps"] += s.left
-                    s.left = 0
+                groups[s.req.problem.d].append(s)
             for d, slots in groups.items():
+                steps = [min(self.chunk, s.left) for s in slots]
                 if len(slots) == 1:  # a group of one steps its plan (and its graph) directly
                     s = slots[0]
-                    s.plan.step(s.u, s.v, self.chunk)
-                    s.left -= self.chunk
+                    s.plan.step(s.u, s.v, steps[0])
+                    s.left -= steps[0]
                     self.stats["single_ticks"] += 1
                     continue
                 key = tuple(id(s) for s in slots)
@@ -224,9 +234,11 @@ class Server:
                         batches[d][1].close()
                     batches[d] = (key, Batch([s.plan for s in slots]))
                     self.stats["batch_rebuilds"] += 1
-                batches[d][1].step([s.u for s in slots], [s.v for s in slots], self.chunk)
-                for s in slots:
-                    s.left -= self.chunk
+                batches[d][1].step([s.u for s in slots], [s.v for s in slots], steps)
+                for s, n in zip(slots, steps):
+                    s.left -= n
+                    if n < self.chunk:
+                        self.stats["tail_steps"] += n
                 self.stats["ticks"] += 1
             # retire finished solves: copy results out asynchronously
             done = [s for s in self.active if s.left == 0]

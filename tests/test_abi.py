@@ -51,8 +51,9 @@ def test_struct_layout_matches_c(adr):
 #include <stdio.h>
 #include "adr.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(adr_problem), offsetof(adr_problem, n),
-         offsetof(adr_problem, tau), sizeof(adr_stats), offsetof(adr_stats, ms));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(adr_problem), offsetof(adr_problem, n),
+         offsetof(adr_problem, tau), offsetof(adr_problem, state), sizeof(adr_stats),
+         offsetof(adr_stats, ms));
   return 0;
 }
 """
@@ -64,7 +65,8 @@ int main(void) {
         vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True,
                                                check=True).stdout.split()]
     P, S = _abi.AdrProblem, _abi.AdrStats
-    assert vals == [ctypes.sizeof(P), P.n.offset, P.tau.offset, ctypes.sizeof(S), S.ms.offset]
+    assert vals == [ctypes.sizeof(P), P.n.offset, P.tau.offset, P.state.offset, ctypes.sizeof(S),
+                    S.ms.offset]
 
 
 def test_invalid_problems_rejected_on_host(adr):
@@ -81,6 +83,20 @@ def test_invalid_problems_rejected_on_host(adr):
         assert st == adr.ADR_EINVAL, p
         assert not plan.value
         assert len(L.adr_last_error()) > 0
+    # state modes: unknown -> EINVAL; compensated where it does not apply -> EUNSUPPORTED
+    for p, want in ((good.replace(state=3), adr.ADR_EINVAL),
+                    (good.replace(precision=wl.FP32, state=wl.STATE_COMPENSATED),
+                     adr.ADR_EUNSUPPORTED),
+                    (good.replace(precision=wl.BF16X3, scheme=wl.LAWSON2B,
+                                  state=wl.STATE_COMPENSATED), adr.ADR_EUNSUPPORTED)):
+        s = adr.make_problem(p)
+        plan = _abi.AdrPlan()
+        assert L.adr_plan_create(ctypes.byref(s), None, ctypes.byref(plan)) == want, p
+        assert not plan.value
+    s = adr.make_problem(good)
+    s.reserved = 1
+    assert L.adr_plan_create(ctypes.byref(s), None, ctypes.byref(_abi.AdrPlan())) == adr.ADR_EINVAL
+    assert L.adr_plan_reset_state(None) == adr.ADR_EINVAL
     assert L.adr_plan_create(None, None, ctypes.byref(_abi.AdrPlan())) == adr.ADR_EINVAL
     assert L.adr_step(None, None, None, 1) == adr.ADR_EINVAL
     assert L.adr_status_str(adr.ADR_EBUSY) == b"ADR_EBUSY"
@@ -92,6 +108,10 @@ def test_plan_bytes_host_only(adr):
     assert cb > sb
     sb64, _ = adr.plan_bytes(wl.schnakenberg_64())
     assert sb64 == 2 * 64 * 64 * 8
+    # a compensated state adds one FP32 word per point and component
+    _, c_auto = adr.plan_bytes(wl.fhn_1024(precision=wl.BF16X3))
+    _, c_plain = adr.plan_bytes(wl.fhn_1024(precision=wl.BF16X3).replace(state=wl.STATE_PLAIN))
+    assert c_auto - c_plain == 2 * 1024 * 1024 * 4
 
 
 def test_selftest_limits_checked_on_the_host(adr):

@@ -36,11 +36,41 @@ def test_hbm_roofline_arithmetic():
     assert r["frac"] == pytest.approx(r["achieved"] / 8000.0)
 
 
-def test_traffic_only_for_the_captured_source_and_kernel():
-    t = bench.profiled_traffic("fhn1024", 4)
-    assert isinstance(t, int) and t > 0
-    assert bench.profiled_traffic("fhn1024", 0) is None
-    assert bench.profiled_traffic("no_such_workload", 4) is None
+def test_traffic_only_for_the_captured_source_and_kernel(tmp_path):
+    """A capture summary is used only when its source hash is the current
+    tc.cu's and its kernel is the one timed."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2307_10684_gb300", "csrc", "tc.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    (tmp_path / "tc_mode_fhn1024.md").write_text(
+        f"source_sha256(tc.cu): {sha}\ncaptured_kernel: 4\ndram_bytes_per_launch: 25000000\n")
+    (tmp_path / "tc_mode_old.md").write_text(
+        "source_sha256(tc.cu): 0123456789abcdef\ncaptured_kernel: 4\n"
+        "dram_bytes_per_launch: 25000000\n")
+    assert bench.profiled_traffic("fhn1024", 4, str(tmp_path)) == 25000000
+    assert bench.profiled_traffic("fhn1024", 0, str(tmp_path)) is None
+    assert bench.profiled_traffic("old", 4, str(tmp_path)) is None
+    assert bench.profiled_traffic("no_such_workload", 4, str(tmp_path)) is None
+
+
+def test_in_step_roofline_arithmetic():
+    """Algorithmic work per mode-product launch: 4 n N flops and 16 + 8/d
+    bytes per point; frac is the slower bound's share of the duration."""
+    peaks = {"bf16_tflops": 2000.0, "hbm_gbs": 8000.0}
+    p = wl.fhn_1024(precision=wl.BF16X3)  # 1024^2, d = 2
+    N = 1024 * 1024
+    r = bench.mode_product_roofline(p, wl.BF16X3, 0.02, 4, peaks, "test", None)
+    assert r["algorithmic_flops_per_launch"] == pytest.approx(4 * 1024 * N)
+    assert r["algorithmic_bytes_per_launch"] == pytest.approx(20 * N + 8 * 1024 * 1024)
+    t_tc = 4 * 1024 * N / 2e15
+    t_hbm = (20 * N + 8 * 1024 * 1024) / 8e12
+    assert r["bound"] == ("tensor" if t_tc >= t_hbm else "hbm")
+    assert r["frac"] == pytest.approx(max(t_tc, t_hbm) / 2e-5)
+    assert r["issued_tensor_frac"] == pytest.approx(6 * t_tc / 2e-5)
+    q = wl.brusselator_256(precision=wl.BF16X3)  # 256^3, d = 3: HBM-bound
+    r3 = bench.mode_product_roofline(q, wl.BF16X3, 0.1, 6, peaks, "test", None)
+    assert r3["bound"] == "hbm" and r3["unit"] == "GB/s"
+    assert r3["achieved"] == pytest.approx(((16 + 8 / 3) * 256 ** 3 + 8 * 256 * 256) / 1e-4 / 1e9)
 
 
 @pytest.mark.parametrize("scheme", [wl.ETD2RKDS, wl.LAWSON2B])

@@ -127,9 +127,11 @@ def test_batch_churn_without_synchronisation(adr):
     no synchronisation in between (descriptor uploads through the page-locked
     ring, stream-ordered batch memory, deferred teardown): every solve equals
     the same solve stepped alone.  The loop uploads more descriptor bytes than
-    the ring's first capacity, so the ring wraps and waits for its events."""
+    the ring's first capacity, so the ring wraps and waits for its events.
+    The compensated state is carried across calls (ADR_STATE_COMPENSATED),
+    so 40 one-step calls in changing batches equal one call of 40 steps."""
     import torch
-    probs = mixed_problems(d=2, count=6)
+    probs = [p.replace(state=wl.STATE_COMPENSATED) for p in mixed_problems(d=2, count=6)]
     plans = [adr.Plan(p) for p in probs]
     us, vs, inits = states(adr, probs)
     ref = []
@@ -239,3 +241,69 @@ def test_plans_of_a_live_batch_are_protected(adr):
     plans[0].set_kernel(2)
     plans[0].close()
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_mixed_horizons_in_one_call_equal_alone(adr, d):
+    """adr_batch_step with a horizon per solve (0, 3, 17, 40, ...): solves
+    that finish drop out of the grouped work of the rest; each result equals
+    the same solve stepped alone for its own horizon (bitwise), and a solve
+    with horizon 0 is untouched."""
+    import torch
+    probs = mixed_problems(d=d, count=6)
+    horizons = [40, 3, 17, 0, 40, 33]
+    plans = [adr.Plan(p) for p in probs]
+    us, vs, inits = states(adr, probs)
+    with adr.Batch(plans) as b:
+        assert b.grouped
+        b.step(us, vs, horizons)
+    torch.cuda.synchronize()
+    for i, (p, (u0, v0)) in enumerate(zip(probs, inits)):
+        u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+        with adr.Plan(p) as one:
+            one.step(u, v, horizons[i])
+        torch.cuda.synchronize()
+        assert torch.equal(u, us[i]) and torch.equal(v, vs[i]), i
+    assert torch.equal(us[3], torch.tensor(inits[3][0], dtype=torch.float32, device="cuda"))
+    for pl in plans:
+        pl.close()
+
+
+def test_equal_operators_share_one_matrix_set(adr):
+    """Plans whose directional operators and step coincide take the FP64
+    matrix functions (and their split pieces) from the library's cache
+    instead of computing them again; the shared plan still steps exactly like
+    the first."""
+    import torch
+    # a step no other test uses, so that no live plan holds these sets
+    p = wl.fhn_1024(precision=wl.BF16X3, n=192, nsteps=10).replace(tau=0.0123456789)
+    a = adr.Plan(p)
+    # FHN on a square grid: each component's operator is the same in both
+    # directions, so a plan holds two distinct sets (u's, v's)
+    assert a.stats()["shared_matrices"] == 0
+    b = adr.Plan(p)
+    assert b.stats()["shared_matrices"] == 2  # both found in the cache
+    for w in range(4):
+        for c in range(2):
+            for mu in range(2):
+                assert np.array_equal(a.matrix(w, c, mu), b.matrix(w, c, mu))
+    u0, v0 = wl.initial_data(p)
+    outs = []
+    for pl in (a, b):
+        u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+        pl.step(u, v, p.nsteps)
+        torch.cuda.synchronize()
+        outs.append((u.cpu(), v.cpu()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    a.close()
+    # the set outlives the first plan while the second holds it
+    c = adr.Plan(p)
+    assert c.stats()["shared_matrices"] == 2
+    b.close()
+    c.close()
+    # a different step is another operator function: nothing shared
+    d = adr.Plan(p.replace(tau=p.tau * 0.5))
+    assert d.stats()["shared_matrices"] == 0
+    d.close()

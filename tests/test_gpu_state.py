@@ -1,0 +1,140 @@
+"""Compensated single-precision state (adr_state_mode) against the oracle.
+
+The stage updates U2 = U + tau T and U+ = U2 + 2^(d-1) tau S of Eq. 11 add a
+small increment to the state.  Rounding that sum to FP32 every step loses
+~1e-7 of the state per step, and over a long horizon of an unstable system
+those losses are amplified.  A CPU emulation (FP64 everywhere except an
+FP32 rounding of the two state updates) gives 4.4e-4 on the Brusselator
+256^2 served request below, against 1.4e-7 when the state is carried exactly
+and only the right-hand sides see its FP32 value.  The compensated state
+keeps hi + lo words, so these served requests meet the 1e-5 bound.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from oracle import schemes
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def adr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2307_10684_gb300 import build
+    build.build()
+    import paper_2307_10684_gb300 as adr
+    return adr
+
+
+def _served(rid):
+    return wl.serving_stream(count=2000)[rid][1]
+
+
+def _gpu(adr, p, u0, v0, nsteps, chunks=None):
+    import torch
+    u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+    v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+    with adr.Plan(p) as plan:
+        for n in (chunks or [nsteps]):
+            plan.step(u, v, n)
+        torch.cuda.synchronize()
+    return u.double().cpu().numpy(), v.double().cpu().numpy()
+
+
+# served requests whose plain FP32-state error was above 1e-5: a 2D
+# Brusselator at b = 4.36 (Hopf-unstable), 991 steps, and a 3D Schnakenberg
+# 64^3, 634 steps
+@pytest.mark.parametrize("rid", [60, 1180])
+def test_long_horizon_served_request_within_bound(adr, rid):
+    p = _served(rid).replace(precision=wl.BF16X3)
+    u0, v0 = wl.initial_data(p)
+    u0, v0 = wl.round_to(u0, wl.FP32), wl.round_to(v0, wl.FP32)
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, p.nsteps)
+    # the server's mode: compensated, carried across its 32-step ticks
+    chunks = [32] * (p.nsteps // 32) + [p.nsteps % 32]
+    Uc, Vc = _gpu(adr, p.replace(state=wl.STATE_COMPENSATED), u0, v0, p.nsteps, chunks)
+    Up, Vp = _gpu(adr, p.replace(state=wl.STATE_PLAIN), u0, v0, p.nsteps)
+    ec = oracle.max_rel_err(Uc, Vc, Ur, Vr)
+    ep = oracle.max_rel_err(Up, Vp, Ur, Vr)
+    assert ec <= TOL, (ec, ep)
+    assert ep > 3.0 * ec, (ec, ep)  # the plain state is what misses the bound
+
+
+def test_carried_state_equals_one_call(adr):
+    """ADR_STATE_COMPENSATED carries the low-order words across calls on the
+    same buffers, so 40 steps in calls of 13 + 27 equal one call of 40."""
+    import torch
+    p = wl.fhn_1024(precision=wl.BF16X3, n=128, nsteps=40).replace(state=wl.STATE_COMPENSATED)
+    u0, v0 = wl.initial_data(p)
+    a = _gpu(adr, p, u0, v0, 40)
+    b = _gpu(adr, p, u0, v0, 40, chunks=[13, 27])
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_auto_restarts_at_every_call(adr):
+    """ADR_STATE_AUTO restarts the compensation at each call, so stepping new
+    values in reused buffers needs no reset; with ADR_STATE_COMPENSATED the
+    same reuse needs adr_plan_reset_state."""
+    import torch
+    p = wl.fhn_1024(precision=wl.BF16X3, n=128, nsteps=20)
+    u0, v0 = wl.initial_data(p)
+    ref = _gpu(adr, p, u0, v0, 20)
+    for mode in (wl.STATE_AUTO, wl.STATE_COMPENSATED):
+        q = p.replace(state=mode)
+        u = torch.empty(p.shape, dtype=torch.float32, device="cuda")
+        v = torch.empty(p.shape, dtype=torch.float32, device="cuda")
+        with adr.Plan(q) as plan:
+            for rep in range(2):
+                u.copy_(torch.tensor(u0))
+                v.copy_(torch.tensor(v0))
+                if mode == wl.STATE_COMPENSATED and rep == 1:
+                    plan.reset_state()
+                plan.step(u, v, 20)
+                torch.cuda.synchronize()
+                assert np.array_equal(u.double().cpu().numpy(), ref[0]), (mode, rep)
+                assert np.array_equal(v.double().cpu().numpy(), ref[1]), (mode, rep)
+
+
+def test_solve_restarts_compensation(adr):
+    """adr_solve starts from (u0, v0) alone, whatever the plan stepped before."""
+    import torch
+    p = wl.brusselator_256(precision=wl.BF16X3, n=32, nsteps=30).replace(
+        state=wl.STATE_COMPENSATED)
+    u0, v0 = wl.initial_data(p)
+    hu0 = torch.tensor(u0, dtype=torch.float32)
+    hv0 = torch.tensor(v0, dtype=torch.float32)
+    outs = []
+    with adr.Plan(p) as plan:
+        for _ in range(2):
+            uT = torch.empty_like(hu0)
+            vT = torch.empty_like(hv0)
+            plan.solve(hu0, hv0, uT, vT, p.nsteps)
+            outs.append((uT.clone(), vT.clone()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("kernel", [0, 2, 4])
+def test_compensated_more_accurate_than_plain(adr, kernel):
+    """On a 256^2 FHN run of 200 steps every kernel's compensated result is
+    closer to the oracle than the plain one and within the bound."""
+    p = wl.fhn_1024(precision=wl.BF16X3, n=256, nsteps=200)
+    u0, v0 = wl.initial_data(p)
+    u0, v0 = wl.round_to(u0, wl.FP32), wl.round_to(v0, wl.FP32)
+    Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, p.nsteps)
+    import torch
+    errs = {}
+    for mode in (wl.STATE_PLAIN, wl.STATE_AUTO):
+        u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+        with adr.Plan(p.replace(state=mode), kernel=kernel) as plan:
+            plan.step(u, v, p.nsteps)
+        torch.cuda.synchronize()
+        errs[mode] = oracle.max_rel_err(u.double().cpu().numpy(), v.double().cpu().numpy(), Ur, Vr)
+    assert errs[wl.STATE_AUTO] <= TOL
+    assert errs[wl.STATE_AUTO] < errs[wl.STATE_PLAIN], errs

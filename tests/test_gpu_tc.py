@@ -86,9 +86,11 @@ def test_stage_one_fusion_both_ways(adr, n, fuse, monkeypatch):
     monkeypatch.setenv("ADR_TC_FUSE", fuse)
     monkeypatch.setenv("ADR_TC_VARIANT", "0")
     d = len(n)
+    # the fused epilogues carry a plain FP32 state (a compensated plan keeps
+    # the separate kernel)
     p = wl.Problem(d=d, n=n, lo=(0.0,) * d, hi=(1.0,) * d, diff=(0.05, 0.3),
                    adv=((0.2, -0.1, 0.3)[:d], (-0.2, 0.1, 0.05)[:d]), model=wl.SCHNAKENBERG,
-                   params=(300.0, 0.1, 0.9), tau=1e-3, nsteps=6, seed=17)
+                   params=(300.0, 0.1, 0.9), tau=1e-3, nsteps=6, seed=17, state=wl.STATE_PLAIN)
     u0, v0 = inputs(p, kind="uniform")
     Ur, Vr = schemes.etd2rkds_solve(schemes.make_plan(p), u0, v0, p.nsteps)
     U, V, st = run(adr, p, u0, v0, p.nsteps)

@@ -36,6 +36,11 @@ MODEL_NAMES = {SCHNAKENBERG: "schnakenberg", FHN: "fhn", BRUSSELATOR: "brusselat
 ETD2RKDS = 0
 LAWSON2B = 1
 
+# State modes (mirrors the C ABI enum adr_state_mode).
+STATE_AUTO = 0
+STATE_PLAIN = 1
+STATE_COMPENSATED = 2
+
 # Precision identifiers (mirrors the C ABI enum adr_precision).
 FP64 = 0
 FP32 = 1
@@ -70,6 +75,7 @@ class Problem:
     seed: int = 0
     name: str = ""
     scheme: int = 0   # 0 = ETD2RKds (Eq. 11), 1 = Lawson2b (Eq. 7)
+    state: int = 0    # adr_state_mode: 0 = library's choice, 1 = plain, 2 = compensated
 
     @property
     def shape(self) -> Tuple[int, ...]:
