@@ -601,10 +601,39 @@ def run_single(args, p, nts: int, R, with_compare: bool, oracle):
             dv, mv = adr.max_abs_diff(cv, torch.tensor(Vo, dtype=torch.float64, device="cuda"))
             compare["max_rel_err_vs_oracle"] = max(du / mu, dv / mv)
 
+    # the accurate mode (compensated state, double-float reactions) on the
+    # same workload: rate and accuracy
+    accurate = None
+    if (with_compare and prec in (wl.BF16X3, wl.TF32X3) and p.scheme == wl.ETD2RKDS
+            and int(getattr(p, "state", 0)) != wl.STATE_COMPENSATED):
+        pc = p.replace(state=wl.STATE_COMPENSATED)
+        with adr.Plan(pc, kernel=kernel) as aplan:
+            ams = []
+            for k in range(1 + max(1, args.steps // 2)):
+                u.copy_(u0)
+                v.copy_(v0)
+                flush.fill_(1.0)
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                aplan.step(u, v, nts)  # a new call on the same buffers: lo restarts below
+                a1.record(stream)
+                torch.cuda.synchronize()
+                aplan.reset_state()
+                if k > 0:
+                    ams.append(a0.elapsed_time(a1))
+        accurate = {"state": "compensated", "ms_per_step": float(np.mean(ams)),
+                    "value": npts * nts / (float(np.mean(ams)) / 1e3)}
+        if oracle is not None:
+            Uo, Vo, _ = oracle[0].result(oracle[1])
+            du, mu = adr.max_abs_diff(u, torch.tensor(Uo, dtype=torch.float64, device="cuda"))
+            dv, mv = adr.max_abs_diff(v, torch.tensor(Vo, dtype=torch.float64, device="cuda"))
+            accurate["max_rel_err_vs_oracle"] = max(du / mu, dv / mv)
+
     plan.close()
     if rank != 0:
         return None
-    state = {0: "auto", 1: "plain", 2: "compensated"}[int(getattr(p, "state", 0))]
+    state = {0: "auto (plain)", 1: "plain", 2: "compensated"}[int(getattr(p, "state", 0))]
     return {"metric": "point-steps/s", "value": value, "unit": "point-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
@@ -621,7 +650,7 @@ def run_single(args, p, nts: int, R, with_compare: bool, oracle):
             **acc, "plan_ms": plan_ms,
             "e2e": e2e, "gpu_launches": launches,
             "roofline": roof, "in_step_check": in_step, "clocks": clocks,
-            "same_gpu_comparison": compare,
+            "same_gpu_comparison": compare, "accurate_mode": accurate,
             "kernel_timing": "per-kernel shares from a second pass of the same solves; graph "
                              "chunks replayed with an event-record node before and after every "
                              "kernel (no host launch gaps; kernels serialised)",
@@ -799,7 +828,8 @@ def run_serve(args):
     world, rank, local = R.world, R.rank, R.local
     torch.cuda.set_device(local)
     prec = PREC[args.precision]
-    stream_reqs = wl.serving_stream(count=args.requests, precision=prec, seed=5 + rank)
+    stream_reqs = wl.serving_stream(count=args.requests, rate=args.rate, precision=prec,
+                                    seed=5 + rank)
 
     def make(i, t, p):
         def init(p=p):
@@ -877,7 +907,7 @@ def run_serve(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[prec],
                 "data": "synthetic Poisson request stream per rank (seed 5 + rank), "
                         "seeded initial data",
-                "config": {"workload": f"serving, {len(reqs)} requests per GPU at 200/s, 2D sides "
+                "config": {"workload": f"serving, {len(reqs)} requests per GPU at {args.rate:g}/s, 2D sides "
                                        "128-1024, 3D sides 64-192, 3 models, horizons 50-1000",
                            "budget_gb": args.budget_gb, "chunk_steps": srv.chunk,
                            "planner_threads": srv.planners},
@@ -929,6 +959,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=40)
     ap.add_argument("--ref-sample", type=int, default=20)
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: requests per GPU")
+    ap.add_argument("--rate", type=float, default=200.0,
+                    help="serving workload: mean Poisson arrival rate (requests/s)")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device-memory budget")
     args = ap.parse_args()
     if args.precision is None:

@@ -109,32 +109,34 @@ typedef enum {
 } adr_scheme;
 
 /* How a single-precision state is carried from step to step.
+ *  ADR_STATE_AUTO        : the library's choice: plain (below).
  *  ADR_STATE_PLAIN       : the caller's buffers are the whole state; each
  *                          stage update U + tau T of Eq. 11 is rounded to
- *                          FP32.  Over long horizons these roundings
- *                          accumulate, by ~1e-7 relative per step and more
- *                          where the dynamics amplify them.
- *  ADR_STATE_COMPENSATED : the state is hi + lo: hi in the caller's buffer
+ *                          FP32 and the reactions are evaluated in FP32.
+ *                          Over long horizons these roundings accumulate, by
+ *                          ~1e-7 relative per step and more where the
+ *                          dynamics amplify them.
+ *  ADR_STATE_COMPENSATED : the accurate mode for long or unstable horizons.
+ *                          The state is hi + lo: hi in the caller's buffer
  *                          (the FP32 value nearest the state) and lo, a
  *                          low-order FP32 word per point and component, in
  *                          plan memory.  The stage updates of Eq. 11 add the
  *                          increment to hi + lo with its exact rounding
  *                          error (TwoSum) and renormalise, so the state
  *                          keeps about 48 bits; the right-hand sides are
- *                          evaluated from hi.  16 bytes of extra traffic per
- *                          point and step.  The lo words carry over from one
- *                          call to the next while the plan (alone or in a
- *                          batch) steps the same (u, v) pair; they restart
- *                          at zero when it steps another pair, when
- *                          adr_solve starts, and on adr_plan_reset_state.
- *                          A caller that writes new values into buffers the
- *                          plan has stepped calls adr_plan_reset_state.
- *  ADR_STATE_AUTO        : the library's choice.  For ADR_BF16X3 and
- *                          ADR_TF32X3 plans of ADR_ETD2RKDS: compensated
- *                          within each call (the lo words restart at zero at
- *                          every adr_step, adr_solve and adr_batch_step
- *                          call, so reused buffers need nothing extra);
- *                          plain for every other plan.
+ *                          evaluated from hi, with the reactions (and the
+ *                          stage-2 reaction difference) in double-float
+ *                          arithmetic and double-float parameters, since an
+ *                          FP32 reaction whose terms cancel loses digits
+ *                          every step.  Costs 16 bytes of traffic per point
+ *                          and step and more pointwise arithmetic.  The lo
+ *                          words carry over from one call to the next while
+ *                          the plan (alone or in a batch) steps the same
+ *                          (u, v) pair; they restart at zero when it steps
+ *                          another pair, when adr_solve starts, and on
+ *                          adr_plan_reset_state.  A caller that writes new
+ *                          values into buffers the plan has stepped calls
+ *                          adr_plan_reset_state.
  * Compensation applies to tensor-core ETD2RKds plans only: other plans
  * asking for ADR_STATE_COMPENSATED get ADR_EUNSUPPORTED. */
 typedef enum {
@@ -402,6 +404,47 @@ adr_status adr_plan_indicator_log(adr_plan plan, double* out, int64_t max_steps,
  * Needs adr_plan_set_indicators(plan, 1).  Synchronous. */
 adr_status adr_run(adr_plan plan, void* u, void* v, double t_end, double tol, int64_t check_every,
                    int64_t* steps_done, double ind_last[4]);
+
+/* ---------------------------------------------------------------- general
+ * Plans beyond the finite-difference two-component setting: the method
+ * needs nothing of the directional matrices but their size (Sec. 1, Eq. 3-4:
+ * any A_mu in the Kronecker sum) and extends to more than two components
+ * (Sec. 3, closing remark).  A general plan has m = 1..4 components, caller
+ * matrices A_mu^c (dense, any entries), and a polynomial reaction: each term
+ * adds coef * prod_j u_j^pow[j] to g^comp.  One step is Eq. 11 per
+ * component, with K^c U_c = sum_mu U_c x_mu A_mu^c as d dense mode products;
+ * every stage value is formed before any stage-2 reaction.  Products in
+ * FP64 or FP32 (ADR_FP64 / ADR_FP32; other precisions: ADR_EUNSUPPORTED);
+ * matrix functions in FP64 on the GPU as for the other plans (Pade [13/13]
+ * scaling and squaring, dense powers and LU). */
+typedef struct {
+  int32_t comp;     /* component the term adds to, 0..m-1                  */
+  int32_t pow[4];   /* exponents of u_0..u_3, 0..8 (0 beyond m)             */
+  double coef;      /* finite                                              */
+} adr_term;
+
+typedef struct {
+  int32_t d;                 /* 2 or 3                                     */
+  int32_t m;                 /* components, 1..4                           */
+  int32_t precision;         /* ADR_FP64 or ADR_FP32                       */
+  int32_t nterms;            /* 0..64                                      */
+  int64_t n[3];              /* grid points per direction, 1..4096          */
+  const double* A[4][3];     /* host, A[c][mu]: n[mu] x n[mu] row-major,
+                                read during the call only                   */
+  const adr_term* terms;     /* host, nterms entries, read during the call  */
+  double tau;                /* constant step (> 0)                        */
+} adr_general_problem;
+
+/* Create a general plan (copies everything it needs).  Synchronises the
+ * stream.  adr_step / adr_solve / batches refuse general plans
+ * (ADR_EINVAL); adr_plan_matrix, adr_plan_stats, adr_plan_set_timing and
+ * adr_plan_destroy work as for other plans (component 0..m-1). */
+adr_status adr_plan_create_general(const adr_general_problem* problem, void* stream,
+                                   adr_plan* out);
+/* Advance the m device state tensors states[0..m-1] (layout as above,
+ * double for ADR_FP64, float for ADR_FP32, distinct) by nsteps steps in
+ * place.  Asynchronous. */
+adr_status adr_step_general(adr_plan plan, void* const* states, int64_t nsteps);
 
 /* Short name of a status code (static storage). */
 const char* adr_status_str(adr_status s);

@@ -23,7 +23,7 @@ from ._abi import (ADR_OK, ADR_EINVAL, ADR_ENOMEM, ADR_ECUDA, ADR_EUNSUPPORTED, 
                    LAWSON2B, STATE_AUTO, STATE_PLAIN, STATE_COMPENSATED, AdrError, lib,
                    library_path)
 
-__all__ = ["Plan", "Batch", "AdrError", "lib", "library_path", "plan_bytes", "max_abs_diff",
+__all__ = ["Plan", "Batch", "GeneralPlan", "AdrError", "lib", "library_path", "plan_bytes", "max_abs_diff",
            "make_problem", "state_dtype"]
 
 
@@ -212,6 +212,82 @@ class Plan:
         st = _abi.AdrStats()
         _abi.check(lib().adr_plan_stats(self._p, ctypes.byref(st)))
         return _stats_dict(st)
+
+
+class GeneralPlan:
+    """adr_plan_create_general: m = 1..4 components, dense directional
+    matrices A[c][mu] (numpy n_mu x n_mu), polynomial reaction terms
+    (comp, exponents, coef) each adding coef * prod_j u_j^e_j to g^comp."""
+
+    def __init__(self, A, terms, tau: float, precision: int = FP64, stream=None):
+        import numpy as np
+        self.m = len(A)
+        self.d = len(A[0])
+        self.n = [int(A[0][mu].shape[0]) for mu in range(self.d)]
+        self.shape = tuple(reversed(self.n))
+        self.precision = int(precision)
+        gp = _abi.AdrGeneralProblem()
+        gp.d, gp.m, gp.precision, gp.nterms = self.d, self.m, self.precision, len(terms)
+        for mu in range(3):
+            gp.n[mu] = self.n[mu] if mu < self.d else 1
+        keep = []
+        for c in range(self.m):
+            for mu in range(self.d):
+                a = np.ascontiguousarray(A[c][mu], dtype=np.float64)
+                if a.shape != (self.n[mu], self.n[mu]):
+                    raise ValueError("A[c][mu] must be n_mu x n_mu for every component")
+                keep.append(a)
+                gp.A[c][mu] = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        T = (_abi.AdrTerm * max(1, len(terms)))()
+        for i, (c, exps, coef) in enumerate(terms):
+            T[i].comp = int(c)
+            for j in range(4):
+                T[i].pow[j] = int(exps[j]) if j < len(exps) else 0
+            T[i].coef = float(coef)
+        gp.terms = ctypes.cast(T, ctypes.POINTER(_abi.AdrTerm))
+        gp.tau = float(tau)
+        self._p = _abi.AdrPlan()
+        _abi.check(lib().adr_plan_create_general(ctypes.byref(gp),
+                                                 ctypes.c_void_p(_stream_handle(stream)),
+                                                 ctypes.byref(self._p)))
+
+    def step(self, states, nsteps: int = 1):
+        """adr_step_general: advance the m CUDA tensors in place."""
+        import torch
+        dt = state_dtype(self.precision)
+        if len(states) != self.m:
+            raise ValueError("one state tensor per component")
+        for x in states:
+            if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == dt and
+                    x.is_contiguous() and tuple(x.shape) == self.shape):
+                raise ValueError(f"states must be contiguous CUDA {dt} tensors of shape {self.shape}")
+        S = (ctypes.c_void_p * self.m)(*[x.data_ptr() for x in states])
+        _abi.check(lib().adr_step_general(self._p, S, ctypes.c_int64(int(nsteps))))
+
+    def matrix(self, which: int, component: int, mu: int):
+        import numpy as np
+        n = self.n[mu]
+        out = np.empty((n, n), dtype=np.float64)
+        _abi.check(lib().adr_plan_matrix(self._p, int(which), int(component), int(mu),
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def close(self):
+        if self._p:
+            _abi.check(lib().adr_plan_destroy(self._p))
+            self._p = _abi.AdrPlan()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def _stats_dict(st) -> dict:

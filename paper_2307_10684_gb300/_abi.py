@@ -37,6 +37,16 @@ class AdrTuning(ctypes.Structure):
     _fields_ = [("kernel", c_int32), ("reserved", c_int32 * 7)]
 
 
+class AdrTerm(ctypes.Structure):
+    _fields_ = [("comp", c_int32), ("pow", c_int32 * 4), ("coef", c_double)]
+
+
+class AdrGeneralProblem(ctypes.Structure):
+    _fields_ = [("d", c_int32), ("m", c_int32), ("precision", c_int32), ("nterms", c_int32),
+                ("n", c_int64 * 3), ("A", (ctypes.POINTER(c_double) * 3) * 4),
+                ("terms", ctypes.POINTER(AdrTerm)), ("tau", c_double)]
+
+
 class AdrPlan(ctypes.c_void_p):
     pass
 
@@ -55,6 +65,9 @@ SIGNATURES = {
     "adr_plan_set_stream": (c_int32, [AdrPlan, c_void_p]),
     "adr_step": (c_int32, [AdrPlan, c_void_p, c_void_p, c_int64]),
     "adr_plan_reset_state": (c_int32, [AdrPlan]),
+    "adr_plan_create_general": (c_int32, [ctypes.POINTER(AdrGeneralProblem), c_void_p,
+                                          ctypes.POINTER(AdrPlan)]),
+    "adr_step_general": (c_int32, [AdrPlan, ctypes.POINTER(c_void_p), c_int64]),
     "adr_plan_set_indicators": (c_int32, [AdrPlan, c_int32]),
     "adr_plan_indicator_log": (c_int32, [AdrPlan, ctypes.POINTER(c_double), c_int64,
                                          ctypes.POINTER(c_int64)]),

@@ -112,6 +112,9 @@ cudaError_t launch_rdiff(const PointwiseArgsT<T>& a, const T* u, const T* v, con
 // Matrix-function helpers (matfun.cu).
 cudaError_t matfun_phi(int n, const Tridiag& A, double tau, double* E, double* P1, double* P2,
                        cudaStream_t s);
+// The same for a dense row-major A (device), norm1_A = ||A||_1.
+cudaError_t matfun_phi_dense(int n, const double* A, double norm1_A, double tau, double* E,
+                             double* P1, double* P2, cudaStream_t s);
 cudaError_t launch_build_dense(int n, const Tridiag& A, double scale, double* X, cudaStream_t s);
 cudaError_t launch_convert(const double* src, void* dst, int64_t count, int to_double,
                            int transpose_n, cudaStream_t s);
@@ -139,6 +142,8 @@ inline uint64_t key_bits(double x) {
   memcpy(&b, &x, sizeof(b));
   return b;
 }
+
+struct GeneralState;  // general plans (general.cu): m components, dense A_mu
 
 // Tensor-core operand set of a plan (tc.cu).
 struct TcOperands {
@@ -192,6 +197,7 @@ struct adr_plan_s {
   void* dstate[2];  // device state for adr_solve with host buffers
   double* ind;      // 4 accumulators of adr_indicators
   std::vector<void*> allocs;
+  adr::GeneralState* gen;     // non-null for plans of adr_plan_create_general
   std::vector<void*> shared;  // matrix sets held in the process-wide cache
   int32_t shared_hits;        // of them, found there (computed by another plan)
   // counters
@@ -230,9 +236,9 @@ static const char* const kClassNames[KC_COUNT] = {"rhs_stencil_reaction", "react
 void tc_init(TcOperands* t);
 void tc_free(TcOperands* t);
 // variant_req: -1 = the library's choice, else a kernel variant (adr_tuning)
-// comp: carry the state as hi + lo FP32 words; 1 = within each call
-// (ADR_STATE_AUTO), 2 = across calls on the same (u, v) pair
-// (ADR_STATE_COMPENSATED)
+// comp: 2 = carry the state as hi + lo FP32 words across calls on the same
+// (u, v) pair and evaluate the reactions in double-float
+// (ADR_STATE_COMPENSATED); 0 = plain
 cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t n[3],
                        double* const master[2][3][4], cudaStream_t s, int variant_req, int comp);
 // Clear the low-order state words (no-op without compensation).
@@ -305,3 +311,11 @@ inline void harvest_timing(adr_plan_s* P, const std::vector<TimedLaunch>& v) {
 // Advance a plan's (u, v) by nsteps, continuing its compensated state as it
 // stands (api.cu; the batch path uses it for plans it steps one by one).
 adr_status plan_step_continue(adr_plan plan, void* u, void* v, int64_t nsteps);
+
+namespace adr {
+// General plans (general.cu).
+cudaError_t general_step(adr_plan P, void* const* U);
+void general_free(adr_plan P);
+int general_components(const adr_plan_s* P);
+const double* general_master(const adr_plan_s* P, int c, int mu, int which);
+}  // namespace adr

@@ -92,12 +92,11 @@ static Tridiag fd_coefficients(int64_t n, double lo, double hi, double delta, do
   return t;
 }
 
-// How a (validated) problem carries its state: 0 = plain FP32, 1 = hi + lo
-// FP32 words within each call, 2 = hi + lo carried across calls.
+// How a (validated) problem carries its state: 0 = plain FP32, 2 = hi + lo
+// FP32 words carried across calls, with the reactions in double-float.
 static int compensated(const adr_problem* p) {
   const bool tc = p->precision == ADR_BF16X3 || p->precision == ADR_TF32X3;
-  if (!tc || p->scheme != ADR_ETD2RKDS || p->state == ADR_STATE_PLAIN) return 0;
-  return p->state == ADR_STATE_COMPENSATED ? 2 : 1;
+  return (tc && p->scheme == ADR_ETD2RKDS && p->state == ADR_STATE_COMPENSATED) ? 2 : 0;
 }
 
 static bool same_operator(const Tridiag& a, const Tridiag& b) {
@@ -248,6 +247,7 @@ static void plan_free(adr_plan P) {
   // the operand pieces first: they are keyed by the FP64 matrices' addresses
   tc_free(&P->tc);
   for (void* q : P->shared) shared_release(q);
+  general_free(P);
   for (cudaEvent_t e : P->event_pool) cudaEventDestroy(e);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->gexec_timed) cudaGraphExecDestroy(P->gexec_timed);
@@ -267,6 +267,7 @@ extern "C" adr_status adr_plan_create_tuned(const adr_problem* problem, const ad
   adr_status st = validate(problem);
   if (st != ADR_OK) return st;
   adr_plan P = new adr_plan_s();
+  P->gen = nullptr;
   memset(&P->pw, 0, sizeof(P->pw));
   memset(P->master, 0, sizeof(P->master));
   memset(P->op, 0, sizeof(P->op));
@@ -492,6 +493,7 @@ static void build_graph(adr_plan P, void* u, void* v) {
 
 static adr_status step_impl(adr_plan P, void* u, void* v, int64_t nsteps) {
   int64_t done = 0;
+  if (P->gen) return fail(ADR_EINVAL, "a general plan steps with adr_step_general");
   if (nsteps == 0) return ADR_OK;
   if (P->prec == ADR_TF32X3 || P->prec == ADR_BF16X3) {
     if ((((uintptr_t)u) | ((uintptr_t)v)) & 15)
@@ -640,6 +642,7 @@ extern "C" adr_status adr_plan_reset_state(adr_plan plan) {
 extern "C" adr_status adr_solve(adr_plan plan, const void* u0, const void* v0, void* uT, void* vT,
                                 int64_t nsteps) {
   if (!plan) return fail(ADR_EINVAL, "plan is NULL");
+  if (plan->gen) return fail(ADR_EINVAL, "a general plan steps with adr_step_general");
   if (!u0 || !v0 || !uT || !vT) return fail(ADR_EINVAL, "NULL state pointer");
   if (uT == vT) return fail(ADR_EINVAL, "uT and vT must differ");
   if (nsteps < 0) return fail(ADR_EINVAL, "nsteps < 0");
@@ -702,11 +705,13 @@ extern "C" adr_status adr_plan_bytes(const adr_problem* problem, size_t* state_b
 
 extern "C" adr_status adr_plan_matrix(adr_plan plan, int which, int component, int mu, double* out) {
   if (!plan || !out) return fail(ADR_EINVAL, "NULL argument");
-  if (which < 0 || which > 3 || component < 0 || component > 1 || mu < 0 || mu >= plan->d)
+  const int ncomp = plan->gen ? general_components(plan) : 2;
+  if (which < 0 || which > 3 || component < 0 || component >= ncomp || mu < 0 || mu >= plan->d)
     return fail(ADR_EINVAL, "matrix index out of range");
   const int64_t n = plan->n[mu];
-  ADR_CUDA_TRY(cudaMemcpyAsync(out, plan->master[component][mu][which], (size_t)n * n * 8,
-                               cudaMemcpyDeviceToHost, plan->stream));
+  const double* src = plan->gen ? general_master(plan, component, mu, which)
+                                 : plan->master[component][mu][which];
+  ADR_CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)n * n * 8, cudaMemcpyDeviceToHost, plan->stream));
   ADR_CUDA_TRY(cudaStreamSynchronize(plan->stream));
   return ADR_OK;
 }

@@ -372,8 +372,32 @@ static cudaError_t gemm64(int n, const double* A, const double* B, double* C, co
 // banded with bandwidth k and q(Xs) has bandwidth 13: powers are formed by
 // three-term recurrences and q is factorised as a band matrix; only the
 // squaring phase uses dense products.  Synchronises the stream.
+// Xs = scale * A for a dense row-major A (the first power of the dense path).
+__global__ void scale_kernel(const double* __restrict__ A, double scale, double* __restrict__ X,
+                             int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    X[e] = scale * A[e];
+}
+
+static cudaError_t matfun_core(int n, const Tridiag* Atri, const double* Adense, double norm1,
+                               double tau, double* E, double* P1, double* P2, cudaStream_t s);
+
+cudaError_t matfun_phi_dense(int n, const double* A, double norm1_A, double tau, double* E,
+                             double* P1, double* P2, cudaStream_t s) {
+  return matfun_core(n, nullptr, A, norm1_A * tau, tau, E, P1, P2, s);
+}
+
 cudaError_t matfun_phi(int n, const Tridiag& A, double tau, double* E, double* P1, double* P2,
                        cudaStream_t s) {
+  return matfun_core(n, &A, nullptr, -1.0, tau, E, P1, P2, s);
+}
+
+// The same algorithm for a tridiagonal A (banded powers and band LU) or a
+// dense A (norm1 = ||tau A||_1 given; dense products and a full-bandwidth
+// LU).
+static cudaError_t matfun_core(int n, const Tridiag* Atri, const double* Adense, double norm1,
+                               double tau, double* E, double* P1, double* P2, cudaStream_t s) {
   DevBufs mem;
   const size_t nn = (size_t)n * n;
   double *Pa, *Pb, *Qm, *Pm, *R1m, *R2m, *T1, *T2, *T3;
@@ -396,13 +420,15 @@ cudaError_t matfun_phi(int n, const Tridiag& A, double tau, double* E, double* P
   // have column norm 1 < theta_13, so only X matters)
   MF_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long), s));
   MF_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
-  norm1_tridiag_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, A, tau, nrm);
-  MF_TRY(cudaGetLastError());
-  unsigned long long nbits = 0;
-  MF_TRY(cudaMemcpyAsync(&nbits, nrm, sizeof(nbits), cudaMemcpyDeviceToHost, s));
-  MF_TRY(cudaStreamSynchronize(s));
-  double norm;
-  memcpy(&norm, &nbits, sizeof(norm));
+  double norm = norm1;
+  if (Atri) {
+    norm1_tridiag_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, *Atri, tau, nrm);
+    MF_TRY(cudaGetLastError());
+    unsigned long long nbits = 0;
+    MF_TRY(cudaMemcpyAsync(&nbits, nrm, sizeof(nbits), cudaMemcpyDeviceToHost, s));
+    MF_TRY(cudaStreamSynchronize(s));
+    memcpy(&norm, &nbits, sizeof(norm));
+  }
   int sp = 0;
   if (norm > kTheta13) sp = std::max(0, (int)ceil(log2(norm / kTheta13)));
   const double c = ldexp(1.0, -sp);
@@ -429,17 +455,30 @@ cudaError_t matfun_phi(int n, const Tridiag& A, double tau, double* E, double* P
   MF_TRY(cudaGetLastError());
   const double* prev = nullptr;  // identity
   double* bufs[2] = {Pa, Pb};
+  double* X1 = nullptr;  // dense path: Xs, the factor of every power
+  if (Adense) {
+    MF_TRY(mem.alloc(&X1, nn));
+    scale_kernel<<<g, 256, 0, s>>>(Adense, xs, X1, (int64_t)nn);
+    MF_TRY(cudaGetLastError());
+  }
   for (int k = 1; k <= 13; ++k) {
     double* cur = bufs[k & 1];
-    tridiag_apply_kernel<<<g, 256, 0, s>>>(n, A, xs, prev, cur);
-    MF_TRY(cudaGetLastError());
+    if (Atri) {
+      tridiag_apply_kernel<<<g, 256, 0, s>>>(n, *Atri, xs, prev, cur);
+      MF_TRY(cudaGetLastError());
+    } else if (k == 1) {
+      MF_TRY(cudaMemcpyAsync(cur, X1, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      MF_TRY(gemm64(n, prev, X1, cur, nullptr, 0.0, nullptr, 0.0, s));
+    }
     accumulate4_kernel<<<g, 256, 0, s>>>(n, cur, coef(k), Qm, Pm, R1m, R2m);
     MF_TRY(cudaGetLastError());
     prev = cur;
   }
 
-  // q R = [p | p1 - q1 | p2 - q1 - q2] (band LU with partial pivoting)
-  const int bl = 13, bu = 13;
+  // q R = [p | p1 - q1 | p2 - q1 - q2] (LU with partial pivoting: banded for
+  // a tridiagonal A, full bandwidth for a dense one)
+  const int bl = Atri ? 13 : n - 1, bu = Atri ? 13 : n - 1;
   band_lu_kernel<<<1, 1024, 0, s>>>(n, bl, bu, Qm, piv, info);
   MF_TRY(cudaGetLastError());
   band_solve_kernel<<<(3 * n + 127) / 128, 128, 0, s>>>(n, bl, bu, Qm, piv, Pm, R1m, R2m, 1.0, c,

@@ -570,13 +570,17 @@ __device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cluster_add
 // columns; it prefetches its FP32 base values two 16-column chunks ahead,
 // starting before the accumulator is ready.
 //
+// IND instantiation: the last product of a step with the indicators of
+// Sec. 4 on (a separate instantiation, so that the other launches carry none
+// of its code).
+//
 // XCHG instantiation (launched in clusters of two, for the kStage1X pass):
 // CTA 2k + c holds component c of the tile, forms U2 (or V2) in its
 // epilogue, stores it, then each epilogue warp signals its counterpart in
 // the other CTA through that CTA's `xready` barrier and waits for its own;
 // it then reads the other component's base and stage values (L2) and writes
 // its component of D = G(U2, V2) - G(U, V) as BF16 pieces.
-template <int SW, int BN, bool PAIR, bool XCHG, int F = kFmtBF16>
+template <int SW, int BN, bool PAIR, bool XCHG, int F = kFmtBF16, bool IND = false>
 __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_constant__ TcLaunch L) {
   using C = TcCfg<SW, BN, F>;
   static_assert(F == kFmtBF16 || (!PAIR && !XCHG), "TF32 pieces: plain epilogues only");
@@ -841,7 +845,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
         float bv[HC];
         const float* bsrc = D->base[w.c_lo];
         float* lp = mode == kAxpy ? D->lo[w.c_lo] : nullptr;  // compensated state update
-        double* ind = mode == kAxpy ? indicator_slot(D, w.c_lo) : nullptr;
+        double* ind = (IND && mode == kAxpy) ? indicator_slot(D, w.c_lo) : nullptr;
 #pragma unroll
         for (int j = 0; j < HC; ++j) {
           const int col = n0 + j;
@@ -1164,7 +1168,7 @@ __device__ __forceinline__ Unit2 decode_unit2(const TcLaunch& L, int u, int bn) 
   return w;
 }
 
-template <int SW>
+template <int SW, bool IND = false>
 __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_constant__ TcLaunch L) {
   using C = Tc2Cfg<SW>;
   constexpr int BN = C::BN;
@@ -1310,7 +1314,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
       float bv[HC];
       const float* bsrc = D->base[w.c];
       float* lp = mode == kAxpy ? D->lo[w.c] : nullptr;  // compensated state update
-      double* ind = mode == kAxpy ? indicator_slot(D, w.c) : nullptr;
+      double* ind = (IND && mode == kAxpy) ? indicator_slot(D, w.c) : nullptr;
 #pragma unroll
       for (int j = 0; j < HC; ++j) {
         const int col = n0 + j;
@@ -1541,7 +1545,7 @@ __device__ __forceinline__ Coef coef(const TridiagT<float>& A) { return Coef{A.l
 // and issues all their loads (the planes and the x values beyond the warp's
 // run) before any arithmetic, so that a warp keeps several planes of loads
 // in flight; the planes z - 1 and z + ZB carry over.
-template <int ZB, int F = kFmtBF16>
+template <int ZB, int F = kFmtBF16, bool DF = false>
 __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_constant__ PwLaunch L) {
   __shared__ PwDesc sd;
   int lb;
@@ -1618,7 +1622,10 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_
         ku += tri_dir(el(pu[q], j), cu, el(pu[q + 2], j), zq, nz, czu.lo, czu.up, czu.b0, czu.bn);
         kv += tri_dir(el(pv[q], j), cv, el(pv[q + 2], j), zq, nz, czv.lo, czv.up, czv.b0, czv.bn);
         float gu, gv;
-        react_df(rx, cu, cv, gu, gv);
+        if constexpr (DF)
+          react_df(rx, cu, cv, gu, gv);
+        else
+          react<float>(rx, cu, cv, gu, gv);
         ou[j] = ku + gu;
         ov[j] = kv + gv;
       }
@@ -1653,7 +1660,7 @@ constexpr int kRingSlots = 5;
 constexpr int kRingSmem = kRingSlots * 2 * kRingField * 4 + 128 + kRingSlots * 8;
 static_assert(kRingField * 4 % 128 == 0, "copy destinations keep 128-byte alignment");
 
-template <int F = kFmtBF16>
+template <int F = kFmtBF16, bool DF = false>
 __global__ void __launch_bounds__(kPwThreads, 2) rhs3_ring_kernel(const __grid_constant__ PwLaunch L) {
   extern __shared__ uint8_t smem_raw[];
   float* ring = (float*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -1772,7 +1779,10 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs3_ring_kernel(const __grid_c
           kv += tri_dir(el(vzm, j), cv, el(vzp, j), z, nz, czv.lo, czv.up, czv.b0, czv.bn);
         }
         float gu, gv;
-        react_df(rx, cu, cv, gu, gv);
+        if constexpr (DF)
+          react_df(rx, cu, cv, gu, gv);
+        else
+          react<float>(rx, cu, cv, gu, gv);
         ou[j] = ku + gu;
         ov[j] = kv + gv;
       }
@@ -1802,7 +1812,7 @@ constexpr int kZB2 = 4;  // planes per iteration of the 2D stencil kernel
 
 // D^c = G^c(U2, V2) - G^c(U, V) written as BF16 pieces [3][N] (Eq. 11,
 // second stage).
-template <int F = kFmtBF16>
+template <int F = kFmtBF16, bool DF = false>
 __global__ void __launch_bounds__(kPwThreads) rdiff_pieces_kernel(const __grid_constant__ PwLaunch L) {
   FLAT_PROLOGUE
   const ReactionT<float> rx = sd.a.rx;
@@ -1824,7 +1834,15 @@ __global__ void __launch_bounds__(kPwThreads) rdiff_pieces_kernel(const __grid_c
     float du[4], dv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      react_diff_df(rx, el(a0[k], j), el(a1[k], j), el(a2[k], j), el(a3[k], j), du[j], dv[j]);
+      if constexpr (DF) {
+        react_diff_df(rx, el(a0[k], j), el(a1[k], j), el(a2[k], j), el(a3[k], j), du[j], dv[j]);
+      } else {
+        float g0u, g0v, g2u, g2v;
+        react<float>(rx, el(a0[k], j), el(a1[k], j), g0u, g0v);
+        react<float>(rx, el(a2[k], j), el(a3[k], j), g2u, g2v);
+        du[j] = g2u - g0u;
+        dv[j] = g2v - g0v;
+      }
     }
     store_pieces_fmt<F>(sd.wu, N, 4 * g, du);
     store_pieces_fmt<F>(sd.wv, N, 4 * g, dv);
@@ -1985,12 +2003,19 @@ cudaError_t set_smem_attr() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(tc_mode_kernel<SW, BN, false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_mode_kernel<SW, BN, false, false, kFmtBF16, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   return e;
 }
 template <int SW>
 cudaError_t set_smem_attr_pair() {
-  return cudaFuncSetAttribute(tc_pair_kernel<SW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              Tc2Cfg<SW>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel<SW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Tc2Cfg<SW>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_pair_kernel<SW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Tc2Cfg<SW>::SMEM);
+  return e;
 }
 
 // Programmatic dependent launch for the kernels of a step (ADR_PDL=0 turns
@@ -2019,15 +2044,18 @@ cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-template <bool PAIR>
+template <bool PAIR, bool IND = false>
 cudaError_t launch_tc_t(int v, dim3 grid, cudaStream_t s, const TcLaunch& L) {
   switch (v) {
     case 0:
-      return launch_k(tc_mode_kernel<64, 128, PAIR, false>, grid, dim3(kThreads), TcCfg<64, 128>::SMEM, s, L);
+      return launch_k(tc_mode_kernel<64, 128, PAIR, false, kFmtBF16, IND>, grid, dim3(kThreads),
+                      TcCfg<64, 128>::SMEM, s, L);
     case 1:
-      return launch_k(tc_mode_kernel<128, 128, PAIR, false>, grid, dim3(kThreads), TcCfg<128, 128>::SMEM, s, L);
+      return launch_k(tc_mode_kernel<128, 128, PAIR, false, kFmtBF16, IND>, grid, dim3(kThreads),
+                      TcCfg<128, 128>::SMEM, s, L);
     case 2:
-      return launch_k(tc_mode_kernel<64, 64, PAIR, false>, grid, dim3(kThreads), TcCfg<64, 64>::SMEM, s, L);
+      return launch_k(tc_mode_kernel<64, 64, PAIR, false, kFmtBF16, IND>, grid, dim3(kThreads),
+                      TcCfg<64, 64>::SMEM, s, L);
     default:
       return cudaErrorInvalidValue;
   }
@@ -2101,7 +2129,7 @@ int xchg_clusters(int v) {
 // pair: the launch's units are (u, v) pairs (the fused stage-1 epilogue).
 // A pair-variant launch: clusters of two CTAs, at most `clusters` of them
 // (the number that fit on the GPU at once).
-template <int SW>
+template <int SW, bool IND = false>
 cudaError_t launch_pair(int clusters, cudaStream_t s, const TcLaunch& L) {
   const int nc = L.nunits < clusters ? L.nunits : clusters;
   cudaLaunchConfig_t cfg = {};
@@ -2118,7 +2146,7 @@ cudaError_t launch_pair(int clusters, cudaStream_t s, const TcLaunch& L) {
   at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = pdl_enabled() ? 2 : 1;
-  return cudaLaunchKernelEx(&cfg, tc_pair_kernel<SW>, L);
+  return cudaLaunchKernelEx(&cfg, tc_pair_kernel<SW, IND>, L);
 }
 
 // Clusters of the pair kernel that can be resident at once.
@@ -2151,11 +2179,17 @@ int pair_clusters(int variant) {
 
 // pair: the launch's units are (u, v) pairs (the fused stage-1 epilogue).
 // slots: resident CTAs (one-CTA variants) or clusters (pair variants).
-cudaError_t launch_tc(int v, int slots, cudaStream_t s, const TcLaunch& L, bool pair) {
+// ind: the pass accumulates the step's indicators.
+cudaError_t launch_tc(int v, int slots, cudaStream_t s, const TcLaunch& L, bool pair, bool ind) {
   if (L.nunits <= 0) return cudaSuccess;
-  if (kVariants[v].cta2)
+  if (kVariants[v].cta2) {
+    if (ind)
+      return kVariants[v].sw == 64 ? launch_pair<64, true>(slots, s, L)
+                                   : launch_pair<128, true>(slots, s, L);
     return kVariants[v].sw == 64 ? launch_pair<64>(slots, s, L) : launch_pair<128>(slots, s, L);
+  }
   dim3 grid((unsigned)(L.nunits < slots ? L.nunits : slots));
+  if (ind) return launch_tc_t<false, true>(v, grid, s, L);
   return pair ? launch_tc_t<true>(v, grid, s, L) : launch_tc_t<false>(v, grid, s, L);
 }
 
@@ -2223,7 +2257,7 @@ struct TcState {
   void* bound_v;
   // compensated state: low-order words per component [N], valid for the
   // state pair (comp_u, comp_v); null when the plan carries a plain state.
-  // comp: 0 plain, 1 restarted at every call, 2 carried across calls
+  // comp: 0 plain; 2 compensated (hi + lo state, double-float reactions)
   int comp;
   float* lo[2];
   void* comp_u;
@@ -2423,6 +2457,16 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   TcCfg<128, 128, kFmtTF32>::SMEM)) != cudaSuccess)
       return e;
+    if ((e = cudaFuncSetAttribute(tc_mode_kernel<128, 128, false, false, kFmtTF32, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  TcCfg<128, 128, kFmtTF32>::SMEM)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(rhs3_ring_kernel<kFmtBF16, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmem)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(rhs3_ring_kernel<kFmtTF32, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmem)) != cudaSuccess)
+      return e;
     if ((e = cudaFuncSetAttribute(rhs3_ring_kernel<kFmtBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kRingSmem)) != cudaSuccess)
       return e;
@@ -2607,10 +2651,10 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
 // descriptors are host copies passed by value in every launch, so binding
 // neither copies to the device nor synchronises.  A no-op when already bound.
 // Start of a stepping call on (u, v).  The low-order words of a
-// compensated state restart at zero (enqueued on s) at every call (comp 1),
-// or when the call steps another pair than the one they belong to (comp 2).
+// compensated state restart at zero (enqueued on s) when the call steps
+// another pair than the one they belong to.
 static cudaError_t comp_own(TcState* S, void* u, void* v, cudaStream_t s) {
-  if (!S->comp || (S->comp == 2 && S->comp_u == u && S->comp_v == v)) return cudaSuccess;
+  if (!S->comp || (S->comp_u == u && S->comp_v == v)) return cudaSuccess;
   for (int c = 0; c < 2; ++c) {
     cudaError_t e = cudaMemsetAsync(S->lo[c], 0, sizeof(float) * S->N, s);
     if (e != cudaSuccess) return e;
@@ -2664,6 +2708,8 @@ struct GroupStep {
   int units[16];
   int pair[16];             // per pass: units are (u, v) pairs
   int xchg[16];             // per pass: kStage1X (clusters of two)
+  int ind[16];              // per pass: accumulates the step's indicators
+  int df;                   // reactions in double-float (ADR_STATE_COMPENSATED)
   int xslots;               // resident clusters of the exchanging kernel
   PwLaunch rhs, flat;       // stencil blocks; flat pointwise blocks
   int rhs_blocks, flat_blocks;
@@ -2683,24 +2729,29 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
         e = timed_kernel(ctl, KC_RHS, N * 2.0 * (6.0 * G.d + 10.0), N * (8.0 + 12.0), [&] {
           PwLaunch R = G.rhs;
           R.err = G.err;
+          const dim3 gr(G.rhs_blocks), bl(kPwThreads);
           if (G.fmt == kFmtTF32) {
             if (G.d == 3)
-              return launch_k(rhs3_ring_kernel<kFmtTF32>, dim3(G.rhs_blocks), dim3(kPwThreads),
-                              kRingSmem, st, R);
-            return launch_k(rhs_pieces_kernel<kZB2, kFmtTF32>, dim3(G.rhs_blocks), dim3(kPwThreads),
-                            0, st, R);
+              return G.df ? launch_k(rhs3_ring_kernel<kFmtTF32, true>, gr, bl, kRingSmem, st, R)
+                          : launch_k(rhs3_ring_kernel<kFmtTF32>, gr, bl, kRingSmem, st, R);
+            return G.df ? launch_k(rhs_pieces_kernel<kZB2, kFmtTF32, true>, gr, bl, 0, st, R)
+                        : launch_k(rhs_pieces_kernel<kZB2, kFmtTF32>, gr, bl, 0, st, R);
           }
           if (G.d == 3)
-            return launch_k(rhs3_ring_kernel<>, dim3(G.rhs_blocks), dim3(kPwThreads), kRingSmem, st, R);
-          return launch_k(rhs_pieces_kernel<kZB2>, dim3(G.rhs_blocks), dim3(kPwThreads), 0, st, R);
+            return G.df ? launch_k(rhs3_ring_kernel<kFmtBF16, true>, gr, bl, kRingSmem, st, R)
+                        : launch_k(rhs3_ring_kernel<>, gr, bl, kRingSmem, st, R);
+          return G.df ? launch_k(rhs_pieces_kernel<kZB2, kFmtBF16, true>, gr, bl, 0, st, R)
+                      : launch_k(rhs_pieces_kernel<kZB2>, gr, bl, 0, st, R);
         });
         break;
       case kOpRdiff:
         e = timed_kernel(ctl, KC_RDIFF, N * 2.0 * 12.0, N * (16.0 + 12.0), [&] {
+          const dim3 gr(G.flat_blocks), bl(kPwThreads);
           if (G.fmt == kFmtTF32)
-            return launch_k(rdiff_pieces_kernel<kFmtTF32>, dim3(G.flat_blocks), dim3(kPwThreads), 0,
-                            st, G.flat);
-          return launch_k(rdiff_pieces_kernel<>, dim3(G.flat_blocks), dim3(kPwThreads), 0, st, G.flat);
+            return G.df ? launch_k(rdiff_pieces_kernel<kFmtTF32, true>, gr, bl, 0, st, G.flat)
+                        : launch_k(rdiff_pieces_kernel<kFmtTF32>, gr, bl, 0, st, G.flat);
+          return G.df ? launch_k(rdiff_pieces_kernel<kFmtBF16, true>, gr, bl, 0, st, G.flat)
+                      : launch_k(rdiff_pieces_kernel<>, gr, bl, 0, st, G.flat);
         });
         break;
       case kOpLawsonPre:
@@ -2738,10 +2789,14 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
                            if (G.xchg[p]) return launch_xchg(G.variant, G.xslots, st, L);
                            if (G.fmt == kFmtTF32) {
                              dim3 grid((unsigned)(L.nunits < G.num_sms ? L.nunits : G.num_sms));
+                             if (G.ind[p])
+                               return launch_k(tc_mode_kernel<128, 128, false, false, kFmtTF32, true>,
+                                               grid, dim3(kThreads), TcCfg<128, 128, kFmtTF32>::SMEM,
+                                               st, L);
                              return launch_k(tc_mode_kernel<128, 128, false, false, kFmtTF32>, grid,
                                              dim3(kThreads), TcCfg<128, 128, kFmtTF32>::SMEM, st, L);
                            }
-                           return launch_tc(G.variant, G.num_sms, st, L, G.pair[p] != 0);
+                           return launch_tc(G.variant, G.num_sms, st, L, G.pair[p] != 0, G.ind[p] != 0);
                          });
       } break;
       default:
@@ -2772,6 +2827,7 @@ static void fill_ops(GroupStep& G, const TcState* S) {
   }
   G.xslots = S->xslots;
   G.fmt = S->fmt;
+  G.df = S->comp == 2;
 }
 
 cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
@@ -2789,6 +2845,7 @@ cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
   G.ustart = nullptr;
   for (int p = 0; p < G.np; ++p) {
     G.units[p] = S->units[p];
+    G.ind[p] = S->h_desc[p].ind != nullptr;
     pass_work(S, S->passes[p], G.flops[p], G.bytes[p]);
   }
   memset(&G.rhs, 0, sizeof(G.rhs));
@@ -2828,6 +2885,7 @@ cudaError_t tc_time_passes(TcOperands* t, adr_plan_s* P, void* u, void* v, int r
   G.hdesc = S->h_desc.data();
   for (int p = 0; p < G.np; ++p) {
     G.units[p] = S->units[p];
+    G.ind[p] = S->h_desc[p].ind != nullptr;
     pass_work(S, S->passes[p], G.flops[p], G.bytes[p]);
   }
   G.err = S->err;
@@ -2953,6 +3011,7 @@ struct adr_batch_s {
   int rhs_blocks, rdiff_blocks;
   double flops[8], bytes[8], pw_n;
   std::vector<void*> bound_u, bound_v;
+  int ind_pass[8];      // per pass: some solve of the binding has indicators on
   // CUDA graph of kBatchChunk steps
   cudaStream_t cap;
   cudaGraphExec_t gexec;
@@ -3098,6 +3157,7 @@ static bool same_sequence(const adr_plan_s* a, const adr_plan_s* b) {
   if (a->prec != b->prec || (a->prec != ADR_BF16X3 && a->prec != ADR_TF32X3) || !A || !S)
     return false;
   if (S->d != A->d || S->variant != A->variant || S->fmt != A->fmt || S->scheme != A->scheme ||
+      (S->comp == 2) != (A->comp == 2) ||
       S->passes.size() != A->passes.size() || S->ops.size() != A->ops.size())
     return false;
   for (size_t p = 0; p < S->passes.size(); ++p)
@@ -3283,6 +3343,10 @@ static cudaError_t batch_bind(adr_batch B, void* const* u, void* const* v) {
     cudaError_t e = make_pw(S, P, (float*)u[i], (float*)v[i], &hp[i], (double)S->N / B->pw_n);
     if (e != cudaSuccess) return e;
   }
+  for (int p = 0; p < B->np; ++p) {
+    B->ind_pass[p] = 0;
+    for (int i = 0; i < S_; ++i) B->ind_pass[p] |= hd[(size_t)p * S_ + i].ind != nullptr;
+  }
   cudaError_t e = g_upload_ring.upload(B->d_desc, hd.data(), sizeof(TcPassDesc) * hd.size(),
                                        B->ctl->stream);
   if (e == cudaSuccess)
@@ -3315,6 +3379,7 @@ static cudaError_t batch_step_direct(adr_batch B, int64_t nsteps) {
     G.units[p] = B->units[p];
     G.flops[p] = B->flops[p];
     G.bytes[p] = B->bytes[p];
+    G.ind[p] = B->ind_pass[p];
   }
   memset(&G.rhs, 0, sizeof(G.rhs));
   G.rhs.desc = B->d_pw;

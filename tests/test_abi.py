@@ -109,9 +109,10 @@ def test_plan_bytes_host_only(adr):
     sb64, _ = adr.plan_bytes(wl.schnakenberg_64())
     assert sb64 == 2 * 64 * 64 * 8
     # a compensated state adds one FP32 word per point and component
-    _, c_auto = adr.plan_bytes(wl.fhn_1024(precision=wl.BF16X3))
+    _, c_comp = adr.plan_bytes(wl.fhn_1024(precision=wl.BF16X3).replace(state=wl.STATE_COMPENSATED))
     _, c_plain = adr.plan_bytes(wl.fhn_1024(precision=wl.BF16X3).replace(state=wl.STATE_PLAIN))
-    assert c_auto - c_plain == 2 * 1024 * 1024 * 4
+    _, c_auto = adr.plan_bytes(wl.fhn_1024(precision=wl.BF16X3))
+    assert c_comp - c_plain == 2 * 1024 * 1024 * 4 and c_auto == c_plain
 
 
 def test_selftest_limits_checked_on_the_host(adr):

@@ -71,27 +71,32 @@ def _run(adr, p, precision):
 
 
 def test_fhn_1024_500_steps_against_oracle(adr, refs):
-    """The headline workload: BF16x3 split products (compensated state) and
-    the plain FP32 SIMT form, both against the oracle over all 500 steps; the
-    split form is at least as accurate as plain FP32 (within 1.5x)."""
+    """The headline workload: BF16x3 split products (the plain and the
+    compensated state) and the plain FP32 SIMT form, all against the oracle
+    over the 500 steps; the split form is at least as accurate as plain FP32
+    (within 1.5x)."""
     p = wl.fhn_1024()
+    Uc, Vc = _run(adr, p.replace(state=wl.STATE_COMPENSATED), wl.BF16X3)
     Ub, Vb = _run(adr, p, wl.BF16X3)
     Uf, Vf = _run(adr, p, wl.FP32)
     Ur, Vr = refs["fhn1024"].result()
     eb = oracle.max_rel_err(Ub, Vb, Ur, Vr)
+    ec = oracle.max_rel_err(Uc, Vc, Ur, Vr)
     ef = oracle.max_rel_err(Uf, Vf, Ur, Vr)
-    print(f"fhn1024 500 steps: bf16x3 {eb:.3e}, fp32 {ef:.3e}")
-    assert eb <= TOL, (eb, ef)
+    print(f"fhn1024 500 steps: bf16x3 {eb:.3e}, bf16x3 compensated {ec:.3e}, fp32 {ef:.3e}")
+    assert eb <= TOL and ec <= TOL, (eb, ec, ef)
     assert eb <= 1.5 * ef, (eb, ef)
 
 
 def test_brusselator_256_100_steps_against_oracle(adr, refs):
     p = wl.brusselator_256()
     Ub, Vb = _run(adr, p, wl.BF16X3)
+    Uc, Vc = _run(adr, p.replace(state=wl.STATE_COMPENSATED), wl.BF16X3)
     Ur, Vr = refs["bruss256"].result()
     eb = oracle.max_rel_err(Ub, Vb, Ur, Vr)
-    print(f"bruss256 100 steps: bf16x3 {eb:.3e}")
-    assert eb <= TOL, eb
+    ec = oracle.max_rel_err(Uc, Vc, Ur, Vr)
+    print(f"bruss256 100 steps: bf16x3 {eb:.3e}, bf16x3 compensated {ec:.3e}")
+    assert eb <= TOL and ec <= TOL, (eb, ec)
 
 
 def test_batch_512_sample_against_oracle(adr, refs):
