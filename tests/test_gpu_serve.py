@@ -63,7 +63,7 @@ def small_requests(count=10, seed=9):
 @pytest.mark.parametrize("budget_mb", [100000, 8])
 def test_served_results_equal_alone(adr, budget_mb):
     import torch
-    from paper_2307_10684_gb300.serve import Server
+    from paper_2307_10684_gb300.serve import Server, served_problem
     reqs = small_requests()
     srv = Server(budget_bytes=budget_mb * 2**20, chunk=16, keep_results=True)
     res = srv.run(reqs)
@@ -75,7 +75,10 @@ def test_served_results_equal_alone(adr, budget_mb):
         u0, v0 = req.init()
         u = torch.tensor(u0, device="cuda")
         v = torch.tensor(v0, device="cuda")
-        with adr.Plan(req.problem) as plan:
+        # alone: the same problem as the server plans it (compensated state
+        # carried across its ticks), stepped in one call
+        assert served_problem(req.problem).state == wl.STATE_COMPENSATED
+        with adr.Plan(served_problem(req.problem)) as plan:
             plan.step(u, v, req.nsteps)
         torch.cuda.synchronize()
         assert torch.equal(u.cpu(), out.u) and torch.equal(v.cpu(), out.v), req.rid
