@@ -97,6 +97,10 @@ def profiled_traffic(workload_name: str, kernel: int, profiles: str = None):
     return None
 
 
+# workload name -> the key of its committed capture summary (profiles/tc_mode_<key>.md)
+PROFILE_KEY = {"fhn2d_adv_1024": "fhn1024", "brusselator3d_adv_256": "bruss256"}
+
+
 def workload(name: str, precision: int):
     if name == "fhn1024":
         return wl.fhn_1024(precision=precision)
@@ -514,7 +518,9 @@ def run_single(args, p, nts: int, R, with_compare: bool, oracle):
     in_step = None
     if dom == "mode_product_tc":
         used = kernel if kernel >= 0 else (4 if npts >= 1000000 else 0)  # the plan default
-        traffic = profiled_traffic(p.name, used) if p.scheme == wl.ETD2RKDS else None
+        traffic = (profiled_traffic(PROFILE_KEY.get(p.name, p.name), used)
+                   if p.scheme == wl.ETD2RKDS and int(getattr(p, "state", 0)) != wl.STATE_COMPENSATED
+                   else None)
         ms_launch, per_step = plan.time_mode_products(u, v, reps=64)
         roof = mode_product_roofline(p, prec, ms_launch, per_step, peaks, peak_src, traffic)
         roof["share_of_kernel_time"] = kd["ms"] / total_kernel_ms
