@@ -52,7 +52,9 @@ struct PointwiseArgsT {
   int d;
   int64_t n[3];
   int64_t N;
-  TridiagT<T> A[2][3];  // [component][mu]
+  TridiagT<T> A[2][3];    // [component][mu]
+  TridiagT<T> Alo[2][3];  // low-order parts: A + Alo is the double-precision operator
+                          // (zero when T is double)
   ReactionT<T> rx;
 };
 using PointwiseArgs = PointwiseArgsT<double>;
@@ -64,9 +66,14 @@ inline PointwiseArgsT<T> cast_args(const PointwiseArgs& a) {
   r.N = a.N;
   for (int m = 0; m < 3; ++m) r.n[m] = a.n[m];
   for (int c = 0; c < 2; ++c)
-    for (int m = 0; m < 3; ++m)
-      r.A[c][m] = TridiagT<T>{(T)a.A[c][m].lo, (T)a.A[c][m].di, (T)a.A[c][m].up,
-                              (T)a.A[c][m].b0, (T)a.A[c][m].bn};
+    for (int m = 0; m < 3; ++m) {
+      const Tridiag& x = a.A[c][m];
+      r.A[c][m] = TridiagT<T>{(T)x.lo, (T)x.di, (T)x.up, (T)x.b0, (T)x.bn};
+      const TridiagT<T>& h = r.A[c][m];
+      r.Alo[c][m] = TridiagT<T>{(T)(x.lo - (double)h.lo), (T)(x.di - (double)h.di),
+                                (T)(x.up - (double)h.up), (T)(x.b0 - (double)h.b0),
+                                (T)(x.bn - (double)h.bn)};
+    }
   r.rx.model = a.rx.model;
   for (int i = 0; i < 16; ++i) {
     r.rx.p[i] = (T)a.rx.p[i];

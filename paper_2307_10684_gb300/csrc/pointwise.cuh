@@ -83,18 +83,59 @@ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
 }
 
 // The reaction of Eq. 1 evaluated in double-float from single-precision
-// state values, rounded once to FP32 (parameters as p + plo).
-__device__ __forceinline__ void react_df(const ReactionT<float>& rx, float u, float v, float& gu,
-                                         float& gv) {
+// state values (parameters as p + plo).
+__device__ __forceinline__ void react_dfd(const ReactionT<float>& rx, float u, float v, dfloat& gu,
+                                          dfloat& gv) {
   ReactionT<dfloat> r;
   r.model = rx.model;
 #pragma unroll
   for (int i = 0; i < 16; ++i) r.p[i] = dfloat(rx.p[i], rx.plo[i]);
+  react<dfloat>(r, dfloat(u), dfloat(v), gu, gv);
+}
+
+// The same, rounded once to FP32.
+__device__ __forceinline__ void react_df(const ReactionT<float>& rx, float u, float v, float& gu,
+                                         float& gv) {
   dfloat a, b;
-  react<dfloat>(r, dfloat(u), dfloat(v), a, b);
+  react_dfd(rx, u, v, a, b);
   gu = __fadd_rn(a.h, a.l);
   gv = __fadd_rn(b.h, b.l);
 }
+
+// x - y exactly, as a double-float.
+__device__ __forceinline__ dfloat df_diff(float x, float y) { return df_two_sum(x, -y); }
+
+// One direction of the stencil of Eq. 6 in double-float, coefficients as
+// hi + lo (the FP64 operator): interior rows lo (x- - x) + up (x+ - x),
+// Neumann rows b0 (x+ - x) and bn (x- - x).  The stencil's terms can be
+// large next to their sum (delta / h^2 of 10^5 on fine grids), so the
+// accurate mode sums them without intermediate rounding.
+__device__ __forceinline__ dfloat dtri_in(float xm, float xc, float xp, dfloat lo, dfloat up) {
+  return lo * df_diff(xm, xc) + up * df_diff(xp, xc);
+}
+__device__ __forceinline__ dfloat dtri_dir(float xm, float xc, float xp, int i, int n, dfloat lo,
+                                           dfloat up, dfloat b0, dfloat bn) {
+  if (i == 0) return b0 * df_diff(xp, xc);
+  if (i == n - 1) return bn * df_diff(xm, xc);
+  return dtri_in(xm, xc, xp, lo, up);
+}
+__device__ __forceinline__ dfloat dtri_x4(int j, float xm, float xc, float xp, int i, int n,
+                                          dfloat lo, dfloat up, dfloat b0, dfloat bn) {
+  if (j == 0 && i == 0) return b0 * df_diff(xp, xc);
+  if (j == 3 && i == n - 1) return bn * df_diff(xm, xc);
+  return dtri_in(xm, xc, xp, lo, up);
+}
+
+// The tridiagonal coefficients of one component on one axis as double-floats.
+struct CoefDF {
+  dfloat lo, up, b0, bn;
+};
+__device__ __forceinline__ CoefDF coef_df(const TridiagT<float>& A, const TridiagT<float>& Al) {
+  return CoefDF{dfloat(A.lo, Al.lo), dfloat(A.up, Al.up), dfloat(A.b0, Al.b0), dfloat(A.bn, Al.bn)};
+}
+
+// Round a double-float to FP32.
+__device__ __forceinline__ float df_round(dfloat x) { return __fadd_rn(x.h, x.l); }
 
 // D = G(u2, v2) - G(u0, v0) (the stage-2 reaction difference of Eq. 11),
 // both reactions and the difference in double-float, rounded once.

@@ -1617,17 +1617,29 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs_pieces_kernel(const __grid_
         const float cu = el(uc, j), cv = el(vc, j);
         const float lu = j == 0 ? ul : el(uc, j - 1), lv = j == 0 ? vl : el(vc, j - 1);
         const float ru = j == 3 ? ur : el(uc, j + 1), rv = j == 3 ? vr : el(vc, j + 1);
-        float ku = tri_x4(j, lu, cu, ru, xi, nx, cxu.lo, cxu.up, cxu.b0, cxu.bn);
-        float kv = tri_x4(j, lv, cv, rv, xi, nx, cxv.lo, cxv.up, cxv.b0, cxv.bn);
-        ku += tri_dir(el(pu[q], j), cu, el(pu[q + 2], j), zq, nz, czu.lo, czu.up, czu.b0, czu.bn);
-        kv += tri_dir(el(pv[q], j), cv, el(pv[q + 2], j), zq, nz, czv.lo, czv.up, czv.b0, czv.bn);
-        float gu, gv;
-        if constexpr (DF)
-          react_df(rx, cu, cv, gu, gv);
-        else
+        if constexpr (DF) {  // accurate mode: stencil and reaction in double-float, one rounding
+          const CoefDF dxu = coef_df(dp->a.A[0][0], dp->a.Alo[0][0]);
+          const CoefDF dxv = coef_df(dp->a.A[1][0], dp->a.Alo[1][0]);
+          const CoefDF dzu = coef_df(dp->a.A[0][1], dp->a.Alo[0][1]);
+          const CoefDF dzv = coef_df(dp->a.A[1][1], dp->a.Alo[1][1]);
+          dfloat gu, gv;
+          react_dfd(rx, cu, cv, gu, gv);
+          ou[j] = df_round(dtri_x4(j, lu, cu, ru, xi, nx, dxu.lo, dxu.up, dxu.b0, dxu.bn) +
+                           dtri_dir(el(pu[q], j), cu, el(pu[q + 2], j), zq, nz, dzu.lo, dzu.up,
+                                    dzu.b0, dzu.bn) + gu);
+          ov[j] = df_round(dtri_x4(j, lv, cv, rv, xi, nx, dxv.lo, dxv.up, dxv.b0, dxv.bn) +
+                           dtri_dir(el(pv[q], j), cv, el(pv[q + 2], j), zq, nz, dzv.lo, dzv.up,
+                                    dzv.b0, dzv.bn) + gv);
+        } else {
+          float ku = tri_x4(j, lu, cu, ru, xi, nx, cxu.lo, cxu.up, cxu.b0, cxu.bn);
+          float kv = tri_x4(j, lv, cv, rv, xi, nx, cxv.lo, cxv.up, cxv.b0, cxv.bn);
+          ku += tri_dir(el(pu[q], j), cu, el(pu[q + 2], j), zq, nz, czu.lo, czu.up, czu.b0, czu.bn);
+          kv += tri_dir(el(pv[q], j), cv, el(pv[q + 2], j), zq, nz, czv.lo, czv.up, czv.b0, czv.bn);
+          float gu, gv;
           react<float>(rx, cu, cv, gu, gv);
-        ou[j] = ku + gu;
-        ov[j] = kv + gv;
+          ou[j] = ku + gu;
+          ov[j] = kv + gv;
+        }
       }
       if (act) {
         const int64_t idx = (int64_t)zq * sz + col;
@@ -1765,26 +1777,42 @@ __global__ void __launch_bounds__(kPwThreads, 2) rhs3_ring_kernel(const __grid_c
         const float cu = el(uc, j), cv = el(vc, j);
         const float lu = j == 0 ? ul : el(uc, j - 1), lv = j == 0 ? vl : el(vc, j - 1);
         const float ru = j == 3 ? ur : el(uc, j + 1), rv = j == 3 ? vr : el(vc, j + 1);
-        float ku = tri_x4(j, lu, cu, ru, xi, nx, cxu.lo, cxu.up, cxu.b0, cxu.bn);
-        float kv = tri_x4(j, lv, cv, rv, xi, nx, cxv.lo, cxv.up, cxv.b0, cxv.bn);
-        if (yzin) {
-          ku += tri_in(el(uym, j), cu, el(uyp, j), cyu.lo, cyu.up);
-          kv += tri_in(el(vym, j), cv, el(vyp, j), cyv.lo, cyv.up);
-          ku += tri_in(el(uzm, j), cu, el(uzp, j), czu.lo, czu.up);
-          kv += tri_in(el(vzm, j), cv, el(vzp, j), czv.lo, czv.up);
+        if constexpr (DF) {  // accurate mode: stencil and reaction in double-float, one rounding
+          const CoefDF dxu = coef_df(dp->a.A[0][0], dp->a.Alo[0][0]);
+          const CoefDF dxv = coef_df(dp->a.A[1][0], dp->a.Alo[1][0]);
+          const CoefDF dyu = coef_df(dp->a.A[0][1], dp->a.Alo[0][1]);
+          const CoefDF dyv = coef_df(dp->a.A[1][1], dp->a.Alo[1][1]);
+          const CoefDF dzu = coef_df(dp->a.A[0][2], dp->a.Alo[0][2]);
+          const CoefDF dzv = coef_df(dp->a.A[1][2], dp->a.Alo[1][2]);
+          dfloat gu, gv;
+          react_dfd(rx, cu, cv, gu, gv);
+          const dfloat ku = dtri_x4(j, lu, cu, ru, xi, nx, dxu.lo, dxu.up, dxu.b0, dxu.bn) +
+                            dtri_dir(el(uym, j), cu, el(uyp, j), y, ny, dyu.lo, dyu.up, dyu.b0, dyu.bn) +
+                            dtri_dir(el(uzm, j), cu, el(uzp, j), z, nz, dzu.lo, dzu.up, dzu.b0, dzu.bn);
+          const dfloat kv = dtri_x4(j, lv, cv, rv, xi, nx, dxv.lo, dxv.up, dxv.b0, dxv.bn) +
+                            dtri_dir(el(vym, j), cv, el(vyp, j), y, ny, dyv.lo, dyv.up, dyv.b0, dyv.bn) +
+                            dtri_dir(el(vzm, j), cv, el(vzp, j), z, nz, dzv.lo, dzv.up, dzv.b0, dzv.bn);
+          ou[j] = df_round(ku + gu);
+          ov[j] = df_round(kv + gv);
         } else {
-          ku += tri_dir(el(uym, j), cu, el(uyp, j), y, ny, cyu.lo, cyu.up, cyu.b0, cyu.bn);
-          kv += tri_dir(el(vym, j), cv, el(vyp, j), y, ny, cyv.lo, cyv.up, cyv.b0, cyv.bn);
-          ku += tri_dir(el(uzm, j), cu, el(uzp, j), z, nz, czu.lo, czu.up, czu.b0, czu.bn);
-          kv += tri_dir(el(vzm, j), cv, el(vzp, j), z, nz, czv.lo, czv.up, czv.b0, czv.bn);
-        }
-        float gu, gv;
-        if constexpr (DF)
-          react_df(rx, cu, cv, gu, gv);
-        else
+          float ku = tri_x4(j, lu, cu, ru, xi, nx, cxu.lo, cxu.up, cxu.b0, cxu.bn);
+          float kv = tri_x4(j, lv, cv, rv, xi, nx, cxv.lo, cxv.up, cxv.b0, cxv.bn);
+          if (yzin) {
+            ku += tri_in(el(uym, j), cu, el(uyp, j), cyu.lo, cyu.up);
+            kv += tri_in(el(vym, j), cv, el(vyp, j), cyv.lo, cyv.up);
+            ku += tri_in(el(uzm, j), cu, el(uzp, j), czu.lo, czu.up);
+            kv += tri_in(el(vzm, j), cv, el(vzp, j), czv.lo, czv.up);
+          } else {
+            ku += tri_dir(el(uym, j), cu, el(uyp, j), y, ny, cyu.lo, cyu.up, cyu.b0, cyu.bn);
+            kv += tri_dir(el(vym, j), cv, el(vyp, j), y, ny, cyv.lo, cyv.up, cyv.b0, cyv.bn);
+            ku += tri_dir(el(uzm, j), cu, el(uzp, j), z, nz, czu.lo, czu.up, czu.b0, czu.bn);
+            kv += tri_dir(el(vzm, j), cv, el(vzp, j), z, nz, czv.lo, czv.up, czv.b0, czv.bn);
+          }
+          float gu, gv;
           react<float>(rx, cu, cv, gu, gv);
-        ou[j] = ku + gu;
-        ov[j] = kv + gv;
+          ou[j] = ku + gu;
+          ov[j] = kv + gv;
+        }
       }
       if (act) {
         const int64_t idx = (int64_t)z * sz + (int64_t)y * sy + xl;

@@ -51,11 +51,7 @@ def _gpu(adr, p, u0, v0, nsteps, chunks=None):
     return u.double().cpu().numpy(), v.double().cpu().numpy()
 
 
-# served requests whose plain FP32-state error was above 1e-5: a 2D
-# Brusselator at b = 4.36 (Hopf-unstable), 991 steps, and a 3D Schnakenberg
-# 64^3, 634 steps
-@pytest.mark.parametrize("rid", [60, 1180])
-def test_long_horizon_served_request_within_bound(adr, rid):
+def _served_errors(adr, rid):
     p = _served(rid).replace(precision=wl.BF16X3)
     u0, v0 = wl.initial_data(p)
     u0, v0 = wl.round_to(u0, wl.FP32), wl.round_to(v0, wl.FP32)
@@ -64,8 +60,26 @@ def test_long_horizon_served_request_within_bound(adr, rid):
     chunks = [32] * (p.nsteps // 32) + [p.nsteps % 32]
     Uc, Vc = _gpu(adr, p.replace(state=wl.STATE_COMPENSATED), u0, v0, p.nsteps, chunks)
     Up, Vp = _gpu(adr, p.replace(state=wl.STATE_PLAIN), u0, v0, p.nsteps)
-    ec = oracle.max_rel_err(Uc, Vc, Ur, Vr)
-    ep = oracle.max_rel_err(Up, Vp, Ur, Vr)
+    return oracle.max_rel_err(Uc, Vc, Ur, Vr), oracle.max_rel_err(Up, Vp, Ur, Vr)
+
+
+def test_turing_unstable_request_near_its_floor(adr):
+    """Served request 0: 3D Schnakenberg 96^3, gamma = 688, D_v/D_u = 16.9,
+    455 steps, Turing-unstable.  An FP64 solve from data perturbed by 2^-24
+    ends 9.0e-6 away (the floor any single-precision-class solve meets),
+    so 1e-5 is out of reach for single-precision products; the compensated
+    mode stays within a small factor of that floor, 5x closer than plain."""
+    ec, ep = _served_errors(adr, 0)
+    assert ec <= 4.0 * 9.0e-6, (ec, ep)
+    assert ep >= 4.0 * ec, (ec, ep)
+
+
+# served requests whose plain FP32-state error was above 1e-5: a 2D
+# Brusselator at b = 4.36 (Hopf-unstable), 991 steps, and a 3D Schnakenberg
+# 64^3, 634 steps
+@pytest.mark.parametrize("rid", [60, 1180])
+def test_long_horizon_served_request_within_bound(adr, rid):
+    ec, ep = _served_errors(adr, rid)
     assert ec <= TOL, (ec, ep)
     assert ep > 3.0 * ec, (ec, ep)  # the plain state is what misses the bound
 
