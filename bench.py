@@ -376,7 +376,8 @@ class OracleJobs:
         self.ex.shutdown(wait=True)
 
 
-def mode_product_roofline(p, prec, ms_launch: float, per_step: int, peaks, peak_src, traffic):
+def mode_product_roofline(p, prec, ms_launch: float, per_step: int, peaks, peak_src, traffic,
+                          computed_share: float = 1.0):
     """Roofline of the tensor-core mode-product launch, timed as it runs
     inside a step (adr_plan_time_mode_products), on the algorithmic work of
     the method per launch:
@@ -386,8 +387,10 @@ def mode_product_roofline(p, prec, ms_launch: float, per_step: int, peaks, peak_
              Tucker operator: 16 + 8/d B per point on average.
     The bound is the slower of the two at the measured peaks (dense BF16
     burst, HBM copy); `frac` is the algorithmic fraction.  The split-precision
-    form issues 6 (BF16x3) or 3 TF32 (= 6 BF16-rate) MMAs per algorithmic
-    product: `issued_tensor_frac` counts them."""
+    form issues 6 (BF16x3) or 3 TF32 (= 6 BF16-rate) MMAs per product it
+    computes, and computes `computed_share` of the dense products (each tile
+    contracts over the column support of its rows of phi, adr_plan_mode_product_macs):
+    `issued_tensor_frac` counts the MMAs actually issued."""
     d = p.d
     N = float(p.npoints)
     nmu = float(sum(p.n[:d])) / d
@@ -407,8 +410,9 @@ def mode_product_roofline(p, prec, ms_launch: float, per_step: int, peaks, peak_
                                  "dependent launch, no timing node between launches)",
               "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
               "tensor_frac_algorithmic": t_tc / avg_s, "hbm_frac_algorithmic": t_hbm / avg_s,
-              "issued_tensor_frac": issue * t_tc / avg_s,
+              "issued_tensor_frac": issue * computed_share * t_tc / avg_s,
               "issued_mmas_per_product": int(issue),
+              "computed_share_of_dense_products": computed_share,
               "launches_per_time_step": per_step}
     if t_tc >= t_hbm:
         return dict(common, bound="tensor", achieved=flops / avg_s / 1e12, peak=tc_peak / 1e12,
@@ -522,7 +526,9 @@ def run_single(args, p, nts: int, R, with_compare: bool, oracle):
                    if p.scheme == wl.ETD2RKDS and int(getattr(p, "state", 0)) != wl.STATE_COMPENSATED
                    else None)
         ms_launch, per_step = plan.time_mode_products(u, v, reps=64)
-        roof = mode_product_roofline(p, prec, ms_launch, per_step, peaks, peak_src, traffic)
+        dense_macs, computed_macs = plan.mode_product_macs()
+        roof = mode_product_roofline(p, prec, ms_launch, per_step, peaks, peak_src, traffic,
+                                     computed_macs / dense_macs)
         roof["share_of_kernel_time"] = kd["ms"] / total_kernel_ms
         step_ms = tot_ms / args.steps / nts
         in_step = {"mode_product_ms_per_time_step": per_step * ms_launch,

@@ -282,6 +282,22 @@ adr_status adr_plan_matrix(adr_plan plan, int which, int component, int mu, doub
 adr_status adr_plan_time_mode_products(adr_plan plan, void* u, void* v, int32_t reps,
                                        double* ms_per_launch, int32_t* launches_per_step);
 
+/* Measurement aid: multiply-adds of the mode products of one time step.
+ * *dense counts them as the Tucker operators of Eq. 5 state them: per
+ * component, two operators of d full contractions, N n_mu multiply-adds
+ * each (4 N sum_mu n_mu for two components).  *computed counts what the
+ * kernels run.  On the tensor-core path every 128-row group of
+ * phi(tau A_mu) contracts only over the column support of its rows: the
+ * union of each row's narrowest column range whose left-out entries weigh
+ * at most 2^-40 of the row's absolute sum (from the FP64 matrix at plan
+ * time), widened to multiples of 64 columns, the same for every kernel
+ * choice.  The left-out part of a product is then below
+ * 2^-40 max|x| sum_j |phi_ij| per row, far below the products' own 2^-24
+ * rounding.  (The environment variable ADR_KSUPPORT=0, read at plan
+ * creation, runs every tile over all of K.)  Other plans: *computed =
+ * *dense.  Host-only, never fails on a valid plan. */
+adr_status adr_plan_mode_product_macs(adr_plan plan, double* dense, double* computed);
+
 /* Counters of a plan since creation (or the last reset). */
 typedef struct {
   int64_t launches;        /* kernels launched by adr_step / adr_solve     */

@@ -144,6 +144,15 @@ class Plan:
                                                      ctypes.byref(ms), ctypes.byref(n)))
         return float(ms.value), int(n.value)
 
+    def mode_product_macs(self):
+        """adr_plan_mode_product_macs: (dense, computed) multiply-adds of
+        one step's mode products."""
+        dense = ctypes.c_double()
+        computed = ctypes.c_double()
+        _abi.check(lib().adr_plan_mode_product_macs(self._p, ctypes.byref(dense),
+                                                    ctypes.byref(computed)))
+        return float(dense.value), float(computed.value)
+
     def set_indicators(self, enable: bool = True):
         """adr_plan_set_indicators: per-step indicators of Sec. 4 fused into
         the last product of every step."""

@@ -75,6 +75,8 @@ SIGNATURES = {
                           ctypes.POINTER(c_int64), ctypes.POINTER(c_double)]),
     "adr_plan_time_mode_products": (c_int32, [AdrPlan, c_void_p, c_void_p, c_int32,
                                               ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
+    "adr_plan_mode_product_macs": (c_int32, [AdrPlan, ctypes.POINTER(c_double),
+                                             ctypes.POINTER(c_double)]),
     "adr_solve": (c_int32, [AdrPlan, c_void_p, c_void_p, c_void_p, c_void_p, c_int64]),
     "adr_plan_bytes": (c_int32, [ctypes.POINTER(AdrProblem), ctypes.POINTER(ctypes.c_size_t),
                                  ctypes.POINTER(ctypes.c_size_t)]),

@@ -262,6 +262,8 @@ cudaError_t tc_indicator_log(TcOperands* t, cudaStream_t s, double* out, int64_t
                              int64_t* count);
 cudaError_t tc_time_passes(TcOperands* t, adr_plan_s* P, void* u, void* v, int reps, float* ms,
                            int* passes);
+// multiply-adds of one step's mode products: dense, and as the tiles run them
+void tc_mode_macs(const TcOperands* t, double* dense, double* computed);
 
 inline cudaEvent_t pool_event(adr_plan_s* P) {
   if (P->event_next < P->event_pool.size()) return P->event_pool[P->event_next++];

@@ -567,6 +567,21 @@ extern "C" adr_status adr_plan_time_mode_products(adr_plan plan, void* u, void* 
   return ADR_OK;
 }
 
+extern "C" adr_status adr_plan_mode_product_macs(adr_plan plan, double* dense, double* computed) {
+  if (!plan || !dense || !computed) return fail(ADR_EINVAL, "adr_plan_mode_product_macs: bad argument");
+  if (!plan->gen && (plan->prec == ADR_BF16X3 || plan->prec == ADR_TF32X3)) {
+    tc_mode_macs(&plan->tc, dense, computed);
+    return ADR_OK;
+  }
+  // FP32 / FP64 products and general plans: two Tucker operators per
+  // component and step, each a full contraction along every direction
+  const int m = plan->gen ? general_components(plan) : 2;
+  double sum_n = 0.0;
+  for (int mu = 0; mu < plan->d; ++mu) sum_n += (double)plan->n[mu];
+  *dense = *computed = 2.0 * m * (double)plan->N * sum_n;
+  return ADR_OK;
+}
+
 static bool tc_etd2rkds(adr_plan P) {
   return (P->prec == ADR_BF16X3 || P->prec == ADR_TF32X3) && P->scheme == ADR_ETD2RKDS;
 }

@@ -338,6 +338,8 @@ struct alignas(128) TcPassDesc {
   const float* base[2];     // FP32 base per component (kStage1, kAxpy)
   float* lo[2];             // kAxpy of a compensated state: low-order words, read and
                             // rewritten in place (null: plain FP32 update)
+  const int2* kband[2];     // per component: column support [lo, hi) of each 128-row group
+                            // of Phi (null: every tile runs the whole K)
   double* ind;              // last product of a step: indicator ring [ind_k][4] (null: off)
   const int64_t* ind_ctr;   // the step's slot: *ind_ctr % ind_k
   int ind_k;
@@ -499,6 +501,28 @@ __device__ __forceinline__ int find_segment(const int* __restrict__ start, int n
   return lo;
 }
 
+// K-blocks [kb0, kb1) that a tile of Phi rows starting at n0 contracts over.
+// The support table holds one column range per 128-row group of Phi, with
+// both ends on multiples of 64 (the end clipped to K); tiles of 64 or 128
+// rows (starting at multiples of their height) take their group's range.
+// Every kernel variant's K-block (32 or 64 values) divides 64, so all
+// variants accumulate each output over the same K values in the same order.
+// Without a table, all of K.  The table is plan data, so it may be read
+// before the programmatic dependency on the previous kernel is resolved.
+__device__ __forceinline__ void k_blocks(const TcPassDesc* d, int c, int n0, int bk, int& kb0,
+                                         int& kb1) {
+  const int nk = (d->K + bk - 1) / bk;
+  const int2* t = d->kband[c];
+  kb0 = 0;
+  kb1 = nk;
+  if (t == nullptr) return;
+  const int2 r = __ldg(t + (n0 >> 7));
+  if (r.x < r.y) {
+    kb0 = r.x / bk;
+    kb1 = min(nk, (r.y + bk - 1) / bk);
+  }
+}
+
 struct Unit {
   const TcPassDesc* d;
   int m0, n0, c_lo, c_hi;
@@ -632,7 +656,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
     bool waited = false;
     for (int u = blockIdx.x; u < L.nunits && !stop; u += gridDim.x) {
       const Unit w = decode_unit<BN>(L, u);
-      const int nk = (w.d->K + C::BK - 1) / C::BK;
       for (int comp = w.c_lo; comp < w.c_hi; ++comp) {
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&w.d->amap[comp]) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&w.d->bmap[comp]) : "memory");
@@ -640,7 +663,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
       for (int comp = w.c_lo; comp < w.c_hi && !stop; ++comp) {
         const CUtensorMap* ma = &w.d->amap[comp];
         const CUtensorMap* mb = &w.d->bmap[comp];
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        int kb0, kb1;
+        k_blocks(w.d, comp, w.n0, C::BK, kb0, kb1);
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
           const int s = g % C::STAGES;
           const uint32_t it = g / C::STAGES;
           if (*abort_v || (it > 0 && !mbar_wait(&empty[s], (it - 1) & 1))) {
@@ -680,10 +705,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
       }
       tc_fence_after();
       const Unit w = decode_unit<BN>(L, u);
-      const int nk = (w.d->K + C::BK - 1) / C::BK;
       for (int comp = w.c_lo; comp < w.c_hi && !stop; ++comp) {
         const uint32_t dt = tmem + (uint32_t)((slot * 2 + comp - w.c_lo) * BN);
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        int kb0, kb1;
+        k_blocks(w.d, comp, w.n0, C::BK, kb0, kb1);
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
           const int s = g % C::STAGES;
           if (!mbar_wait(&full[s], (g / C::STAGES) & 1)) {
             atomicCAS(L.err, 0, kErrTimeoutFull);
@@ -702,13 +728,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
             const uint64_t b1 = b0 + (uint64_t)(C::TILE_B >> 4);
             if constexpr (F == kFmtTF32) {
               // (lo, hi), (hi, lo), (hi, hi): the lo x lo term (2^-22) is dropped
-              mma_tf32<kColNone>(dt, a1, b0, idesc, (kb | kk) != 0);
+              mma_tf32<kColNone>(dt, a1, b0, idesc, (kb != kb0 || kk != 0));
               mma_tf32<kColFill>(dt, a0, b1, idesc, 1);
               mma_tf32<kColLast>(dt, a0, b0, idesc, 1);
             } else {
               const uint64_t a2 = a0 + (uint64_t)(2 * C::TILE_A >> 4);
               const uint64_t b2 = b0 + (uint64_t)(2 * C::TILE_B >> 4);
-              mma_bf16<kColNone>(dt, a2, b0, idesc, (kb | kk) != 0);
+              mma_bf16<kColNone>(dt, a2, b0, idesc, (kb != kb0 || kk != 0));
               mma_bf16<kColFill>(dt, a1, b1, idesc, 1);
               mma_bf16<kColLast>(dt, a1, b0, idesc, 1);
               mma_bf16<kColFill>(dt, a0, b2, idesc, 1);
@@ -1216,13 +1242,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
     bool stop = false, waited = false;
     for (int u = cid; u < L.nunits && !stop; u += ncl) {
       const Unit2 w = decode_unit2(L, u, BN);
-      const int nk = (w.d->K + C::BK - 1) / C::BK;
       const CUtensorMap* ma = &w.d->amap[w.c];
       const CUtensorMap* mb = &w.d->bmap[w.c];
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)ma) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mb) : "memory");
       const int ya = w.m0 + (int)rank * kBM, yb = w.n0 + (int)rank * (BN / 2);
-      for (int kb = 0; kb < nk; ++kb, ++g) {
+      int kb0, kb1;  // the same range in both CTAs: the whole tile's BN rows
+      k_blocks(w.d, w.c, w.n0, C::BK, kb0, kb1);
+      for (int kb = kb0; kb < kb1; ++kb, ++g) {
         const int s = g % C::STAGES;
         const uint32_t it = g / C::STAGES;
         if (*abort_v || (it > 0 && !mbar_wait(&empty[s], (it - 1) & 1))) {
@@ -1270,9 +1297,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
       }
       tc_fence_after();
       const Unit2 w = decode_unit2(L, u, BN);
-      const int nk = (w.d->K + C::BK - 1) / C::BK;
       const uint32_t dt = tmem + (uint32_t)(slot * BN);
-      for (int kb = 0; kb < nk; ++kb, ++g) {
+      int kb0, kb1;
+      k_blocks(w.d, w.c, w.n0, C::BK, kb0, kb1);
+      for (int kb = kb0; kb < kb1; ++kb, ++g) {
         const int s = g % C::STAGES;
         if (!mbar_wait(&full[s], (g / C::STAGES) & 1)) {
           atomicCAS(L.err, 0, kErrTimeoutFull);
@@ -1282,7 +1310,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
         }
         const uint64_t da = dA0 + (uint64_t)((s * C::STAGE) >> 4);
         const uint64_t db = da + (uint64_t)((kPieces * C::TILE_A) >> 4);
-        issue_stage<SW, C::TILE_A, C::TILE_B, true>(dt, da, db, idesc, kb != 0);
+        issue_stage<SW, C::TILE_A, C::TILE_B, true>(dt, da, db, idesc, kb != kb0);
         mma_commit_pair(&empty[s], 0x3);  // frees stage s in both CTAs
       }
       if (stop) break;
@@ -1977,6 +2005,84 @@ __global__ void split_matrix_tf32_kernel(const double* __restrict__ src, float* 
   }
 }
 
+// Column support of each 128-row group of an FP64 n x n matrix Phi
+// (row-major).  Row i keeps the narrowest column range [lo_i, hi_i) whose
+// left-out entries weigh at most drop * sum_j |Phi_ij|, half on each side:
+//   lo_i = max { l : sum_{j < l} |Phi_ij| <= t_i },
+//   hi_i = min { h : sum_{j >= h} |Phi_ij| <= t_i },   t_i = drop / 2 * sum_j |Phi_ij|.
+// A product restricted to the range then differs from the full one by at most
+// drop * max|x| * sum_j |Phi_ij| per row.  With drop < 1 the range is never
+// empty (the two left-out sums cannot cover the row); an all-zero row keeps
+// its diagonal entry.  band[g] = the union over the group's rows, widened to
+// multiples of 64 (the end clipped to n).  One block of kBandWarps warps per
+// group, one warp per row at a time.
+constexpr int kBandRows = 128, kBandWarps = 8;
+// Mass of a row of Phi a tile may leave out: 2^-40 of the row's absolute sum,
+// far below the 2^-24 relative rounding of the split products themselves.
+constexpr double kBandDrop = 9.094947017729282e-13;
+__device__ __forceinline__ double warp_incl_scan(double x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+__global__ void __launch_bounds__(32 * kBandWarps) band_support_kernel(
+    const double* __restrict__ A, int n, double drop, int2* __restrict__ band) {
+  __shared__ int s_lo, s_hi;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    s_lo = n;
+    s_hi = 0;
+  }
+  __syncthreads();
+  const int r_end = min(n, (int)(blockIdx.x + 1) * kBandRows);
+  for (int i = blockIdx.x * kBandRows + warp; i < r_end; i += kBandWarps) {
+    const double* row = A + (int64_t)i * n;
+    double tot = 0.0;
+    for (int j = lane; j < n; j += 32) tot += fabs(row[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    int lo = i, hi = i + 1;
+    if (tot > 0.0) {
+      const double t = 0.5 * drop * tot;
+      lo = n - 1;  // left prefix sums: the last l whose prefix before it is <= t
+      double run = 0.0;
+      for (int c0 = 0; c0 < n; c0 += 32) {
+        const int j = c0 + lane;
+        const double a = j < n ? fabs(row[j]) : 0.0;
+        const double incl = run + warp_incl_scan(a, lane);
+        const unsigned over = __ballot_sync(0xffffffffu, j < n && incl - a > t);
+        if (over) {
+          lo = c0 + __ffs(over) - 2;  // the element before the first prefix above t
+          break;
+        }
+        run = __shfl_sync(0xffffffffu, incl, 31);
+      }
+      hi = 1;  // right suffix sums: one past the last h whose suffix from it exceeds t
+      run = 0.0;
+      for (int c0 = 0; c0 < n; c0 += 32) {
+        const int j = n - 1 - c0 - lane;
+        const double a = j >= 0 ? fabs(row[j]) : 0.0;
+        const double incl = run + warp_incl_scan(a, lane);
+        const unsigned over = __ballot_sync(0xffffffffu, j >= 0 && incl > t);
+        if (over) {
+          hi = n - c0 - __ffs(over) + 1;
+          break;
+        }
+        run = __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+    if (lane == 0) {
+      atomicMin(&s_lo, lo);
+      atomicMax(&s_hi, hi);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) band[blockIdx.x] = make_int2(s_lo & ~63, min(n, (s_hi + 63) & ~63));
+}
+
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -2262,6 +2368,12 @@ struct TcState {
   __nv_bfloat16* buf[2][2];      // [b][c] -> [3][N]
   CUtensorMap amap[2][2][3];     // [b][c][mu]: buffer b viewed as [3][N/n_mu][n_mu]
   CUtensorMap bmap[2][3][3];     // [c][mu][ell]
+  // column supports of the 128-row groups of each Phi (device, inside the
+  // cached piece buffer; host copies for the work accounting); kband null
+  // when the supports are off (every tile contracts over all of K)
+  const int2* kband[2][3][3];
+  std::vector<int2> hband[2][3][3];
+  int ksupport;
   int variant;
   int fmt;       // operand format: kFmtBF16 (three BF16 pieces) or kFmtTF32 (two TF32 pieces)
   int fuse;      // 1: fuse the stage-1 combination into the last stage-1 product
@@ -2324,6 +2436,7 @@ static TcPassDesc make_desc(const TcState* S, const adr_plan_s* P, const TcPass&
   for (int c = 0; c < 2; ++c) {
     D.amap[c] = S->amap[ps.b][c][ps.mu];
     D.bmap[c] = S->bmap[c][ps.mu][ps.ell];
+    D.kband[c] = S->ksupport ? S->kband[c][ps.mu][ps.ell] : nullptr;
     D.outp[c] = S->buf[1 - ps.b][c];
     D.outf[c] = ps.out == kOutStage ? stage[c] : (ps.out == kOutState ? state[c] : nullptr);
     D.base[c] = ps.base == kBaseStage ? stage[c] : (ps.base == kBaseState ? state[c] : nullptr);
@@ -2506,6 +2619,9 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
   TcState* S = new TcState();
   t->work[0] = S;
   t->prec = prec;
+  // Tiles contract over the column support of their rows of Phi (ADR_KSUPPORT=0: all of K)
+  S->ksupport = 1;
+  if (const char* ev = getenv("ADR_KSUPPORT")) S->ksupport = atoi(ev) != 0;
   S->d = d;
   S->fmt = prec == ADR_TF32X3 ? kFmtTF32 : kFmtBF16;
   // Default kernel: on grids of about a million points and more, the
@@ -2576,23 +2692,29 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
         if ((scheme == ADR_LAWSON2B) != (l == 0)) continue;  // only the matrices the scheme uses
         const int64_t nn = n[m] * n[m];
         const size_t pb = S->fmt == kFmtTF32 ? 2 * 4 : (size_t)kPieces * 2;  // piece bytes per value
-        // the pieces of a cached FP64 matrix are cached with it (keyed by
-        // that matrix and the piece format)
+        const int nbands = (int)((n[m] + kBandRows - 1) / kBandRows);
+        // the pieces of a cached FP64 matrix, followed by the column supports
+        // of its row groups, are cached with it (keyed by that matrix and the
+        // piece format); pb * nn is a multiple of 8 bytes
         const double* src = master[c][m][1 + l];
         const std::vector<uint64_t> key = {1, (uint64_t)(uintptr_t)src, (uint64_t)S->fmt,
                                            (uint64_t)nn};
         void* buf = nullptr;
         bool hit = false;
-        e = shared_acquire(key, 1, pb * nn, [&](void* const* b) {
+        e = shared_acquire(key, 1, pb * nn + sizeof(int2) * nbands, [&](void* const* b) {
           if (S->fmt == kFmtTF32)
             split_matrix_tf32_kernel<<<grid_for(nn), 256, 0, s>>>(src, (float*)b[0], nn);
           else
             split_matrix_kernel<<<grid_for(nn), 256, 0, s>>>(src, (__nv_bfloat16*)b[0], nn);
+          band_support_kernel<<<nbands, 32 * kBandWarps, 0, s>>>(
+              src, (int)n[m], kBandDrop, (int2*)((uint8_t*)b[0] + pb * nn));
           return cudaGetLastError();
         }, s, &buf, &hit);
         if (e != cudaSuccess) return e;
         S->shared.push_back(buf);
         S->phi[c][m][l] = (__nv_bfloat16*)buf;
+        S->kband[c][m][l] = (const int2*)((uint8_t*)buf + pb * nn);
+        S->hband[c][m][l].resize(nbands);
         e = encode_pieces(&S->bmap[c][m][l], S->phi[c][m][l], n[m], n[m],
                           kVariants[S->variant].cta2 ? bn / 2 : bn, sw, S->fmt);
         if (e != cudaSuccess) return e;
@@ -2670,6 +2792,14 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
   S->rdiff_blocks = rdiff_blocks_of(S);
   e = cudaStreamSynchronize(s);  // the split matrices are complete
   if (e != cudaSuccess) return e;
+  for (int c = 0; c < 2; ++c)
+    for (int m = 0; m < d; ++m)
+      for (int l = 0; l < 3; ++l)
+        if (!S->hband[c][m][l].empty()) {
+          e = cudaMemcpy(S->hband[c][m][l].data(), S->kband[c][m][l],
+                         sizeof(int2) * S->hband[c][m][l].size(), cudaMemcpyDeviceToHost);
+          if (e != cudaSuccess) return e;
+        }
   S->bound_u = S->bound_v = nullptr;
   t->ready = 1;
   return cudaSuccess;
@@ -2892,6 +3022,42 @@ cudaError_t tc_step(TcOperands* t, adr_plan_s* P, void* u, void* v) {
 // between them), the graph is replayed once to warm up and once between two
 // events.  *ms = the replay's time / (reps x passes per step).  (u, v) are
 // scratch state buffers (the AXPY passes write them).
+// Host mirror of k_blocks: the K-blocks a tile starting at row n0 runs.
+static void host_k_blocks(const std::vector<int2>& band, int64_t K, int64_t n0, int bk,
+                          int64_t& kb0, int64_t& kb1) {
+  const int64_t nk = (K + bk - 1) / bk;
+  kb0 = 0;
+  kb1 = nk;
+  if (band.empty()) return;
+  const int2 r = band[n0 >> 7];
+  if (r.x < r.y) {
+    kb0 = r.x / bk;
+    kb1 = std::min<int64_t>(nk, (r.y + bk - 1) / bk);
+  }
+}
+
+void tc_mode_macs(const TcOperands* t, double* dense, double* computed) {
+  *dense = *computed = 0.0;
+  const TcState* S = (const TcState*)t->work[0];
+  if (!S) return;
+  const int bn = kVariants[S->variant].bn;
+  const int bk = kVariants[S->variant].sw / (S->fmt == kFmtTF32 ? 4 : 2);
+  static const std::vector<int2> none;
+  for (const TcPass& ps : S->passes) {
+    const int64_t K = S->n[ps.mu], M = S->N / K;
+    for (int c = 0; c < 2; ++c) {
+      *dense += (double)M * (double)K * (double)K;
+      const std::vector<int2>& band = S->ksupport ? S->hband[c][ps.mu][ps.ell] : none;
+      for (int64_t n0 = 0; n0 < K; n0 += bn) {
+        int64_t kb0, kb1;
+        host_k_blocks(band, K, n0, bk, kb0, kb1);
+        const int64_t rows = std::min<int64_t>(bn, K - n0);
+        *computed += (double)M * (double)rows * (double)(std::min(kb1 * bk, K) - kb0 * bk);
+      }
+    }
+  }
+}
+
 cudaError_t tc_time_passes(TcOperands* t, adr_plan_s* P, void* u, void* v, int reps, float* ms,
                            int* passes) {
   TcState* S = (TcState*)t->work[0];
