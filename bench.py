@@ -380,23 +380,30 @@ def mode_product_roofline(p, prec, ms_launch: float, per_step: int, peaks, peak_
                           computed_share: float = 1.0):
     """Roofline of the tensor-core mode-product launch, timed as it runs
     inside a step (adr_plan_time_mode_products), on the algorithmic work of
-    the method per launch:
-      flops: 2 flops x n_mu per output x 2 components  = 4 n_mu N (mean over mu)
-      bytes: FP32 operand in + out for both components = 16 B per point, plus
-             the base (U or U2) read by the last product of each ETD2RKds
-             Tucker operator: 16 + 8/d B per point on average.
+    the method per launch.  A step holds two Tucker operators (Eq. 11 or
+    Eq. 7); with `per_step` launches each operator takes P = per_step / 2
+    launches, so one launch computes d / P mode products (2D grids fuse both
+    directions of an operator into one launch):
+      flops: 2 flops x n_mu per output x 2 components per product
+             = (d / P) x 4 n_mu N (n_mu averaged over the directions)
+      bytes: FP32 operand in + out for both components = 16 B per point per
+             launch, plus the base (U or U2) the operator's last launch reads:
+             16 + 8 / P B per point on average (ETD2RKds).
     The bound is the slower of the two at the measured peaks (dense BF16
     burst, HBM copy); `frac` is the algorithmic fraction.  The split-precision
     form issues 6 (BF16x3) or 3 TF32 (= 6 BF16-rate) MMAs per product it
-    computes, and computes `computed_share` of the dense products (each tile
-    contracts over the column support of its rows of phi, adr_plan_mode_product_macs):
+    computes, and computes `computed_share` of the dense products (tiles
+    contract over the column supports of their rows of phi; a fused launch
+    recomputes part of its intermediate, adr_plan_mode_product_macs):
     `issued_tensor_frac` counts the MMAs actually issued."""
     d = p.d
     N = float(p.npoints)
     nmu = float(sum(p.n[:d])) / d
-    flops = 4.0 * nmu * N
-    per_pt = 16.0 + (8.0 / d if p.scheme == wl.ETD2RKDS else 0.0)
-    nbytes = per_pt * N + 2.0 * 4.0 * nmu * nmu
+    passes = max(1.0, per_step / 2.0)
+    products = d / passes
+    flops = products * 4.0 * nmu * N
+    per_pt = 16.0 + (8.0 / passes if p.scheme == wl.ETD2RKDS else 0.0)
+    nbytes = per_pt * N + products * 2.0 * 4.0 * nmu * nmu
     issue = 3.0 if prec == wl.TF32X3 else 6.0
     ratio = 0.5 if prec == wl.TF32X3 else 1.0
     tc_peak = peaks["bf16_tflops"] * 1e12 * ratio
@@ -409,6 +416,7 @@ def mode_product_roofline(p, prec, ms_launch: float, per_step: int, peaks, peak_
                                  "steps replayed back to back in one CUDA graph (programmatic "
                                  "dependent launch, no timing node between launches)",
               "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+              "mode_products_per_launch": products,
               "tensor_frac_algorithmic": t_tc / avg_s, "hbm_frac_algorithmic": t_hbm / avg_s,
               "issued_tensor_frac": issue * computed_share * t_tc / avg_s,
               "issued_mmas_per_product": int(issue),

@@ -340,6 +340,12 @@ struct alignas(128) TcPassDesc {
                             // rewritten in place (null: plain FP32 update)
   const int2* kband[2];     // per component: column support [lo, hi) of each 128-row group
                             // of Phi (null: every tile runs the whole K)
+  // fused two-mode pass (modes 1 and 2 in one launch): amap = Phi_a pieces,
+  // bmap = W pieces (box of kFRowsW rows), cmap = Phi_b pieces, kband /
+  // kband2 = the supports of Phi_a / Phi_b; slabs = n3 (1 in 2D)
+  CUtensorMap cmap[2];
+  const int2* kband2[2];
+  int n1, n2, slabs;
   double* ind;              // last product of a step: indicator ring [ind_k][4] (null: off)
   const int64_t* ind_ctr;   // the step's slot: *ind_ctr % ind_k
   int ind_k;
@@ -419,7 +425,7 @@ __device__ __forceinline__ void axpy_epilogue(uint32_t ta, float* __restrict__ o
       const int col = n0 + bt * 16 + jj;
       const bool ok = mrow && col < N;
       const int64_t o = (int64_t)col * M + m;
-      bb[jj] = ok ? __ldg(bsrc + o) : 0.f;
+      bb[jj] = (ok && bsrc) ? __ldg(bsrc + o) : 0.f;
       lv[jj] = (ok && lp) ? __ldcg(lp + o) : 0.f;
       pv[jj] = (ok && ind) ? __ldcg(of + o) : 0.f;
     }
@@ -1410,6 +1416,457 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
   }
 }
 
+// ---------------------------------------------------------------- fused two-mode kernel
+// T = W x_1 Phi_a x_2 Phi_b, the first two factors of the Tucker operator of
+// Eq. 5, in one launch without storing the intermediate.  A unit is one
+// 128 x 128 tile of T (output rows j1 of Phi_a, output rows j2 of Phi_b) of
+// one component and one x3 slab (the whole field in 2D):
+//   MMA1  D1[j1][i2] = sum_{i1} Phi_a[j1][i1] W[i2][i1] for the i2 of the
+//         column support of the tile's Phi_b rows (in groups of up to 256
+//         i2, the D1 columns), over the K-blocks of the Phi_a rows' support;
+//   split the epilogue warps read D1 back 64 i2 at a time and store its three
+//         BF16 pieces into TMEM;
+//   MMA2  D2[j1][j2] += sum_{i2} P[j1][i2] Phi_b[j2][i2], the pieces P read as
+//         the A operand from TMEM and Phi_b's pieces from shared memory;
+//   out   D2 -> T in the natural layout (x1 contiguous), with the epilogue of
+//         the operator's last product.
+// Both products take the six piece products of the split form.  MMA1 runs
+// over the i2 support of 128 rows of Phi_b (up to 256 i2): about twice the
+// products of a separate first pass, in exchange for the intermediate's
+// round trip through memory and a launch.
+//
+// Shared memory: a ring of kFStages stages; an MMA1 stage holds one K-block
+// (32 values) of Phi_a's 128 rows and of W's kFRowsW rows, an MMA2 stage two
+// K-blocks of Phi_b's 128 rows.  TMEM (512 columns): D2 [0, 128), D1
+// [128, 384), and two buffers for the pieces of a 64-column chunk of D1 (32
+// columns per piece): buffer 0 at [384, 480), buffer 1 in the columns of D1's
+// first chunk [128, 192) and [480, 512).  Chunk ch of a group uses buffer
+// ch & 1, so buffer 1 is written only once chunk 0 has been read, and the
+// split of one chunk overlaps MMA2 of the previous one.
+constexpr int kFBK = 32;                               // K values per K-block (64-byte rows)
+constexpr int kFRowsW = 256;                           // W rows per MMA1 stage (D1 columns)
+constexpr int kFTileA = kBM * 64;                      // one piece of Phi_a's block: 8 KB
+constexpr int kFTileW = kFRowsW * 64;                  // one piece of W's block: 16 KB
+constexpr int kFTileC = kBM * 64;                      // one piece of a Phi_b block: 8 KB
+constexpr int kFStage = kPieces * (kFTileA + kFTileW);  // 72 KB
+constexpr int kFStages = 3;
+constexpr int kFSmem = kFStages * kFStage + 1024 + 256;
+constexpr uint32_t kFColD2 = 0, kFColD1 = 128, kFColP = 384;
+// TMEM column of piece p of pieces buffer b
+__device__ __forceinline__ uint32_t piece_col(int b, int p) {
+  return b == 0 ? kFColP + 32u * p : (p < 2 ? kFColD1 + 32u * p : 480u);
+}
+// Three BF16 pieces of two FP32 values, each level rounded to nearest (the
+// same pieces as split3), packed two per 32-bit word with x0 in the low half.
+__device__ __forceinline__ void split3_pair(float x0, float x1, uint32_t& w0, uint32_t& w1,
+                                            uint32_t& w2) {
+  const __nv_bfloat162 h0 = __floats2bfloat162_rn(x0, x1);
+  const float2 f0 = __bfloat1622float2(h0);
+  const float r0 = x0 - f0.x, r1 = x1 - f0.y;
+  const __nv_bfloat162 h1 = __floats2bfloat162_rn(r0, r1);
+  const float2 f1 = __bfloat1622float2(h1);
+  const __nv_bfloat162 h2 = __floats2bfloat162_rn(r0 - f1.x, r1 - f1.y);
+  w0 = *reinterpret_cast<const uint32_t*>(&h0);
+  w1 = *reinterpret_cast<const uint32_t*>(&h1);
+  w2 = *reinterpret_cast<const uint32_t*>(&h2);
+}
+static_assert(2 * kPieces * kFTileC <= kFStage, "an MMA2 stage fits in a ring slot");
+static_assert(kFSmem <= 227 * 1024, "shared memory per CTA");
+
+// MMA with the A operand in TMEM (kind::f16, BF16 pieces, FP32 accumulate).
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// 32 lanes x 32 bit, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Unit of the fused kernel: component c, slab s, j1 tile a, j2 tile b.
+struct UnitF {
+  const TcPassDesc* d;
+  int c, s, a, b;
+};
+__device__ __forceinline__ UnitF decode_unitf(const TcLaunch& L, int u) {
+  UnitF w;
+  int r = u;
+  if (L.desc == nullptr) {
+    w.d = &L.one;
+  } else {
+    const int sv = find_segment(L.ustart, L.nsolves, u);
+    w.d = L.desc + sv;
+    r -= __ldg(L.ustart + sv);
+  }
+  w.a = r % w.d->tiles_m;
+  r /= w.d->tiles_m;
+  w.b = r % w.d->tiles_n;
+  r /= w.d->tiles_n;
+  w.s = r % w.d->slabs;
+  w.c = r / w.d->slabs;
+  return w;
+}
+// The i2 range [lo, hi) a unit contracts over in MMA2: the column support of
+// its Phi_b rows (multiples of 64, the end clipped to n2), or all of x2.
+__device__ __forceinline__ void x2_range(const TcPassDesc* d, int c, int b, int& lo, int& hi) {
+  lo = 0;
+  hi = d->n2;
+  const int2* t = d->kband2[c];
+  if (t == nullptr) return;
+  const int2 r = __ldg(t + b);  // 128-row groups: the tile's own
+  if (r.x < r.y) {
+    lo = r.x;
+    hi = r.y;
+  }
+}
+
+template <bool IND = false>
+__global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_constant__ TcLaunch L) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + kFStages * kFStage);
+  uint64_t* empty = full + kFStages;
+  uint64_t* d1_full = empty + kFStages;  // MMA1 of a group complete (commit)
+  uint64_t* d1_free = d1_full + 1;       // the group's D1 read by every epilogue warp
+  uint64_t* p_full = d1_free + 1;        // [2] a chunk's pieces stored (every epilogue warp)
+  uint64_t* p_free = p_full + 2;         // [2] MMA2 of a chunk complete (commit)
+  uint64_t* acc_full = p_free + 2;       // D2 of a unit complete (commit)
+  uint64_t* drain = acc_full + 1;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  int* abort_flag = (int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  pdl_trigger();
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kFStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(d1_full, 1);
+    mbar_init(d1_free, kEpiWarps);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&p_full[b], kEpiWarps);
+      mbar_init(&p_free[b], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int* abort_v = abort_flag;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer: per group the MMA1 K-blocks, then the
+    // Phi_b blocks of its chunks, in the order the MMA thread consumes them
+    uint32_t g = 0;
+    bool stop = false, waited = false;
+    auto next_stage = [&](uint32_t bytes) -> uint8_t* {
+      const int s = g % kFStages;
+      const uint32_t it = g / kFStages;
+      if (*abort_v || (it > 0 && !mbar_wait(&empty[s], (it - 1) & 1))) {
+        atomicCAS(L.err, 0, kErrTimeoutEmpty);
+        *abort_v = 1;
+        stop = true;
+        return nullptr;
+      }
+      if (!waited) {  // W is the previous launch's output
+        pdl_wait();
+        waited = true;
+      }
+      mbar_arrive_expect_tx(&full[s], bytes);
+      return smem + s * kFStage;
+    };
+    for (int u = blockIdx.x; u < L.nunits && !stop; u += gridDim.x) {
+      const UnitF w = decode_unitf(L, u);
+      const TcPassDesc* D = w.d;
+      const CUtensorMap* ma = &D->amap[w.c];
+      const CUtensorMap* mw = &D->bmap[w.c];
+      const CUtensorMap* mc = &D->cmap[w.c];
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)ma) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mw) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mc) : "memory");
+      int kb0, kb1, x2lo, x2hi;
+      k_blocks(D, w.c, w.a * kBM, kFBK, kb0, kb1);
+      x2_range(D, w.c, w.b, x2lo, x2hi);
+      for (int g2 = x2lo; g2 < x2hi && !stop; g2 += kFRowsW) {
+        const int nch = (min(kFRowsW, x2hi - g2) + 63) / 64;
+        for (int kb = kb0; kb < kb1 && !stop; ++kb, ++g) {
+          uint8_t* st = next_stage(kFStage);
+          if (!st) break;
+          tma_load_3d(st, ma, &full[g % kFStages], kb * kFBK, w.a * kBM, 0);
+          tma_load_3d(st + kPieces * kFTileA, mw, &full[g % kFStages], kb * kFBK,
+                      w.s * D->n2 + g2, 0);
+        }
+        for (int ch = 0; ch < nch && !stop; ++ch, ++g) {
+          uint8_t* st = next_stage(2 * kPieces * kFTileC);
+          if (!st) break;
+          tma_load_3d(st, mc, &full[g % kFStages], g2 + ch * 64, w.b * kBM, 0);
+          tma_load_3d(st + kPieces * kFTileC, mc, &full[g % kFStages], g2 + ch * 64 + kFBK,
+                      w.b * kBM, 0);
+        }
+      }
+    }
+    // the last kFStages loads must have landed before exit
+    const uint32_t first = g > (uint32_t)kFStages ? g - kFStages : 0;
+    for (uint32_t q = first; q < g; ++q) mbar_wait(&full[q % kFStages], (q / kFStages) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint64_t dS0 = kmajor_desc<64>(smem_u32(smem));
+    const uint32_t idesc2 = idesc_bf16(kBM, kBM);
+    uint32_t g = 0, grp = 0;
+    uint32_t uses[2] = {0, 0};  // completed uses of each pieces buffer
+    bool stop = false;
+    auto wait_full = [&]() -> bool {
+      if (!mbar_wait(&full[g % kFStages], (g / kFStages) & 1)) {
+        atomicCAS(L.err, 0, kErrTimeoutFull);
+        *abort_v = 1;
+        stop = true;
+      }
+      return !stop;
+    };
+    for (int u = blockIdx.x; u < L.nunits && !stop; u += gridDim.x) {
+      const UnitF w = decode_unitf(L, u);
+      const TcPassDesc* D = w.d;
+      int kb0, kb1, x2lo, x2hi;
+      k_blocks(D, w.c, w.a * kBM, kFBK, kb0, kb1);
+      x2_range(D, w.c, w.b, x2lo, x2hi);
+      bool first2 = true;
+      for (int g2 = x2lo; g2 < x2hi && !stop; g2 += kFRowsW, ++grp) {
+        const int nch = (min(kFRowsW, x2hi - g2) + 63) / 64;
+        // D1 is free once the epilogue warps have read the previous group
+        // and MMA2 has read pieces buffer 1 (inside D1) for the last time
+        if (grp > 0 && (!mbar_wait(d1_free, (grp - 1) & 1) ||
+                        (uses[1] > 0 && !mbar_wait(&p_free[1], (uses[1] - 1) & 1)))) {
+          atomicCAS(L.err, 0, kErrTimeoutDone);
+          *abort_v = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t idesc1 = idesc_bf16(kBM, 64 * nch);
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
+          if (!wait_full()) break;
+          const uint64_t da = dS0 + (uint64_t)(((g % kFStages) * kFStage) >> 4);
+          const uint64_t db = da + (uint64_t)((kPieces * kFTileA) >> 4);
+          issue_stage<64, kFTileA, kFTileW, false>(tmem + kFColD1, da, db, idesc1, kb != kb0);
+          mma_commit(&empty[g % kFStages]);
+        }
+        if (stop) break;
+        mma_commit(d1_full);
+        for (int ch = 0; ch < nch; ++ch, ++g) {
+          const int pb = ch & 1;
+          if (!mbar_wait(&p_full[pb], uses[pb] & 1)) {
+            atomicCAS(L.err, 0, kErrTimeoutDone);
+            *abort_v = 1;
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          if (!wait_full()) break;
+          const uint64_t db0 = dS0 + (uint64_t)(((g % kFStages) * kFStage) >> 4);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t b0 = db0 + (uint64_t)(((kk >> 1) * kPieces * kFTileC) >> 4) +
+                                (uint64_t)((kk & 1) * 2);
+            const uint64_t b1 = b0 + (uint64_t)(kFTileC >> 4);
+            const uint64_t b2 = b0 + (uint64_t)(2 * kFTileC >> 4);
+            const uint32_t a0 = tmem + piece_col(pb, 0) + (uint32_t)(kk * 8);
+            const uint32_t a1 = tmem + piece_col(pb, 1) + (uint32_t)(kk * 8);
+            const uint32_t a2 = tmem + piece_col(pb, 2) + (uint32_t)(kk * 8);
+            const uint32_t dt = tmem + kFColD2;
+            mma_bf16_ts(dt, a2, b0, idesc2, (first2 && kk == 0) ? 0u : 1u);
+            mma_bf16_ts(dt, a1, b1, idesc2, 1);
+            mma_bf16_ts(dt, a1, b0, idesc2, 1);
+            mma_bf16_ts(dt, a0, b2, idesc2, 1);
+            mma_bf16_ts(dt, a0, b1, idesc2, 1);
+            mma_bf16_ts(dt, a0, b0, idesc2, 1);
+          }
+          first2 = false;
+          mma_commit(&empty[g % kFStages]);
+          mma_commit(&p_free[pb]);
+          ++uses[pb];
+        }
+      }
+      if (stop) break;
+      mma_commit(acc_full);
+    }
+    mma_commit(drain);
+    mbar_wait(drain, 0);
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps: split D1 into pieces, then write T
+    pdl_wait();
+    const int q = warp & 3;            // TMEM lane quarter
+    const int half = (warp - 2) >> 2;  // column half
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    uint32_t grp = 0;
+    uint32_t uses[2] = {0, 0};  // stores into each pieces buffer so far
+    int i = 0;
+    bool stop = false;
+    for (int u = blockIdx.x; u < L.nunits && !stop; u += gridDim.x, ++i) {
+      const UnitF w = decode_unitf(L, u);
+      const TcPassDesc* D = w.d;
+      int x2lo, x2hi;
+      x2_range(D, w.c, w.b, x2lo, x2hi);
+      for (int g2 = x2lo; g2 < x2hi && !stop; g2 += kFRowsW, ++grp) {
+        const int nch = (min(kFRowsW, x2hi - g2) + 63) / 64;
+        if (!__all_sync(0xffffffffu, mbar_wait_sleep(d1_full, grp & 1))) {
+          if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
+          *abort_v = 1;
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        for (int ch = 0; ch < nch; ++ch) {
+          const int pb = ch & 1;
+          // buffer pb is free once MMA2 has read its previous contents; buffer
+          // 1 lies in D1's first chunk, which every warp must have read
+          bool ok = true;
+          if (uses[pb] > 0) ok = mbar_wait_sleep(&p_free[pb], (uses[pb] - 1) & 1);
+          if (ok && ch == 1) ok = mbar_wait_sleep(&p_full[0], (uses[0] - 1) & 1);
+          if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
+            *abort_v = 1;
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          uint32_t r[2][16];
+          const uint32_t src = tmem + lane_off + kFColD1 + (uint32_t)(ch * 64 + half * 32);
+          tmem_ld16_nw(src, r[0]);
+          tmem_ld16_nw(src + 16, r[1]);
+          tmem_wait_ld();
+          tmem_fence16(r[0]);
+          tmem_fence16(r[1]);
+          // pieces of 32 consecutive i2, two BF16 per 32-bit column (the
+          // lower i2 in the low half)
+          uint32_t pk[3][16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            split3_pair(__uint_as_float(r[j / 8][(2 * j) % 16]),
+                        __uint_as_float(r[j / 8][(2 * j + 1) % 16]), pk[0][j], pk[1][j], pk[2][j]);
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+            tmem_st16(tmem + lane_off + piece_col(pb, p) + (uint32_t)(half * 16), pk[p]);
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&p_full[pb]))
+                         : "memory");
+          ++uses[pb];
+        }
+        if (stop) break;
+        // every D1 column of this group has been read
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(d1_free))
+                       : "memory");
+      }
+      if (stop) break;
+      // ---- T of the unit
+      const int n1 = D->n1, n2 = D->n2, mode = D->mode;
+      const int m = w.a * kBM + q * 32 + lane;  // j1
+      const bool mrow = m < n1;
+      const int n0 = w.b * kBM + half * 64;     // first j2 of this warp
+      const int64_t slab = (int64_t)w.s * n2 * n1;
+      float* lp = (mode == kAxpy && D->lo[w.c]) ? D->lo[w.c] + slab : nullptr;
+      double* ind = (IND && mode == kAxpy) ? indicator_slot(D, w.c) : nullptr;
+      const float* bsrc = D->base[w.c] ? D->base[w.c] + slab : nullptr;
+      const bool plain = mode == kAxpy && !lp && !ind;
+      // plain update: this warp's 64 base values are loaded while the last
+      // MMA2 runs
+      float bv[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        const int col = n0 + j;
+        bv[j] = (plain && bsrc && mrow && col < n2) ? __ldg(bsrc + (int64_t)col * n1 + m) : 0.f;
+      }
+      if (!__all_sync(0xffffffffu, mbar_wait_sleep(acc_full, i & 1))) {
+        if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
+        *abort_v = 1;
+        break;
+      }
+      tc_fence_after();
+      if (__any_sync(0xffffffffu, *abort_v)) break;
+      const uint32_t ta = tmem + lane_off + kFColD2 + (uint32_t)(half * 64);
+      if (plain) {
+        float* of = D->outf[w.c] + slab;
+        const float alpha = D->alpha;
+#pragma unroll
+        for (int bt = 0; bt < 4; bt += 2) {
+          uint32_t r[2][16];
+          tmem_ld16_nw(ta + (uint32_t)(bt * 16), r[0]);
+          tmem_ld16_nw(ta + (uint32_t)((bt + 1) * 16), r[1]);
+          tmem_wait_ld();
+          tmem_fence16(r[0]);
+          tmem_fence16(r[1]);
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const int col = n0 + bt * 16 + jj;
+            if (mrow && col < n2)
+              of[(int64_t)col * n1 + m] =
+                  __fmaf_rn(alpha, __uint_as_float(r[jj / 16][jj % 16]), bv[bt * 16 + jj]);
+          }
+        }
+      } else if (mode == kAxpy) {
+        axpy_epilogue<4>(ta, D->outf[w.c] + slab, bsrc, lp, D->alpha, n1, n2, n0, m, mrow, ind,
+                         D->ind_n1, D->ind_n2);
+      } else {  // kPieces3: three BF16 pieces of T, natural layout
+        __nv_bfloat16* op = D->outp[w.c];
+        const int64_t plane = (int64_t)D->slabs * n2 * n1;
+#pragma unroll 1
+        for (int bt = 0; bt < 4; ++bt) {
+          uint32_t r[16];
+          tmem_ld16_nw(ta + (uint32_t)(bt * 16), r);
+          tmem_wait_ld();
+          tmem_fence16(r);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int col = n0 + bt * 16 + jj;
+            if (mrow && col < n2) {
+              const int64_t o = slab + (int64_t)col * n1 + m;
+              __nv_bfloat16 b0, b1, b2;
+              split3(__uint_as_float(r[jj]), b0, b1, b2);
+              op[o] = b0;
+              op[plane + o] = b1;
+              op[2 * plane + o] = b2;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
 // ---------------------------------------------------------------- pointwise
 // Per-solve arguments of the pointwise kernels of the tensor-core path; one
 // launch covers one solve or a whole batch.
@@ -2327,6 +2784,14 @@ cudaError_t launch_tc(int v, int slots, cudaStream_t s, const TcLaunch& L, bool 
   return pair ? launch_tc_t<true>(v, grid, s, L) : launch_tc_t<false>(v, grid, s, L);
 }
 
+// The fused two-mode kernel: one CTA per SM at most (all of TMEM each).
+cudaError_t launch_fused(int slots, cudaStream_t s, const TcLaunch& L, bool ind) {
+  if (L.nunits <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)(L.nunits < slots ? L.nunits : slots));
+  if (ind) return launch_k(tc_fused_kernel<true>, grid, dim3(kThreads), kFSmem, s, L);
+  return launch_k(tc_fused_kernel<false>, grid, dim3(kThreads), kFSmem, s, L);
+}
+
 int grid_for(int64_t total) {
   int64_t b = (total + 255) / 256;
   if (b < 1) b = 1;
@@ -2345,6 +2810,7 @@ struct TcPass {
   int mode;   // TcMode
   int pair;
   int out, base, alpha;
+  int fused;  // 1: modes 1 and 2 in one launch (tc_fused_kernel); mu = 0
 };
 
 // One launch of the step sequence.
@@ -2374,6 +2840,11 @@ struct TcState {
   const int2* kband[2][3][3];
   std::vector<int2> hband[2][3][3];
   int ksupport;
+  // fused two-mode passes (2D, BF16 pieces): Phi of directions 1 and 2 with
+  // 128-row boxes, and each piece buffer as W with kFRowsW-row boxes
+  int fused12;
+  CUtensorMap fa[2][3], fc[2][3];  // [c][ell]
+  CUtensorMap fw[2][2];            // [b][c]
   int variant;
   int fmt;       // operand format: kFmtBF16 (three BF16 pieces) or kFmtTF32 (two TF32 pieces)
   int fuse;      // 1: fuse the stage-1 combination into the last stage-1 product
@@ -2409,6 +2880,10 @@ struct TcState {
 };
 
 static int units_of(const TcState* S, const TcPass& ps, int bn) {
+  if (ps.fused) {
+    const int64_t n1 = S->n[0], n2 = S->n[1], slabs = S->N / (n1 * n2);
+    return (int)(2 * slabs * ((n1 + kBM - 1) / kBM) * ((n2 + kBM - 1) / kBM));
+  }
   const int64_t nmu = S->n[ps.mu];
   const int64_t M = S->N / nmu;
   const int bm = tile_rows(S->variant);
@@ -2456,6 +2931,23 @@ static TcPassDesc make_desc(const TcState* S, const adr_plan_s* P, const TcPass&
   }
   D.alpha = ps.alpha == kAlphaTau ? (float)tau
                                   : (ps.alpha == kAlphaTauD ? (float)ldexp(tau, S->d - 1) : 1.0f);
+  if (ps.fused) {  // modes 1 and 2: Phi_a = direction 1, Phi_b = direction 2, W = buffer b
+    D.n1 = (int)S->n[0];
+    D.n2 = (int)S->n[1];
+    D.slabs = (int)(S->N / (S->n[0] * S->n[1]));
+    D.M = D.n1;
+    D.N = D.n2;
+    D.K = D.n1;
+    D.tiles_m = (D.n1 + kBM - 1) / kBM;
+    D.tiles_n = (D.n2 + kBM - 1) / kBM;
+    for (int c = 0; c < 2; ++c) {
+      D.amap[c] = S->fa[c][ps.ell];
+      D.bmap[c] = S->fw[ps.b][c];
+      D.cmap[c] = S->fc[c][ps.ell];
+      D.kband[c] = S->ksupport ? S->kband[c][0][ps.ell] : nullptr;
+      D.kband2[c] = S->ksupport ? S->kband[c][1][ps.ell] : nullptr;
+    }
+  }
   return D;
 }
 
@@ -2594,6 +3086,12 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     if ((e = set_smem_attr<64, 64>()) != cudaSuccess) return e;
     if ((e = set_smem_attr_pair<64>()) != cudaSuccess) return e;
     if ((e = set_smem_attr_pair<128>()) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(tc_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kFSmem)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(tc_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kFSmem)) != cudaSuccess)
+      return e;
     if ((e = cudaFuncSetAttribute(tc_mode_kernel<128, 128, false, false, kFmtTF32>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   TcCfg<128, 128, kFmtTF32>::SMEM)) != cudaSuccess)
@@ -2650,6 +3148,11 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     S->fuse = f >= 0 && f <= 2 ? f : 0;
   }
   if (kVariants[S->variant].cta2) S->fuse = 0;  // the CTA-pair kernel has neither epilogue
+  // 2D grids with BF16 pieces: each Tucker operator as one fused two-mode
+  // launch (ADR_TC_FUSED=0: one launch per direction)
+  S->fused12 = d == 2 && prec == ADR_BF16X3;
+  if (const char* ev = getenv("ADR_TC_FUSED")) S->fused12 = S->fused12 && atoi(ev) != 0;
+  if (S->fused12) S->fuse = 0;
   S->comp = scheme == ADR_ETD2RKDS ? comp : 0;
   if (S->comp) S->fuse = 0;  // the fused stage-1 epilogues keep a plain state
   if (S->fmt == kFmtTF32) {  // TF32 pieces: the one-CTA kernel, 128-byte swizzle, plain epilogues
@@ -2739,10 +3242,31 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
         if (e != cudaSuccess) return e;
       }
     }
+  if (S->fused12) {
+    for (int c = 0; c < 2; ++c) {
+      for (int l = 0; l < 3; ++l) {
+        if (!S->phi[c][0][l]) continue;
+        e = encode_pieces(&S->fa[c][l], S->phi[c][0][l], n[0], n[0], kBM, 64, S->fmt);
+        if (e == cudaSuccess)
+          e = encode_pieces(&S->fc[c][l], S->phi[c][1][l], n[1], n[1], kBM, 64, S->fmt);
+        if (e != cudaSuccess) return e;
+      }
+      for (int b = 0; b < 2; ++b) {
+        e = encode_pieces(&S->fw[b][c], S->buf[b][c], n[0], S->N / n[0], kFRowsW, 64, S->fmt);
+        if (e != cudaSuccess) return e;
+      }
+    }
+  }
   // step sequence (piece buffers alternate; pointwise stages write buffer 0)
   S->scheme = scheme;
   auto add_tucker = [&](int ell, int last_out, int last_base, int last_alpha, int stage1_fuse) {
     int b = 0;
+    if (S->fused12) {  // one launch: reads buffer 0, writes the operator's result
+      TcPass ps{0, 0, ell, kAxpy, 0, last_out, last_base, last_alpha, 1};
+      S->passes.push_back(ps);
+      S->ops.push_back({kOpTc, (int)S->passes.size() - 1, 0.f});
+      return 1;
+    }
     for (int mu = 0; mu < d; ++mu) {
       TcPass ps{b, mu, ell, kPieces3, 0, kOutPieces, kBaseNone, kAlphaOne};
       if (mu == d - 1) {
@@ -2774,7 +3298,12 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     // stage 2 reads the reaction difference from buffer 0 (separate kernel)
     // or from the buffer the fused epilogue wrote
     const int b2 = S->fuse ? b1 : 0;
-    for (int mu = 0, b = b2; mu < d; ++mu, b ^= 1) {
+    if (S->fused12) {
+      TcPass ps{b2, 0, 2, kAxpy, 0, kOutState, kBaseStage, kAlphaTauD, 1};
+      S->passes.push_back(ps);
+      S->ops.push_back({kOpTc, (int)S->passes.size() - 1, 0.f});
+    }
+    for (int mu = 0, b = b2; mu < d && !S->fused12; ++mu, b ^= 1) {
       TcPass ps{b, mu, 2, kPieces3, 0, kOutPieces, kBaseNone, kAlphaOne};
       if (mu == d - 1) {
         ps.mode = kAxpy;
@@ -2866,6 +3395,8 @@ struct GroupStep {
   int units[16];
   int pair[16];             // per pass: units are (u, v) pairs
   int xchg[16];             // per pass: kStage1X (clusters of two)
+  int fused[16];            // per pass: modes 1 and 2 in one launch
+  int fslots;               // resident CTAs of the fused kernel (one per SM)
   int ind[16];              // per pass: accumulates the step's indicators
   int df;                   // reactions in double-float (ADR_STATE_COMPENSATED)
   int xslots;               // resident clusters of the exchanging kernel
@@ -2945,6 +3476,7 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
         e = timed_kernel(ctl, KC_MODE_TC, G.flops[p], G.bytes[p],
                          [&] {
                            if (G.xchg[p]) return launch_xchg(G.variant, G.xslots, st, L);
+                           if (G.fused[p]) return launch_fused(G.fslots, st, L, G.ind[p] != 0);
                            if (G.fmt == kFmtTF32) {
                              dim3 grid((unsigned)(L.nunits < G.num_sms ? L.nunits : G.num_sms));
                              if (G.ind[p])
@@ -2969,6 +3501,7 @@ static void pass_work(const TcState* S, const TcPass& ps, double& flops, double&
   const double N = (double)S->N, nmu = (double)S->n[ps.mu];
   const double pb = S->fmt == kFmtTF32 ? 8.0 : 6.0;  // piece bytes per value
   flops = 2.0 * 2.0 * nmu * N;
+  if (ps.fused) flops = 2.0 * 2.0 * (double)(S->n[0] + S->n[1]) * N;  // two products
   bytes = 2.0 * (pb * N + pb * nmu * nmu);
   if (ps.mode == kPieces3) bytes += 2.0 * pb * N;
   if (ps.mode == kAxpy) bytes += 2.0 * (S->comp ? 16.0 : 8.0) * N;  // base, out (+ lo in, out)
@@ -2982,8 +3515,10 @@ static void fill_ops(GroupStep& G, const TcState* S) {
   for (int p = 0; p < G.np; ++p) {
     G.pair[p] = S->passes[p].pair;
     G.xchg[p] = S->passes[p].mode == kStage1X;
+    G.fused[p] = S->passes[p].fused;
   }
   G.xslots = S->xslots;
+  G.fslots = S->num_sms;
   G.fmt = S->fmt;
   G.df = S->comp == 2;
 }
@@ -3044,6 +3579,33 @@ void tc_mode_macs(const TcOperands* t, double* dense, double* computed) {
   const int bk = kVariants[S->variant].sw / (S->fmt == kFmtTF32 ? 4 : 2);
   static const std::vector<int2> none;
   for (const TcPass& ps : S->passes) {
+    if (ps.fused) {  // both products of tc_fused_kernel, as its loops run them
+      const int64_t n1 = S->n[0], n2 = S->n[1], slabs = S->N / (n1 * n2);
+      for (int c = 0; c < 2; ++c) {
+        *dense += (double)slabs * ((double)n1 * n1 * n2 + (double)n2 * n2 * n1);
+        const std::vector<int2>& ba = S->ksupport ? S->hband[c][0][ps.ell] : none;
+        const std::vector<int2>& bb = S->ksupport ? S->hband[c][1][ps.ell] : none;
+        for (int64_t a = 0; a * kBM < n1; ++a) {
+          int64_t kb0, kb1;
+          host_k_blocks(ba, n1, a * kBM, kFBK, kb0, kb1);
+          const double rows = (double)std::min<int64_t>(kBM, n1 - a * kBM);
+          const double kin = (double)(std::min(kb1 * kFBK, n1) - kb0 * kFBK);
+          for (int64_t b = 0; b * kBM < n2; ++b) {
+            int64_t lo = 0, hi = n2;
+            if (!bb.empty() && bb[b].x < bb[b].y) {
+              lo = bb[b].x;
+              hi = bb[b].y;
+            }
+            const double cols = (double)std::min<int64_t>(kBM, n2 - b * kBM);
+            for (int64_t g2 = lo; g2 < hi; g2 += kFRowsW) {
+              const int64_t w = 64 * ((std::min<int64_t>(kFRowsW, hi - g2) + 63) / 64);
+              *computed += (double)slabs * (rows * (double)w * kin + rows * cols * (double)w);
+            }
+          }
+        }
+      }
+      continue;
+    }
     const int64_t K = S->n[ps.mu], M = S->N / K;
     for (int c = 0; c < 2; ++c) {
       *dense += (double)M * (double)K * (double)K;

@@ -54,8 +54,9 @@ def test_traffic_only_for_the_captured_source_and_kernel(tmp_path):
 
 
 def test_in_step_roofline_arithmetic():
-    """Algorithmic work per mode-product launch: 4 n N flops and 16 + 8/d
-    bytes per point; frac is the slower bound's share of the duration."""
+    """Algorithmic work per mode-product launch: 4 n N flops per product and
+    16 + 8/P bytes per point (P launches per Tucker operator); frac is the
+    slower bound's share of the duration."""
     peaks = {"bf16_tflops": 2000.0, "hbm_gbs": 8000.0}
     p = wl.fhn_1024(precision=wl.BF16X3)  # 1024^2, d = 2
     N = 1024 * 1024
@@ -67,6 +68,13 @@ def test_in_step_roofline_arithmetic():
     assert r["bound"] == ("tensor" if t_tc >= t_hbm else "hbm")
     assert r["frac"] == pytest.approx(max(t_tc, t_hbm) / 2e-5)
     assert r["issued_tensor_frac"] == pytest.approx(6 * t_tc / 2e-5)
+    # fused 2D operators: two launches per step, each two mode products
+    # reading and writing the field once (24 B per point with the base)
+    rf = bench.mode_product_roofline(p, wl.BF16X3, 0.02, 2, peaks, "test", None, 0.5)
+    assert rf["mode_products_per_launch"] == 2
+    assert rf["algorithmic_flops_per_launch"] == pytest.approx(8 * 1024 * N)
+    assert rf["algorithmic_bytes_per_launch"] == pytest.approx(24 * N + 16 * 1024 * 1024)
+    assert rf["issued_tensor_frac"] == pytest.approx(0.5 * 6 * (8 * 1024 * N / 2e15) / 2e-5)
     q = wl.brusselator_256(precision=wl.BF16X3)  # 256^3, d = 3: HBM-bound
     r3 = bench.mode_product_roofline(q, wl.BF16X3, 0.1, 6, peaks, "test", None)
     assert r3["bound"] == "hbm" and r3["unit"] == "GB/s"

@@ -247,8 +247,9 @@ def test_timed_graph_replay(adr):
         outs.append((u.cpu(), v.cpu(), st))
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
     st = outs[1][2]
-    assert st["launches"] == 6 * p.nsteps and st["device_error"] == 0
+    # a 2D step: stencil, fused Tucker operator, reaction difference, fused Tucker operator
+    assert st["launches"] == 4 * p.nsteps and st["device_error"] == 0
     k = st["kernels"]
-    assert k["mode_product_tc"]["count"] == 4 * p.nsteps
+    assert k["mode_product_tc"]["count"] == 2 * p.nsteps
     assert k["rhs_stencil_reaction"]["count"] == p.nsteps == k["reaction_diff"]["count"]
     assert all(k[c]["ms"] > 0 for c in ("mode_product_tc", "rhs_stencil_reaction", "reaction_diff"))
