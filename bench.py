@@ -76,21 +76,24 @@ def measured_gemm_peak(dtype) -> float:
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
-def profiled_traffic(workload_name: str, kernel: int, profiles: str = None):
+def profiled_traffic(workload_name: str, kernel, profiles: str = None):
     """DRAM bytes per launch of the tensor-core mode-product kernel from the
     committed ncu summary, or None when the kernel source has changed since
-    that capture or the capture is of another kernel than `kernel`."""
+    that capture or the capture is of another kernel than `kernel` (a
+    variant number of the per-direction kernel, or "fused" for the fused
+    two-mode kernel of 2D grids, summarised in tc_fused_<workload>.md)."""
     import hashlib
     import re
-    prof = os.path.join(profiles or os.path.join(ROOT, "profiles"), f"tc_mode_{workload_name}.md")
+    stem = "tc_fused" if kernel == "fused" else "tc_mode"
+    prof = os.path.join(profiles or os.path.join(ROOT, "profiles"), f"{stem}_{workload_name}.md")
     src = os.path.join(ROOT, "paper_2307_10684_gb300", "csrc", "tc.cu")
     try:
         txt = open(prof).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         m_sha = re.search(r"source_sha256\([^)]*\): ([0-9a-f]+)", txt)
         m_b = re.search(r"dram_bytes_per_launch: (\d+)", txt)
-        m_k = re.search(r"captured_kernel: (-?\d+)", txt)
-        if m_sha and m_b and m_k and m_sha.group(1) == sha and int(m_k.group(1)) == kernel:
+        m_k = re.search(r"captured_kernel: (\S+)", txt)
+        if m_sha and m_b and m_k and m_sha.group(1) == sha and m_k.group(1) == str(kernel):
             return int(m_b.group(1))
     except OSError:
         pass
@@ -530,6 +533,8 @@ def run_single(args, p, nts: int, R, with_compare: bool, oracle):
     in_step = None
     if dom == "mode_product_tc":
         used = kernel if kernel >= 0 else (4 if npts >= 1000000 else 0)  # the plan default
+        if p.d == 2 and prec == wl.BF16X3 and os.environ.get("ADR_TC_FUSED", "1") != "0":
+            used = "fused"  # 2D operators run as one fused two-mode launch
         traffic = (profiled_traffic(PROFILE_KEY.get(p.name, p.name), used)
                    if p.scheme == wl.ETD2RKDS and int(getattr(p, "state", 0)) != wl.STATE_COMPENSATED
                    else None)

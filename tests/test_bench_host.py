@@ -51,6 +51,10 @@ def test_traffic_only_for_the_captured_source_and_kernel(tmp_path):
     assert bench.profiled_traffic("fhn1024", 0, str(tmp_path)) is None
     assert bench.profiled_traffic("old", 4, str(tmp_path)) is None
     assert bench.profiled_traffic("no_such_workload", 4, str(tmp_path)) is None
+    # the fused two-mode kernel has its own summary
+    (tmp_path / "tc_fused_fhn1024.md").write_text(
+        f"source_sha256(tc.cu): {sha}\ncaptured_kernel: fused\ndram_bytes_per_launch: 123\n")
+    assert bench.profiled_traffic("fhn1024", "fused", str(tmp_path)) == 123
 
 
 def test_in_step_roofline_arithmetic():
