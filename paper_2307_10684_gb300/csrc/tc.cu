@@ -291,6 +291,34 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor of an MN-major tile with 128-byte swizzle:
+// atoms of 64 M values (128 bytes) by 8 K rows, consecutive atoms along K
+// `sbo` bytes apart and the second 64 M values `lbo` bytes from the first.
+__device__ __forceinline__ uint64_t mnmajor_desc128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// A operand of a stage in the MMA issue loops: the descriptor of piece 0 at
+// the stage's first K step, and the descriptor increments (16-byte units)
+// from one piece to the next and from one K16 step to the next.
+struct AOperand {
+  uint64_t d;
+  uint32_t piece, kstep;
+};
+// K-major A tile of P pieces of 128 rows x SW bytes, or (amn) MN-major:
+// [M half][piece][bk K rows][128 bytes] as two TMA boxes of 64 M values.
+template <int SW>
+__device__ __forceinline__ AOperand a_operand(uint32_t stage, bool amn) {
+  constexpr int BK = SW / 2;  // BF16 values of K per stage
+  if (amn) return {mnmajor_desc128(stage, kPieces * BK * 128, 1024), (uint32_t)(BK * 128 >> 4), 128u};
+  return {kmajor_desc<SW>(stage), (uint32_t)(kBM * SW >> 4), 2u};
+}
+
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
 // 17-22, M >> 4 at bits 24-28.
@@ -346,6 +374,11 @@ struct alignas(128) TcPassDesc {
   CUtensorMap cmap[2];
   const int2* kband2[2];
   int n1, n2, slabs;
+  int bunit;                // fused pass: j2 tiles per unit (all of them when n2 <= 256, else 1)
+  // 1: the A pieces are MN-major, [piece][K rows][M] (the mode-3 product of a
+  // 3D operator after the fused pass, K = x3): two boxes of 64 M values per
+  // stage, 128-byte swizzle
+  int amn;
   double* ind;              // last product of a step: indicator ring [ind_k][4] (null: off)
   const int64_t* ind_ctr;   // the step's slot: *ind_ctr % ind_k
   int ind_k;
@@ -686,7 +719,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
             waited = true;
           }
           mbar_arrive_expect_tx(&full[s], C::STAGE);
-          tma_load_3d(st, ma, &full[s], kb * C::BK, w.m0, 0);                   // 3 A pieces
+          if (w.d->amn) {  // MN-major A: two boxes of 64 M values
+            tma_load_3d(st, ma, &full[s], w.m0, kb * C::BK, 0);
+            tma_load_3d(st + kPieces * C::BK * 128, ma, &full[s], w.m0 + 64, kb * C::BK, 0);
+          } else {
+            tma_load_3d(st, ma, &full[s], kb * C::BK, w.m0, 0);                 // 3 A pieces
+          }
           tma_load_3d(st + C::P * C::TILE_A, mb, &full[s], kb * C::BK, w.n0, 0);  // B pieces
         }
       }
@@ -724,12 +762,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
             break;
           }
           // (TMA -> MMA hand-off through the mbarrier needs no tcgen05 fence)
-          const uint64_t da = dA0 + (uint64_t)((s * C::STAGE) >> 4);
-          const uint64_t db = da + (uint64_t)((C::P * C::TILE_A) >> 4);
+          const uint64_t db = dA0 + (uint64_t)((s * C::STAGE + C::P * C::TILE_A) >> 4);
+          uint64_t da = dA0 + (uint64_t)((s * C::STAGE) >> 4);
+          uint32_t apiece = C::TILE_A >> 4, akstep = 2, idk = idesc;
+          if (F == kFmtBF16 && w.d->amn) {
+            const AOperand ao = a_operand<SW>(smem_u32(smem) + s * C::STAGE, true);
+            da = ao.d;
+            apiece = ao.piece;
+            akstep = ao.kstep;
+            idk |= 1u << 15;  // A is MN-major
+          }
 #pragma unroll
           for (int kk = 0; kk < C::KSTEPS; ++kk) {
-            const uint64_t a0 = da + (uint64_t)(kk * 2);
-            const uint64_t a1 = a0 + (uint64_t)(C::TILE_A >> 4);
+            const uint64_t a0 = da + (uint64_t)(kk * akstep);
+            const uint64_t a1 = a0 + (uint64_t)apiece;
             const uint64_t b0 = db + (uint64_t)(kk * 2);
             const uint64_t b1 = b0 + (uint64_t)(C::TILE_B >> 4);
             if constexpr (F == kFmtTF32) {
@@ -738,14 +784,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
               mma_tf32<kColFill>(dt, a0, b1, idesc, 1);
               mma_tf32<kColLast>(dt, a0, b0, idesc, 1);
             } else {
-              const uint64_t a2 = a0 + (uint64_t)(2 * C::TILE_A >> 4);
+              const uint64_t a2 = a0 + (uint64_t)(2 * apiece);
               const uint64_t b2 = b0 + (uint64_t)(2 * C::TILE_B >> 4);
-              mma_bf16<kColNone>(dt, a2, b0, idesc, (kb != kb0 || kk != 0));
-              mma_bf16<kColFill>(dt, a1, b1, idesc, 1);
-              mma_bf16<kColLast>(dt, a1, b0, idesc, 1);
-              mma_bf16<kColFill>(dt, a0, b2, idesc, 1);
-              mma_bf16<kColUse>(dt, a0, b1, idesc, 1);
-              mma_bf16<kColLast>(dt, a0, b0, idesc, 1);
+              mma_bf16<kColNone>(dt, a2, b0, idk, (kb != kb0 || kk != 0));
+              mma_bf16<kColFill>(dt, a1, b1, idk, 1);
+              mma_bf16<kColLast>(dt, a1, b0, idk, 1);
+              mma_bf16<kColFill>(dt, a0, b2, idk, 1);
+              mma_bf16<kColUse>(dt, a0, b1, idk, 1);
+              mma_bf16<kColLast>(dt, a0, b0, idk, 1);
             }
           }
           mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
@@ -1150,12 +1196,13 @@ __device__ __forceinline__ void mma_commit_pair(uint64_t* bar, uint16_t mask) {
 // immediates only.  acc0 = 0 starts a new accumulation.
 template <int SW, int TILE_A, int TILE_B, bool CTA2>
 __device__ __forceinline__ void issue_stage(uint32_t dt, uint64_t da, uint64_t db, uint32_t idesc,
-                                            uint32_t acc0) {
+                                            uint32_t acc0, uint32_t apiece = TILE_A >> 4,
+                                            uint32_t akstep = 2) {
 #pragma unroll
   for (int kk = 0; kk < SW / 32; ++kk) {
-    const uint64_t a0 = da + (uint64_t)(kk * 2);
-    const uint64_t a1 = a0 + (uint64_t)(TILE_A >> 4);
-    const uint64_t a2 = a0 + (uint64_t)(2 * TILE_A >> 4);
+    const uint64_t a0 = da + (uint64_t)(kk * akstep);
+    const uint64_t a1 = a0 + (uint64_t)apiece;
+    const uint64_t a2 = a0 + (uint64_t)(2 * apiece);
     const uint64_t b0 = db + (uint64_t)(kk * 2);
     const uint64_t b1 = b0 + (uint64_t)(TILE_B >> 4);
     const uint64_t b2 = b0 + (uint64_t)(2 * TILE_B >> 4);
@@ -1271,7 +1318,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
         if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * C::STAGE);
         const uint32_t fb = mapa_shared(smem_u32(&full[s]), 0);
         uint8_t* st = smem + s * C::STAGE;
-        tma_load_3d_pair(st, ma, fb, kb * C::BK, ya, 0);                        // 3 A pieces
+        if (w.d->amn) {  // MN-major A: two boxes of 64 M values
+          tma_load_3d_pair(st, ma, fb, ya, kb * C::BK, 0);
+          tma_load_3d_pair(st + kPieces * C::BK * 128, ma, fb, ya + 64, kb * C::BK, 0);
+        } else {
+          tma_load_3d_pair(st, ma, fb, kb * C::BK, ya, 0);                      // 3 A pieces
+        }
         tma_load_3d_pair(st + kPieces * C::TILE_A, mb, fb, kb * C::BK, yb, 0);  // 3 B pieces
       }
     }
@@ -1314,9 +1366,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
           stop = true;
           break;
         }
-        const uint64_t da = dA0 + (uint64_t)((s * C::STAGE) >> 4);
-        const uint64_t db = da + (uint64_t)((kPieces * C::TILE_A) >> 4);
-        issue_stage<SW, C::TILE_A, C::TILE_B, true>(dt, da, db, idesc, kb != kb0);
+        const uint64_t db = dA0 + (uint64_t)((s * C::STAGE + kPieces * C::TILE_A) >> 4);
+        if (w.d->amn) {
+          const AOperand ao = a_operand<SW>(smem_u32(smem) + s * C::STAGE, true);
+          issue_stage<SW, C::TILE_A, C::TILE_B, true>(dt, ao.d, db, idesc | (1u << 15), kb != kb0,
+                                                      ao.piece, ao.kstep);
+        } else {
+          const uint64_t da = dA0 + (uint64_t)((s * C::STAGE) >> 4);
+          issue_stage<SW, C::TILE_A, C::TILE_B, true>(dt, da, db, idesc, kb != kb0);
+        }
         mma_commit_pair(&empty[s], 0x3);  // frees stage s in both CTAs
       }
       if (stop) break;
@@ -1419,30 +1477,31 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pair_kernel(const __grid_const
 // ---------------------------------------------------------------- fused two-mode kernel
 // T = W x_1 Phi_a x_2 Phi_b, the first two factors of the Tucker operator of
 // Eq. 5, in one launch without storing the intermediate.  A unit is one
-// 128 x 128 tile of T (output rows j1 of Phi_a, output rows j2 of Phi_b) of
-// one component and one x3 slab (the whole field in 2D):
+// component and one x3 slab (the whole field in 2D), one 128-row tile a of
+// output rows j1 of Phi_a, and the 128-row tiles of output rows j2 of Phi_b
+// in [b0, b0 + nb): all of them when n2 <= 256 (the tiles then share one
+// intermediate), else one.
 //   MMA1  D1[j1][i2] = sum_{i1} Phi_a[j1][i1] W[i2][i1] for the i2 of the
-//         column support of the tile's Phi_b rows (in groups of up to 256
-//         i2, the D1 columns), over the K-blocks of the Phi_a rows' support;
-//   split the epilogue warps read D1 back 64 i2 at a time and store its three
-//         BF16 pieces into TMEM;
-//   MMA2  D2[j1][j2] += sum_{i2} P[j1][i2] Phi_b[j2][i2], the pieces P read as
-//         the A operand from TMEM and Phi_b's pieces from shared memory;
-//   out   D2 -> T in the natural layout (x1 contiguous), with the epilogue of
-//         the operator's last product.
-// Both products take the six piece products of the split form.  MMA1 runs
-// over the i2 support of 128 rows of Phi_b (up to 256 i2): about twice the
-// products of a separate first pass, in exchange for the intermediate's
+//         union of the tiles' Phi_b column supports, in groups of up to 256
+//         i2 (the D1 columns), over the K-blocks of the Phi_a rows' support;
+//   split the epilogue warps read D1 back 64 i2 (a chunk) at a time and
+//         store its three BF16 pieces into TMEM;
+//   MMA2  per tile: D2[j1][j2] += sum_{i2} P[j1][i2] Phi_b[j2][i2] over the
+//         chunks in the tile's support, the pieces P read as the A operand
+//         from TMEM and Phi_b's pieces from shared memory;
+//   out   per tile: D2 -> T in the natural layout (x1 contiguous), with the
+//         epilogue of the operator's last product, or as pieces.
+// Both products take the six piece products of the split form.  With one
+// j2 tile per unit MMA1 covers up to 256 i2 for 128 output rows: about twice
+// the products of a separate first pass, in exchange for the intermediate's
 // round trip through memory and a launch.
 //
 // Shared memory: a ring of kFStages stages; an MMA1 stage holds one K-block
 // (32 values) of Phi_a's 128 rows and of W's kFRowsW rows, an MMA2 stage two
 // K-blocks of Phi_b's 128 rows.  TMEM (512 columns): D2 [0, 128), D1
-// [128, 384), and two buffers for the pieces of a 64-column chunk of D1 (32
-// columns per piece): buffer 0 at [384, 480), buffer 1 in the columns of D1's
-// first chunk [128, 192) and [480, 512).  Chunk ch of a group uses buffer
-// ch & 1, so buffer 1 is written only once chunk 0 has been read, and the
-// split of one chunk overlaps MMA2 of the previous one.
+// [128, 384), 128 spare columns [384, 512).  The pieces of all chunks of a
+// group coexist (slot_col): each epilogue warp writes only into its half of
+// the spare columns and into D1 columns of its own half that it has read.
 constexpr int kFBK = 32;                               // K values per K-block (64-byte rows)
 constexpr int kFRowsW = 256;                           // W rows per MMA1 stage (D1 columns)
 constexpr int kFTileA = kBM * 64;                      // one piece of Phi_a's block: 8 KB
@@ -1451,10 +1510,18 @@ constexpr int kFTileC = kBM * 64;                      // one piece of a Phi_b b
 constexpr int kFStage = kPieces * (kFTileA + kFTileW);  // 72 KB
 constexpr int kFStages = 3;
 constexpr int kFSmem = kFStages * kFStage + 1024 + 256;
-constexpr uint32_t kFColD2 = 0, kFColD1 = 128, kFColP = 384;
-// TMEM column of piece p of pieces buffer b
-__device__ __forceinline__ uint32_t piece_col(int b, int p) {
-  return b == 0 ? kFColP + 32u * p : (p < 2 ? kFColD1 + 32u * p : 480u);
+constexpr uint32_t kFColD2 = 0, kFColD1 = 128, kFColS = 384;
+// TMEM column of the 16-column slot holding piece p of chunk ch for the
+// epilogue warps of column half h: the 32 i2 values [64 ch + 32 h, +32) of
+// the group, two per column, lower i2 in the low half.  The warp's k-th slot
+// (k = 3 ch + p): k < 4 its half of the spare columns, then the D1 columns
+// of its own half of chunks 0, 1, 2, 3 (32 each), so that chunk ch's pieces
+// land only in columns of chunks <= ch that this warp has already read.
+__device__ __forceinline__ uint32_t slot_col(int ch, int p, int h) {
+  const int k = 3 * ch + p;
+  if (k < 4) return kFColS + 64u * h + 16u * k;
+  const int r = k - 4;
+  return kFColD1 + 64u * (r >> 1) + 32u * h + 16u * (r & 1);
 }
 // Three BF16 pieces of two FP32 values, each level rounded to nearest (the
 // same pieces as split3), packed two per 32-bit word with x0 in the low half.
@@ -1495,10 +1562,11 @@ __device__ __forceinline__ void tmem_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// Unit of the fused kernel: component c, slab s, j1 tile a, j2 tile b.
+// Unit of the fused kernel: component c, slab s, j1 tile a, j2 tiles
+// [b0, b0 + nb).
 struct UnitF {
   const TcPassDesc* d;
-  int c, s, a, b;
+  int c, s, a, b0, nb;
 };
 __device__ __forceinline__ UnitF decode_unitf(const TcLaunch& L, int u) {
   UnitF w;
@@ -1510,16 +1578,18 @@ __device__ __forceinline__ UnitF decode_unitf(const TcLaunch& L, int u) {
     w.d = L.desc + sv;
     r -= __ldg(L.ustart + sv);
   }
+  const int nbg = w.d->tiles_n / w.d->bunit;  // groups of j2 tiles
   w.a = r % w.d->tiles_m;
   r /= w.d->tiles_m;
-  w.b = r % w.d->tiles_n;
-  r /= w.d->tiles_n;
+  w.nb = w.d->bunit;
+  w.b0 = (r % nbg) * w.nb;
+  r /= nbg;
   w.s = r % w.d->slabs;
   w.c = r / w.d->slabs;
   return w;
 }
-// The i2 range [lo, hi) a unit contracts over in MMA2: the column support of
-// its Phi_b rows (multiples of 64, the end clipped to n2), or all of x2.
+// The i2 range [lo, hi) of j2 tile b: the column support of its Phi_b rows
+// (multiples of 64, the end clipped to n2), or all of x2.
 __device__ __forceinline__ void x2_range(const TcPassDesc* d, int c, int b, int& lo, int& hi) {
   lo = 0;
   hi = d->n2;
@@ -1531,6 +1601,25 @@ __device__ __forceinline__ void x2_range(const TcPassDesc* d, int c, int b, int&
     hi = r.y;
   }
 }
+// The union of the ranges of a unit's tiles.
+__device__ __forceinline__ void x2_union(const UnitF& w, int& lo, int& hi) {
+  x2_range(w.d, w.c, w.b0, lo, hi);
+  for (int b = w.b0 + 1; b < w.b0 + w.nb; ++b) {
+    int l, h;
+    x2_range(w.d, w.c, b, l, h);
+    lo = min(lo, l);
+    hi = max(hi, h);
+  }
+}
+// Chunks [c0, c1) of the group starting at g2 (nch chunks) that tile b
+// contracts over.
+__device__ __forceinline__ void tile_chunks(const UnitF& w, int b, int g2, int nch, int& c0,
+                                            int& c1) {
+  int l, h;
+  x2_range(w.d, w.c, b, l, h);
+  c0 = max(0, (l - g2) / 64);
+  c1 = min(nch, (h - g2 + 63) / 64);
+}
 
 template <bool IND = false>
 __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_constant__ TcLaunch L) {
@@ -1540,10 +1629,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
   uint64_t* empty = full + kFStages;
   uint64_t* d1_full = empty + kFStages;  // MMA1 of a group complete (commit)
   uint64_t* d1_free = d1_full + 1;       // the group's D1 read by every epilogue warp
-  uint64_t* p_full = d1_free + 1;        // [2] a chunk's pieces stored (every epilogue warp)
-  uint64_t* p_free = p_full + 2;         // [2] MMA2 of a chunk complete (commit)
-  uint64_t* acc_full = p_free + 2;       // D2 of a unit complete (commit)
-  uint64_t* drain = acc_full + 1;
+  uint64_t* p_full = d1_free + 1;        // [4] chunk ch's pieces stored (every epilogue
+                                         // warp), one phase per group
+  uint64_t* p_done = p_full + 4;         // every MMA2 of a group complete (commit)
+  uint64_t* acc_full = p_done + 1;       // D2 of a tile complete (commit)
+  uint64_t* acc_empty = acc_full + 1;    // D2 of a tile read by every epilogue warp
+  uint64_t* drain = acc_empty + 1;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   int* abort_flag = (int*)(tmem_slot + 1);
 
@@ -1557,11 +1648,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
     }
     mbar_init(d1_full, 1);
     mbar_init(d1_free, kEpiWarps);
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&p_full[b], kEpiWarps);
-      mbar_init(&p_free[b], 1);
-    }
+    for (int ch = 0; ch < 4; ++ch) mbar_init(&p_full[ch], kEpiWarps);
+    mbar_init(p_done, 1);
     mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kEpiWarps);
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1577,8 +1667,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
   volatile int* abort_v = abort_flag;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer: per group the MMA1 K-blocks, then the
-    // Phi_b blocks of its chunks, in the order the MMA thread consumes them
+    // ---------------- TMA producer: per group the MMA1 K-blocks, then per
+    // tile the Phi_b blocks of its chunks, in the order the MMA thread
+    // consumes them
     uint32_t g = 0;
     bool stop = false, waited = false;
     auto next_stage = [&](uint32_t bytes) -> uint8_t* {
@@ -1606,11 +1697,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)ma) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mw) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mc) : "memory");
-      int kb0, kb1, x2lo, x2hi;
+      int kb0, kb1, xlo, xhi;
       k_blocks(D, w.c, w.a * kBM, kFBK, kb0, kb1);
-      x2_range(D, w.c, w.b, x2lo, x2hi);
-      for (int g2 = x2lo; g2 < x2hi && !stop; g2 += kFRowsW) {
-        const int nch = (min(kFRowsW, x2hi - g2) + 63) / 64;
+      x2_union(w, xlo, xhi);
+      for (int g2 = xlo; g2 < xhi && !stop; g2 += kFRowsW) {
+        const int nch = (min(kFRowsW, xhi - g2) + 63) / 64;
         for (int kb = kb0; kb < kb1 && !stop; ++kb, ++g) {
           uint8_t* st = next_stage(kFStage);
           if (!st) break;
@@ -1618,12 +1709,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
           tma_load_3d(st + kPieces * kFTileA, mw, &full[g % kFStages], kb * kFBK,
                       w.s * D->n2 + g2, 0);
         }
-        for (int ch = 0; ch < nch && !stop; ++ch, ++g) {
-          uint8_t* st = next_stage(2 * kPieces * kFTileC);
-          if (!st) break;
-          tma_load_3d(st, mc, &full[g % kFStages], g2 + ch * 64, w.b * kBM, 0);
-          tma_load_3d(st + kPieces * kFTileC, mc, &full[g % kFStages], g2 + ch * 64 + kFBK,
-                      w.b * kBM, 0);
+        for (int b = w.b0; b < w.b0 + w.nb && !stop; ++b) {
+          int c0, c1;
+          tile_chunks(w, b, g2, nch, c0, c1);
+          for (int ch = c0; ch < c1 && !stop; ++ch, ++g) {
+            uint8_t* st = next_stage(2 * kPieces * kFTileC);
+            if (!st) break;
+            tma_load_3d(st, mc, &full[g % kFStages], g2 + ch * 64, b * kBM, 0);
+            tma_load_3d(st + kPieces * kFTileC, mc, &full[g % kFStages], g2 + ch * 64 + kFBK,
+                        b * kBM, 0);
+          }
         }
       }
     }
@@ -1634,38 +1729,35 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
     // ---------------- MMA issuer
     const uint64_t dS0 = kmajor_desc<64>(smem_u32(smem));
     const uint32_t idesc2 = idesc_bf16(kBM, kBM);
-    uint32_t g = 0, grp = 0;
-    uint32_t uses[2] = {0, 0};  // completed uses of each pieces buffer
+    uint32_t g = 0, grp = 0, nt = 0;
     bool stop = false;
-    auto wait_full = [&]() -> bool {
-      if (!mbar_wait(&full[g % kFStages], (g / kFStages) & 1)) {
-        atomicCAS(L.err, 0, kErrTimeoutFull);
-        *abort_v = 1;
-        stop = true;
-      }
-      return !stop;
+    auto fail = [&](int code) {
+      atomicCAS(L.err, 0, code);
+      *abort_v = 1;
+      stop = true;
     };
     for (int u = blockIdx.x; u < L.nunits && !stop; u += gridDim.x) {
       const UnitF w = decode_unitf(L, u);
       const TcPassDesc* D = w.d;
-      int kb0, kb1, x2lo, x2hi;
+      int kb0, kb1, xlo, xhi;
       k_blocks(D, w.c, w.a * kBM, kFBK, kb0, kb1);
-      x2_range(D, w.c, w.b, x2lo, x2hi);
-      bool first2 = true;
-      for (int g2 = x2lo; g2 < x2hi && !stop; g2 += kFRowsW, ++grp) {
-        const int nch = (min(kFRowsW, x2hi - g2) + 63) / 64;
-        // D1 is free once the epilogue warps have read the previous group
-        // and MMA2 has read pieces buffer 1 (inside D1) for the last time
-        if (grp > 0 && (!mbar_wait(d1_free, (grp - 1) & 1) ||
-                        (uses[1] > 0 && !mbar_wait(&p_free[1], (uses[1] - 1) & 1)))) {
-          atomicCAS(L.err, 0, kErrTimeoutDone);
-          *abort_v = 1;
+      x2_union(w, xlo, xhi);
+      for (int g2 = xlo; g2 < xhi && !stop; g2 += kFRowsW, ++grp) {
+        const int nch = (min(kFRowsW, xhi - g2) + 63) / 64;
+        const bool first_group = g2 == xlo, last_group = g2 + kFRowsW >= xhi;
+        // D1 and the pieces' columns are free once the epilogue warps have
+        // read the previous group's D1 and its MMA2 have completed
+        if (grp > 0 && (!mbar_wait(d1_free, (grp - 1) & 1) || !mbar_wait(p_done, (grp - 1) & 1))) {
+          fail(kErrTimeoutDone);
           break;
         }
         tc_fence_after();
         const uint32_t idesc1 = idesc_bf16(kBM, 64 * nch);
         for (int kb = kb0; kb < kb1; ++kb, ++g) {
-          if (!wait_full()) break;
+          if (!mbar_wait(&full[g % kFStages], (g / kFStages) & 1)) {
+            fail(kErrTimeoutFull);
+            break;
+          }
           const uint64_t da = dS0 + (uint64_t)(((g % kFStages) * kFStage) >> 4);
           const uint64_t db = da + (uint64_t)((kPieces * kFTileA) >> 4);
           issue_stage<64, kFTileA, kFTileW, false>(tmem + kFColD1, da, db, idesc1, kb != kb0);
@@ -1673,42 +1765,59 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
         }
         if (stop) break;
         mma_commit(d1_full);
-        for (int ch = 0; ch < nch; ++ch, ++g) {
-          const int pb = ch & 1;
-          if (!mbar_wait(&p_full[pb], uses[pb] & 1)) {
-            atomicCAS(L.err, 0, kErrTimeoutDone);
-            *abort_v = 1;
-            stop = true;
+        uint32_t ready = 0;  // chunks of this group whose pieces are known to be stored
+        for (int b = w.b0; b < w.b0 + w.nb && !stop; ++b) {
+          int c0, c1;
+          tile_chunks(w, b, g2, nch, c0, c1);
+          // D2 is free once the epilogue warps have read the previous tile
+          if (first_group && nt > 0 && !mbar_wait(acc_empty, (nt - 1) & 1)) {
+            fail(kErrTimeoutDone);
             break;
           }
-          tc_fence_after();
-          if (!wait_full()) break;
-          const uint64_t db0 = dS0 + (uint64_t)(((g % kFStages) * kFStage) >> 4);
+          for (int ch = c0; ch < c1; ++ch, ++g) {
+            if (!(ready >> ch & 1u)) {
+              if (!mbar_wait(&p_full[ch], grp & 1)) {
+                fail(kErrTimeoutDone);
+                break;
+              }
+              ready |= 1u << ch;
+            }
+            tc_fence_after();
+            if (!mbar_wait(&full[g % kFStages], (g / kFStages) & 1)) {
+              fail(kErrTimeoutFull);
+              break;
+            }
+            const uint64_t db0 = dS0 + (uint64_t)(((g % kFStages) * kFStage) >> 4);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t b0 = db0 + (uint64_t)(((kk >> 1) * kPieces * kFTileC) >> 4) +
-                                (uint64_t)((kk & 1) * 2);
-            const uint64_t b1 = b0 + (uint64_t)(kFTileC >> 4);
-            const uint64_t b2 = b0 + (uint64_t)(2 * kFTileC >> 4);
-            const uint32_t a0 = tmem + piece_col(pb, 0) + (uint32_t)(kk * 8);
-            const uint32_t a1 = tmem + piece_col(pb, 1) + (uint32_t)(kk * 8);
-            const uint32_t a2 = tmem + piece_col(pb, 2) + (uint32_t)(kk * 8);
-            const uint32_t dt = tmem + kFColD2;
-            mma_bf16_ts(dt, a2, b0, idesc2, (first2 && kk == 0) ? 0u : 1u);
-            mma_bf16_ts(dt, a1, b1, idesc2, 1);
-            mma_bf16_ts(dt, a1, b0, idesc2, 1);
-            mma_bf16_ts(dt, a0, b2, idesc2, 1);
-            mma_bf16_ts(dt, a0, b1, idesc2, 1);
-            mma_bf16_ts(dt, a0, b0, idesc2, 1);
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t b0 = db0 + (uint64_t)(((kk >> 1) * kPieces * kFTileC) >> 4) +
+                                  (uint64_t)((kk & 1) * 2);
+              const uint64_t b1 = b0 + (uint64_t)(kFTileC >> 4);
+              const uint64_t b2 = b0 + (uint64_t)(2 * kFTileC >> 4);
+              const uint32_t sub = (uint32_t)((kk & 1) * 8);
+              const uint32_t a0 = tmem + slot_col(ch, 0, kk >> 1) + sub;
+              const uint32_t a1 = tmem + slot_col(ch, 1, kk >> 1) + sub;
+              const uint32_t a2 = tmem + slot_col(ch, 2, kk >> 1) + sub;
+              const uint32_t dt = tmem + kFColD2;
+              const uint32_t acc = (first_group && ch == c0 && kk == 0) ? 0u : 1u;
+              mma_bf16_ts(dt, a2, b0, idesc2, acc);
+              mma_bf16_ts(dt, a1, b1, idesc2, 1);
+              mma_bf16_ts(dt, a1, b0, idesc2, 1);
+              mma_bf16_ts(dt, a0, b2, idesc2, 1);
+              mma_bf16_ts(dt, a0, b1, idesc2, 1);
+              mma_bf16_ts(dt, a0, b0, idesc2, 1);
+            }
+            mma_commit(&empty[g % kFStages]);
           }
-          first2 = false;
-          mma_commit(&empty[g % kFStages]);
-          mma_commit(&p_free[pb]);
-          ++uses[pb];
+          if (stop) break;
+          if (last_group) {
+            mma_commit(acc_full);
+            ++nt;
+          }
         }
+        if (stop) break;
+        mma_commit(p_done);
       }
-      if (stop) break;
-      mma_commit(acc_full);
     }
     mma_commit(drain);
     mbar_wait(drain, 0);
@@ -1718,38 +1827,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
     const int q = warp & 3;            // TMEM lane quarter
     const int half = (warp - 2) >> 2;  // column half
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    uint32_t grp = 0;
-    uint32_t uses[2] = {0, 0};  // stores into each pieces buffer so far
-    int i = 0;
+    uint32_t grp = 0, nt = 0;
     bool stop = false;
-    for (int u = blockIdx.x; u < L.nunits && !stop; u += gridDim.x, ++i) {
+    auto warp_wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+      if (__all_sync(0xffffffffu, mbar_wait_sleep(bar, parity))) return true;
+      if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
+      *abort_v = 1;
+      stop = true;
+      return false;
+    };
+    auto arrive = [&](uint64_t* bar) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+    };
+    for (int u = blockIdx.x; u < L.nunits && !stop; u += gridDim.x) {
       const UnitF w = decode_unitf(L, u);
       const TcPassDesc* D = w.d;
-      int x2lo, x2hi;
-      x2_range(D, w.c, w.b, x2lo, x2hi);
-      for (int g2 = x2lo; g2 < x2hi && !stop; g2 += kFRowsW, ++grp) {
-        const int nch = (min(kFRowsW, x2hi - g2) + 63) / 64;
-        if (!__all_sync(0xffffffffu, mbar_wait_sleep(d1_full, grp & 1))) {
-          if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
-          *abort_v = 1;
-          stop = true;
-          break;
-        }
+      int xlo, xhi;
+      x2_union(w, xlo, xhi);
+      for (int g2 = xlo; g2 < xhi && !stop; g2 += kFRowsW, ++grp) {
+        const int nch = (min(kFRowsW, xhi - g2) + 63) / 64;
+        // the slots are free once the previous group's MMA2 have completed
+        if (grp > 0 && !warp_wait(p_done, (grp - 1) & 1)) break;
+        if (!warp_wait(d1_full, grp & 1)) break;
         tc_fence_after();
         for (int ch = 0; ch < nch; ++ch) {
-          const int pb = ch & 1;
-          // buffer pb is free once MMA2 has read its previous contents; buffer
-          // 1 lies in D1's first chunk, which every warp must have read
-          bool ok = true;
-          if (uses[pb] > 0) ok = mbar_wait_sleep(&p_free[pb], (uses[pb] - 1) & 1);
-          if (ok && ch == 1) ok = mbar_wait_sleep(&p_full[0], (uses[0] - 1) & 1);
-          if (!__all_sync(0xffffffffu, ok)) {
-            if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
-            *abort_v = 1;
-            stop = true;
-            break;
-          }
-          tc_fence_after();
           uint32_t r[2][16];
           const uint32_t src = tmem + lane_off + kFColD1 + (uint32_t)(ch * 64 + half * 32);
           tmem_ld16_nw(src, r[0]);
@@ -1757,106 +1861,98 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
           tmem_wait_ld();
           tmem_fence16(r[0]);
           tmem_fence16(r[1]);
-          // pieces of 32 consecutive i2, two BF16 per 32-bit column (the
-          // lower i2 in the low half)
           uint32_t pk[3][16];
 #pragma unroll
           for (int j = 0; j < 16; ++j)
             split3_pair(__uint_as_float(r[j / 8][(2 * j) % 16]),
                         __uint_as_float(r[j / 8][(2 * j + 1) % 16]), pk[0][j], pk[1][j], pk[2][j]);
 #pragma unroll
-          for (int p = 0; p < 3; ++p)
-            tmem_st16(tmem + lane_off + piece_col(pb, p) + (uint32_t)(half * 16), pk[p]);
+          for (int p = 0; p < 3; ++p) tmem_st16(tmem + lane_off + slot_col(ch, p, half), pk[p]);
           tmem_wait_st();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0)
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&p_full[pb]))
-                         : "memory");
-          ++uses[pb];
+          arrive(&p_full[ch]);
         }
-        if (stop) break;
-        // every D1 column of this group has been read
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0)
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(d1_free))
-                       : "memory");
+        arrive(d1_free);  // every D1 column of this group has been read
       }
       if (stop) break;
-      // ---- T of the unit
+      // ---- T, one j2 tile at a time
       const int n1 = D->n1, n2 = D->n2, mode = D->mode;
       const int m = w.a * kBM + q * 32 + lane;  // j1
       const bool mrow = m < n1;
-      const int n0 = w.b * kBM + half * 64;     // first j2 of this warp
       const int64_t slab = (int64_t)w.s * n2 * n1;
       float* lp = (mode == kAxpy && D->lo[w.c]) ? D->lo[w.c] + slab : nullptr;
       double* ind = (IND && mode == kAxpy) ? indicator_slot(D, w.c) : nullptr;
       const float* bsrc = D->base[w.c] ? D->base[w.c] + slab : nullptr;
       const bool plain = mode == kAxpy && !lp && !ind;
-      // plain update: this warp's 64 base values are loaded while the last
-      // MMA2 runs
-      float bv[64];
-#pragma unroll
-      for (int j = 0; j < 64; ++j) {
-        const int col = n0 + j;
-        bv[j] = (plain && bsrc && mrow && col < n2) ? __ldg(bsrc + (int64_t)col * n1 + m) : 0.f;
-      }
-      if (!__all_sync(0xffffffffu, mbar_wait_sleep(acc_full, i & 1))) {
-        if (lane == 0) atomicCAS(L.err, 0, kErrTimeoutDone);
-        *abort_v = 1;
-        break;
-      }
-      tc_fence_after();
-      if (__any_sync(0xffffffffu, *abort_v)) break;
       const uint32_t ta = tmem + lane_off + kFColD2 + (uint32_t)(half * 64);
-      if (plain) {
-        float* of = D->outf[w.c] + slab;
-        const float alpha = D->alpha;
+      for (int b = w.b0; b < w.b0 + w.nb && !stop; ++b, ++nt) {
+        const int n0 = b * kBM + half * 64;  // first j2 of this warp
+        // plain update: the warp's 64 base values are loaded before D2 is ready
+        float bv[64];
 #pragma unroll
-        for (int bt = 0; bt < 4; bt += 2) {
-          uint32_t r[2][16];
-          tmem_ld16_nw(ta + (uint32_t)(bt * 16), r[0]);
-          tmem_ld16_nw(ta + (uint32_t)((bt + 1) * 16), r[1]);
-          tmem_wait_ld();
-          tmem_fence16(r[0]);
-          tmem_fence16(r[1]);
-#pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            const int col = n0 + bt * 16 + jj;
-            if (mrow && col < n2)
-              of[(int64_t)col * n1 + m] =
-                  __fmaf_rn(alpha, __uint_as_float(r[jj / 16][jj % 16]), bv[bt * 16 + jj]);
-          }
+        for (int j = 0; j < 64; ++j) {
+          const int col = n0 + j;
+          bv[j] = (plain && bsrc && mrow && col < n2) ? __ldg(bsrc + (int64_t)col * n1 + m) : 0.f;
         }
-      } else if (mode == kAxpy) {
-        axpy_epilogue<4>(ta, D->outf[w.c] + slab, bsrc, lp, D->alpha, n1, n2, n0, m, mrow, ind,
-                         D->ind_n1, D->ind_n2);
-      } else {  // kPieces3: three BF16 pieces of T, natural layout
-        __nv_bfloat16* op = D->outp[w.c];
-        const int64_t plane = (int64_t)D->slabs * n2 * n1;
-#pragma unroll 1
-        for (int bt = 0; bt < 4; ++bt) {
-          uint32_t r[16];
-          tmem_ld16_nw(ta + (uint32_t)(bt * 16), r);
-          tmem_wait_ld();
-          tmem_fence16(r);
+        if (!warp_wait(acc_full, nt & 1)) break;
+        tc_fence_after();
+        if (__any_sync(0xffffffffu, *abort_v)) {
+          stop = true;
+          break;
+        }
+        if (plain) {
+          float* of = D->outf[w.c] + slab;
+          const float alpha = D->alpha;
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int col = n0 + bt * 16 + jj;
-            if (mrow && col < n2) {
-              const int64_t o = slab + (int64_t)col * n1 + m;
-              __nv_bfloat16 b0, b1, b2;
-              split3(__uint_as_float(r[jj]), b0, b1, b2);
-              op[o] = b0;
-              op[plane + o] = b1;
-              op[2 * plane + o] = b2;
+          for (int bt = 0; bt < 4; bt += 2) {
+            uint32_t r[2][16];
+            tmem_ld16_nw(ta + (uint32_t)(bt * 16), r[0]);
+            tmem_ld16_nw(ta + (uint32_t)((bt + 1) * 16), r[1]);
+            tmem_wait_ld();
+            tmem_fence16(r[0]);
+            tmem_fence16(r[1]);
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              const int col = n0 + bt * 16 + jj;
+              if (mrow && col < n2)
+                of[(int64_t)col * n1 + m] =
+                    __fmaf_rn(alpha, __uint_as_float(r[jj / 16][jj % 16]), bv[bt * 16 + jj]);
+            }
+          }
+        } else if (mode == kAxpy) {
+          axpy_epilogue<4>(ta, D->outf[w.c] + slab, bsrc, lp, D->alpha, n1, n2, n0, m, mrow, ind,
+                           D->ind_n1, D->ind_n2);
+        } else {  // kPieces3: three BF16 pieces of T, natural layout
+          // Lanes pair up (rows m, m + 1; n1 is even): of two columns the even
+          // lane takes the first and the odd lane the second, each with both
+          // rows, so every store writes two BF16 of one piece (4 bytes)
+          uint32_t* op = reinterpret_cast<uint32_t*>(D->outp[w.c]);
+          const int64_t plane2 = (int64_t)D->slabs * n2 * n1 / 2;
+          const bool odd = lane & 1;
+          const int mp = m - (odd ? 1 : 0);
+#pragma unroll 1
+          for (int bt = 0; bt < 4; ++bt) {
+            uint32_t r[16];
+            tmem_ld16_nw(ta + (uint32_t)(bt * 16), r);
+            tmem_wait_ld();
+            tmem_fence16(r);
+#pragma unroll
+            for (int jj = 0; jj < 16; jj += 2) {
+              const float x0 = __uint_as_float(r[jj]), x1 = __uint_as_float(r[jj + 1]);
+              const float got = __shfl_xor_sync(0xffffffffu, odd ? x0 : x1, 1);
+              const int col = n0 + bt * 16 + jj + (odd ? 1 : 0);
+              if (mp < n1 && col < n2) {
+                uint32_t w0, w1, w2;
+                split3_pair(odd ? got : x0, odd ? x1 : got, w0, w1, w2);
+                const int64_t o2 = (slab + (int64_t)col * n1 + mp) >> 1;
+                op[o2] = w0;
+                op[plane2 + o2] = w1;
+                op[2 * plane2 + o2] = w2;
+              }
             }
           }
         }
+        arrive(acc_empty);  // D2 of this tile has been read
       }
-      tc_fence_before();
-      __syncwarp();
     }
   }
   tc_fence_before();
@@ -2574,6 +2670,19 @@ cudaError_t encode_pieces(CUtensorMap* map, const void* base, int64_t K, int64_t
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// [3][K][M] BF16 pieces read MN-major (M contiguous): box {64, bk, 3} with
+// 128-byte swizzle, two boxes per 128-row tile.
+cudaError_t encode_pieces_mn(CUtensorMap* map, const void* base, int64_t M, int64_t K, int bk) {
+  cuuint64_t dims[3] = {(cuuint64_t)M, (cuuint64_t)K, (cuuint64_t)kPieces};
+  cuuint64_t strides[2] = {(cuuint64_t)M * 2, (cuuint64_t)(M * K) * 2};
+  cuuint32_t box[3] = {64, (cuuint32_t)bk, (cuuint32_t)kPieces};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Kernel variants (swizzle width, tile width, CTA pair).  Pair variants run
 // tc_pair_kernel: 256-row tiles over two SMs.
 struct Variant {
@@ -2811,6 +2920,7 @@ struct TcPass {
   int pair;
   int out, base, alpha;
   int fused;  // 1: modes 1 and 2 in one launch (tc_fused_kernel); mu = 0
+  int amn;    // 1: reads the fused pass's natural-layout pieces as an MN-major A (mu = 2)
 };
 
 // One launch of the step sequence.
@@ -2845,6 +2955,7 @@ struct TcState {
   int fused12;
   CUtensorMap fa[2][3], fc[2][3];  // [c][ell]
   CUtensorMap fw[2][2];            // [b][c]
+  CUtensorMap amn_map[2][2];       // [b][c] 3D: buffer b as [piece][x3][x2 x1], 64 x BK boxes
   int variant;
   int fmt;       // operand format: kFmtBF16 (three BF16 pieces) or kFmtTF32 (two TF32 pieces)
   int fuse;      // 1: fuse the stage-1 combination into the last stage-1 product
@@ -2880,9 +2991,9 @@ struct TcState {
 };
 
 static int units_of(const TcState* S, const TcPass& ps, int bn) {
-  if (ps.fused) {
+  if (ps.fused) {  // one unit per j1 tile and (when n2 > 256) j2 tile
     const int64_t n1 = S->n[0], n2 = S->n[1], slabs = S->N / (n1 * n2);
-    return (int)(2 * slabs * ((n1 + kBM - 1) / kBM) * ((n2 + kBM - 1) / kBM));
+    return (int)(2 * slabs * ((n1 + kBM - 1) / kBM) * (n2 <= kFRowsW ? 1 : (n2 + kBM - 1) / kBM));
   }
   const int64_t nmu = S->n[ps.mu];
   const int64_t M = S->N / nmu;
@@ -2904,12 +3015,13 @@ static TcPassDesc make_desc(const TcState* S, const adr_plan_s* P, const TcPass&
   D.tiles_n = (D.N + bn - 1) / bn;
   D.pair = ps.pair;
   D.mode = ps.mode;
+  D.amn = ps.amn;
   D.rx = P->pwf.rx;
   float* stage[2] = {(float*)P->u2, (float*)P->v2};
   float* state[2] = {u, v};
   const double tau = P->prob.tau;
   for (int c = 0; c < 2; ++c) {
-    D.amap[c] = S->amap[ps.b][c][ps.mu];
+    D.amap[c] = ps.amn ? S->amn_map[ps.b][c] : S->amap[ps.b][c][ps.mu];
     D.bmap[c] = S->bmap[c][ps.mu][ps.ell];
     D.kband[c] = S->ksupport ? S->kband[c][ps.mu][ps.ell] : nullptr;
     D.outp[c] = S->buf[1 - ps.b][c];
@@ -2940,6 +3052,7 @@ static TcPassDesc make_desc(const TcState* S, const adr_plan_s* P, const TcPass&
     D.K = D.n1;
     D.tiles_m = (D.n1 + kBM - 1) / kBM;
     D.tiles_n = (D.n2 + kBM - 1) / kBM;
+    D.bunit = D.n2 <= kFRowsW ? D.tiles_n : 1;  // the tiles of x2 share one intermediate
     for (int c = 0; c < 2; ++c) {
       D.amap[c] = S->fa[c][ps.ell];
       D.bmap[c] = S->fw[ps.b][c];
@@ -3148,9 +3261,11 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     S->fuse = f >= 0 && f <= 2 ? f : 0;
   }
   if (kVariants[S->variant].cta2) S->fuse = 0;  // the CTA-pair kernel has neither epilogue
-  // 2D grids with BF16 pieces: each Tucker operator as one fused two-mode
-  // launch (ADR_TC_FUSED=0: one launch per direction)
-  S->fused12 = d == 2 && prec == ADR_BF16X3;
+  // BF16 pieces: the first two directions of each Tucker operator as one
+  // fused launch (2D: the whole operator; 3D: then the x3 product on the
+  // fused pass's natural-layout output read MN-major).  ADR_TC_FUSED=0: one
+  // launch per direction.
+  S->fused12 = (d == 2 || d == 3) && prec == ADR_BF16X3;
   if (const char* ev = getenv("ADR_TC_FUSED")) S->fused12 = S->fused12 && atoi(ev) != 0;
   if (S->fused12) S->fuse = 0;
   S->comp = scheme == ADR_ETD2RKDS ? comp : 0;
@@ -3253,6 +3368,8 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
       }
       for (int b = 0; b < 2; ++b) {
         e = encode_pieces(&S->fw[b][c], S->buf[b][c], n[0], S->N / n[0], kFRowsW, 64, S->fmt);
+        if (e == cudaSuccess && d == 3)
+          e = encode_pieces_mn(&S->amn_map[b][c], S->buf[b][c], S->N / n[2], n[2], sw / 2);
         if (e != cudaSuccess) return e;
       }
     }
@@ -3261,9 +3378,17 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
   S->scheme = scheme;
   auto add_tucker = [&](int ell, int last_out, int last_base, int last_alpha, int stage1_fuse) {
     int b = 0;
-    if (S->fused12) {  // one launch: reads buffer 0, writes the operator's result
-      TcPass ps{0, 0, ell, kAxpy, 0, last_out, last_base, last_alpha, 1};
-      S->passes.push_back(ps);
+    if (S->fused12) {  // reads buffer 0; 2D: writes the operator's result
+      if (d == 3) {    // modes 1 and 2 to pieces in buffer 1, then mode 3 from them
+        TcPass f{0, 0, ell, kPieces3, 0, kOutPieces, kBaseNone, kAlphaOne, 1, 0};
+        S->passes.push_back(f);
+        S->ops.push_back({kOpTc, (int)S->passes.size() - 1, 0.f});
+        TcPass m3{1, 2, ell, kAxpy, 0, last_out, last_base, last_alpha, 0, 1};
+        S->passes.push_back(m3);
+      } else {
+        TcPass f{0, 0, ell, kAxpy, 0, last_out, last_base, last_alpha, 1, 0};
+        S->passes.push_back(f);
+      }
       S->ops.push_back({kOpTc, (int)S->passes.size() - 1, 0.f});
       return 1;
     }
@@ -3299,8 +3424,16 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
     // or from the buffer the fused epilogue wrote
     const int b2 = S->fuse ? b1 : 0;
     if (S->fused12) {
-      TcPass ps{b2, 0, 2, kAxpy, 0, kOutState, kBaseStage, kAlphaTauD, 1};
-      S->passes.push_back(ps);
+      if (d == 3) {
+        TcPass f{b2, 0, 2, kPieces3, 0, kOutPieces, kBaseNone, kAlphaOne, 1, 0};
+        S->passes.push_back(f);
+        S->ops.push_back({kOpTc, (int)S->passes.size() - 1, 0.f});
+        TcPass m3{1 - b2, 2, 2, kAxpy, 0, kOutState, kBaseStage, kAlphaTauD, 0, 1};
+        S->passes.push_back(m3);
+      } else {
+        TcPass f{b2, 0, 2, kAxpy, 0, kOutState, kBaseStage, kAlphaTauD, 1, 0};
+        S->passes.push_back(f);
+      }
       S->ops.push_back({kOpTc, (int)S->passes.size() - 1, 0.f});
     }
     for (int mu = 0, b = b2; mu < d && !S->fused12; ++mu, b ^= 1) {
@@ -3319,16 +3452,18 @@ cudaError_t tc_prepare(TcOperands* t, int prec, int scheme, int d, const int64_t
   for (int p = 0; p < np; ++p) S->units[p] = units_of(S, S->passes[p], bn);
   S->rhs_blocks = rhs_blocks_of(S);
   S->rdiff_blocks = rdiff_blocks_of(S);
-  e = cudaStreamSynchronize(s);  // the split matrices are complete
-  if (e != cudaSuccess) return e;
+  // host copies of the supports, ordered on the plan's stream (a copy on the
+  // legacy stream would wait for every other stream's queued work)
   for (int c = 0; c < 2; ++c)
     for (int m = 0; m < d; ++m)
       for (int l = 0; l < 3; ++l)
         if (!S->hband[c][m][l].empty()) {
-          e = cudaMemcpy(S->hband[c][m][l].data(), S->kband[c][m][l],
-                         sizeof(int2) * S->hband[c][m][l].size(), cudaMemcpyDeviceToHost);
+          e = cudaMemcpyAsync(S->hband[c][m][l].data(), S->kband[c][m][l],
+                              sizeof(int2) * S->hband[c][m][l].size(), cudaMemcpyDeviceToHost, s);
           if (e != cudaSuccess) return e;
         }
+  e = cudaStreamSynchronize(s);  // the split matrices and the supports' copies are complete
+  if (e != cudaSuccess) return e;
   S->bound_u = S->bound_v = nullptr;
   t->ready = 1;
   return cudaSuccess;
@@ -3581,25 +3716,44 @@ void tc_mode_macs(const TcOperands* t, double* dense, double* computed) {
   for (const TcPass& ps : S->passes) {
     if (ps.fused) {  // both products of tc_fused_kernel, as its loops run them
       const int64_t n1 = S->n[0], n2 = S->n[1], slabs = S->N / (n1 * n2);
+      const int64_t tn = (n2 + kBM - 1) / kBM, bunit = n2 <= kFRowsW ? tn : 1;
       for (int c = 0; c < 2; ++c) {
         *dense += (double)slabs * ((double)n1 * n1 * n2 + (double)n2 * n2 * n1);
         const std::vector<int2>& ba = S->ksupport ? S->hband[c][0][ps.ell] : none;
         const std::vector<int2>& bb = S->ksupport ? S->hband[c][1][ps.ell] : none;
+        auto range = [&](int64_t b, int64_t& lo, int64_t& hi) {
+          lo = 0;
+          hi = n2;
+          if (!bb.empty() && bb[b].x < bb[b].y) {
+            lo = bb[b].x;
+            hi = bb[b].y;
+          }
+        };
         for (int64_t a = 0; a * kBM < n1; ++a) {
           int64_t kb0, kb1;
           host_k_blocks(ba, n1, a * kBM, kFBK, kb0, kb1);
           const double rows = (double)std::min<int64_t>(kBM, n1 - a * kBM);
           const double kin = (double)(std::min(kb1 * kFBK, n1) - kb0 * kFBK);
-          for (int64_t b = 0; b * kBM < n2; ++b) {
-            int64_t lo = 0, hi = n2;
-            if (!bb.empty() && bb[b].x < bb[b].y) {
-              lo = bb[b].x;
-              hi = bb[b].y;
+          for (int64_t b0 = 0; b0 < tn; b0 += bunit) {
+            int64_t lo, hi;
+            range(b0, lo, hi);
+            for (int64_t b = b0 + 1; b < b0 + bunit; ++b) {
+              int64_t l, h;
+              range(b, l, h);
+              lo = std::min(lo, l);
+              hi = std::max(hi, h);
             }
-            const double cols = (double)std::min<int64_t>(kBM, n2 - b * kBM);
             for (int64_t g2 = lo; g2 < hi; g2 += kFRowsW) {
-              const int64_t w = 64 * ((std::min<int64_t>(kFRowsW, hi - g2) + 63) / 64);
-              *computed += (double)slabs * (rows * (double)w * kin + rows * cols * (double)w);
+              const int64_t nch = (std::min<int64_t>(kFRowsW, hi - g2) + 63) / 64;
+              *computed += (double)slabs * rows * (double)(64 * nch) * kin;  // MMA1
+              for (int64_t b = b0; b < b0 + bunit; ++b) {                   // MMA2 per tile
+                int64_t l, h;
+                range(b, l, h);
+                const int64_t c0 = std::max<int64_t>(0, (l - g2) / 64);
+                const int64_t c1 = std::min<int64_t>(nch, (h - g2 + 63) / 64);
+                const double cols = (double)std::min<int64_t>(kBM, n2 - b * kBM);
+                if (c1 > c0) *computed += (double)slabs * rows * cols * (double)(64 * (c1 - c0));
+              }
             }
           }
         }

@@ -1,12 +1,17 @@
 """Fused two-mode products (modes 1 and 2 of the Tucker operator, Eq. 5, in
 one launch; the intermediate stays in TMEM) against the FP64 oracle.
 
-On 2D grids with BF16x3 products every Tucker operator runs as one fused
-launch by default.  Covered here: grids that are not multiples of the 128 x
-128 tile, grids smaller than one tile, x2 ranges wider than the kernel's 256
-intermediate columns (several groups per tile), each reaction model and both
-schemes, the compensated state, and agreement with the per-direction launches
-(ADR_TC_FUSED=0) to rounding level.
+With BF16x3 products the first two directions of every Tucker operator run
+as one fused launch by default: the whole operator on 2D grids; on 3D grids
+the fused launch works on every x3 slab and writes its pieces in the natural
+layout, and the x3 product reads them as an MN-major operand.
+
+Covered here: grids that are not multiples of the 128 x 128 tile, grids
+smaller than one tile, x2 ranges wider than the kernel's 256 intermediate
+columns (several groups per tile), each reaction model and both schemes, the
+compensated state, every per-direction kernel for the x3 product, and
+agreement with the per-direction launches (ADR_TC_FUSED=0) to rounding level,
+in 2D and 3D.
 """
 import numpy as np
 import pytest
@@ -137,3 +142,62 @@ def test_fused_agrees_with_per_direction_launches(adr, n, monkeypatch):
     assert std["kernels"]["mode_product_tc"]["count"] == 4 * p.nsteps
     assert oracle.max_rel_err(U, V, Ud, Vd) <= 1e-6
     assert np.isfinite(U).all() and np.isfinite(V).all()
+
+
+def problem3(n, model, nsteps=6, scheme=wl.ETD2RKDS, state=wl.STATE_AUTO, seed=61):
+    return wl.Problem(d=3, n=n, lo=(0.0,) * 3, hi=(1.0,) * 3, diff=(0.02, 0.1),
+                      adv=((0.2, -0.1, 0.3), (-0.2, 0.1, 0.05)), model=model, params=PARAMS[model],
+                      tau=2e-3, nsteps=nsteps, precision=wl.BF16X3, seed=seed, scheme=scheme,
+                      state=state)
+
+
+@pytest.mark.parametrize("n,model", [((40, 24, 56), wl.BRUSSELATOR), ((136, 24, 40), wl.FHN),
+                                     ((64, 200, 72), wl.SCHNAKENBERG), ((8, 16, 8), wl.FHN),
+                                     ((128, 128, 136), wl.BRUSSELATOR)])
+def test_fused_3d_matches_oracle(adr, n, model):
+    """3D: the fused pass per x3 slab (pieces out, natural layout) and the x3
+    product on an MN-major operand, over ragged sides (M = n1 n2 not a
+    multiple of 128, x3 not a multiple of the K-block)."""
+    p = problem3(n, model)
+    u0, v0 = inputs(p)
+    Ur, Vr = oracle_run(p, u0, v0, p.nsteps)
+    U, V, st = run(adr, p, u0, v0, p.nsteps)
+    assert st["kernels"]["mode_product_tc"]["count"] == 4 * p.nsteps  # two per Tucker operator
+    assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4])
+def test_fused_3d_every_kernel(adr, kernel):
+    """The x3 product on an MN-major operand in every per-direction kernel
+    (one-CTA and CTA-pair, 64- and 128-byte swizzle of the other operand)."""
+    import torch
+    p = problem3((72, 40, 48), wl.FHN)
+    u0, v0 = inputs(p)
+    Ur, Vr = oracle_run(p, u0, v0, p.nsteps)
+    u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+    v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+    with adr.Plan(p, kernel=kernel) as plan:
+        plan.step(u, v, p.nsteps)
+        assert plan.stats()["device_error"] == 0
+    U, V = u.double().cpu().numpy(), v.double().cpu().numpy()
+    assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+def test_fused_3d_lawson_and_compensated(adr):
+    for p in (problem3((40, 24, 56), wl.FHN, scheme=wl.LAWSON2B),
+              problem3((40, 24, 56), wl.SCHNAKENBERG, state=wl.STATE_COMPENSATED, nsteps=20)):
+        u0, v0 = inputs(p)
+        Ur, Vr = oracle_run(p, u0, v0, p.nsteps)
+        U, V, _ = run(adr, p, u0, v0, p.nsteps)
+        assert oracle.max_rel_err(U, V, Ur, Vr) <= TOL
+
+
+def test_fused_3d_agrees_with_per_direction_launches(adr, monkeypatch):
+    p = problem3((128, 96, 64), wl.BRUSSELATOR, nsteps=8)
+    u0, v0 = inputs(p)
+    U, V, st = run(adr, p, u0, v0, p.nsteps)
+    monkeypatch.setenv("ADR_TC_FUSED", "0")
+    Ud, Vd, std = run(adr, p, u0, v0, p.nsteps)
+    assert st["kernels"]["mode_product_tc"]["count"] == 4 * p.nsteps
+    assert std["kernels"]["mode_product_tc"]["count"] == 6 * p.nsteps
+    assert oracle.max_rel_err(U, V, Ud, Vd) <= 1e-6

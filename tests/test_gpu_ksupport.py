@@ -71,10 +71,12 @@ def oracle_plan(p):
 
 
 def expected_macs(p, kernel, fused):
-    """(dense, computed) multiply-adds of one ETD2RKds step.  fused: each
-    Tucker operator of a 2D grid is one two-mode launch (MMA1 over the Phi_b
-    rows' x2 support in groups of up to 256, padded to 64; MMA2 over the same
-    x2); otherwise one launch per direction."""
+    """(dense, computed) multiply-adds of one ETD2RKds step.  fused: the first
+    two directions of each Tucker operator are one two-mode launch per x3
+    slab (MMA1 over the union of the Phi_b tiles' x2 supports of a unit, in
+    groups of up to 256 padded to 64 -- one unit holds every x2 tile when
+    n2 <= 256; MMA2 per tile over its chunks), and a 3D operator's x3 product
+    is a launch of its own; otherwise one launch per direction."""
     bn, bk = KERNELS[kernel]
     op = oracle_plan(p)
     N = int(np.prod(p.n))
@@ -83,21 +85,31 @@ def expected_macs(p, kernel, fused):
         for c in range(2):
             if fused:
                 n1, n2 = p.n[0], p.n[1]
-                dense += n1 * n1 * n2 + n2 * n2 * n1
+                slabs = N // (n1 * n2)
+                dense += slabs * (n1 * n1 * n2 + n2 * n2 * n1)
                 sa, sb = group_supports(mats[c][0]), group_supports(mats[c][1])
+                tn = -(-n2 // 128)
+                bunit = tn if n2 <= 256 else 1  # tiles sharing one intermediate
                 for a0 in range(0, n1, 128):
                     lo, hi = sa[a0 // 128]
                     kb0, kb1 = lo // 32, min(-(-n1 // 32), -(-hi // 32))
                     rows = min(128, n1 - a0)
                     kin = min(kb1 * 32, n1) - kb0 * 32
-                    for b0 in range(0, n2, 128):
-                        lo2, hi2 = sb[b0 // 128]
-                        cols = min(128, n2 - b0)
+                    for b0 in range(0, tn, bunit):
+                        tiles = range(b0, b0 + bunit)
+                        lo2 = min(sb[b][0] for b in tiles)
+                        hi2 = max(sb[b][1] for b in tiles)
                         for g2 in range(lo2, hi2, 256):
-                            w = 64 * -(-min(256, hi2 - g2) // 64)
-                            computed += rows * w * kin + rows * cols * w
-                continue
-            for mu in range(p.d):
+                            nch = -(-min(256, hi2 - g2) // 64)
+                            computed += slabs * rows * 64 * nch * kin
+                            for b in tiles:
+                                c0 = max(0, (sb[b][0] - g2) // 64)
+                                c1 = min(nch, -(-(sb[b][1] - g2) // 64))
+                                if c1 > c0:
+                                    computed += slabs * rows * min(128, n2 - 128 * b) * 64 * (c1 - c0)
+                if p.d == 2:
+                    continue
+            for mu in range(2 if fused else 0, p.d):
                 K = p.n[mu]
                 M = N // K
                 sup = group_supports(mats[c][mu])
@@ -141,7 +153,6 @@ CASES = {
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_reported_work_matches_the_support_rule(adr, case, kernel, fused, monkeypatch):
     p = CASES[case]()
-    fused = fused and p.d == 2
     if not fused:
         monkeypatch.setenv("ADR_TC_FUSED", "0")
     with adr.Plan(p, kernel=kernel) as plan:
