@@ -1630,7 +1630,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
   uint64_t* d1_full = empty + kFStages;  // MMA1 of a group complete (commit)
   uint64_t* d1_free = d1_full + 1;       // the group's D1 read by every epilogue warp
   uint64_t* p_full = d1_free + 1;        // [4] chunk ch's pieces stored (every epilogue
-                                         // warp), one phase per group
+                                         // warp), one phase per group that has a chunk ch
   uint64_t* p_done = p_full + 4;         // every MMA2 of a group complete (commit)
   uint64_t* acc_full = p_done + 1;       // D2 of a tile complete (commit)
   uint64_t* acc_empty = acc_full + 1;    // D2 of a tile read by every epilogue warp
@@ -1730,6 +1730,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
     const uint64_t dS0 = kmajor_desc<64>(smem_u32(smem));
     const uint32_t idesc2 = idesc_bf16(kBM, kBM);
     uint32_t g = 0, grp = 0, nt = 0;
+    uint32_t pu[4] = {0, 0, 0, 0};  // completed phases of p_full[ch]: groups with a chunk ch
     bool stop = false;
     auto fail = [&](int code) {
       atomicCAS(L.err, 0, code);
@@ -1776,7 +1777,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
           }
           for (int ch = c0; ch < c1; ++ch, ++g) {
             if (!(ready >> ch & 1u)) {
-              if (!mbar_wait(&p_full[ch], grp & 1)) {
+              if (!mbar_wait(&p_full[ch], pu[ch] & 1)) {
                 fail(kErrTimeoutDone);
                 break;
               }
@@ -1816,6 +1817,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
           }
         }
         if (stop) break;
+        for (int ch = 0; ch < nch; ++ch) ++pu[ch];  // waited on or not, every chunk completed
         mma_commit(p_done);
       }
     }

@@ -201,3 +201,31 @@ def test_fused_3d_agrees_with_per_direction_launches(adr, monkeypatch):
     assert st["kernels"]["mode_product_tc"]["count"] == 4 * p.nsteps
     assert std["kernels"]["mode_product_tc"]["count"] == 6 * p.nsteps
     assert oracle.max_rel_err(U, V, Ud, Vd) <= 1e-6
+
+
+def test_fused_batch_of_uneven_chunk_counts(adr):
+    """A grouped launch over solves whose units have different numbers of
+    64-column chunks per group (x2 sides 64, 136, 256, 520): every solve gets
+    the result it gets alone, bit for bit, and matches the oracle."""
+    import torch
+    probs = [problem(n, m, seed=70 + i, nsteps=6)
+             for i, (n, m) in enumerate([((136, 64), wl.FHN), ((200, 256), wl.SCHNAKENBERG),
+                                         ((72, 136), wl.BRUSSELATOR), ((128, 520), wl.FHN)])]
+    inits = [inputs(p) for p in probs]
+    plans = [adr.Plan(p) for p in probs]
+    us = [torch.tensor(u0, dtype=torch.float32, device="cuda") for u0, _ in inits]
+    vs = [torch.tensor(v0, dtype=torch.float32, device="cuda") for _, v0 in inits]
+    with adr.Batch(plans) as batch:
+        batch.step(us, vs, 6)
+    torch.cuda.synchronize()
+    for i, (p, pl, (u0, v0)) in enumerate(zip(probs, plans, inits)):
+        u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        v = torch.tensor(v0, dtype=torch.float32, device="cuda")
+        pl.step(u, v, 6)
+        torch.cuda.synchronize()
+        assert torch.equal(u, us[i]) and torch.equal(v, vs[i]), i
+        Ur, Vr = oracle_run(p, u0, v0, 6)
+        assert oracle.max_rel_err(u.double().cpu().numpy(), v.double().cpu().numpy(), Ur, Vr) <= TOL, i
+        assert pl.stats()["device_error"] == 0
+    for pl in plans:
+        pl.close()
