@@ -1924,6 +1924,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
           axpy_epilogue<4>(ta, D->outf[w.c] + slab, bsrc, lp, D->alpha, n1, n2, n0, m, mrow, ind,
                            D->ind_n1, D->ind_n2);
         } else {  // kPieces3: three BF16 pieces of T, natural layout
+          // the warp's 64 columns are read into registers and D2 released
+          // before the stores, so the next tile's MMA2 overlaps them
+          uint32_t r[4][16];
+#pragma unroll
+          for (int bt = 0; bt < 4; ++bt) tmem_ld16_nw(ta + (uint32_t)(bt * 16), r[bt]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int bt = 0; bt < 4; ++bt) tmem_fence16(r[bt]);
+          arrive(acc_empty);
           // Lanes pair up (rows m, m + 1; n1 is even): of two columns the even
           // lane takes the first and the odd lane the second, each with both
           // rows, so every store writes two BF16 of one piece (4 bytes)
@@ -1931,27 +1940,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_kernel(const __grid_cons
           const int64_t plane2 = (int64_t)D->slabs * n2 * n1 / 2;
           const bool odd = lane & 1;
           const int mp = m - (odd ? 1 : 0);
-#pragma unroll 1
-          for (int bt = 0; bt < 4; ++bt) {
-            uint32_t r[16];
-            tmem_ld16_nw(ta + (uint32_t)(bt * 16), r);
-            tmem_wait_ld();
-            tmem_fence16(r);
 #pragma unroll
-            for (int jj = 0; jj < 16; jj += 2) {
-              const float x0 = __uint_as_float(r[jj]), x1 = __uint_as_float(r[jj + 1]);
-              const float got = __shfl_xor_sync(0xffffffffu, odd ? x0 : x1, 1);
-              const int col = n0 + bt * 16 + jj + (odd ? 1 : 0);
-              if (mp < n1 && col < n2) {
-                uint32_t w0, w1, w2;
-                split3_pair(odd ? got : x0, odd ? x1 : got, w0, w1, w2);
-                const int64_t o2 = (slab + (int64_t)col * n1 + mp) >> 1;
-                op[o2] = w0;
-                op[plane2 + o2] = w1;
-                op[2 * plane2 + o2] = w2;
-              }
+          for (int jj = 0; jj < 64; jj += 2) {
+            const float x0 = __uint_as_float(r[jj / 16][jj % 16]);
+            const float x1 = __uint_as_float(r[jj / 16][jj % 16 + 1]);
+            const float got = __shfl_xor_sync(0xffffffffu, odd ? x0 : x1, 1);
+            const int col = n0 + jj + (odd ? 1 : 0);
+            if (mp < n1 && col < n2) {
+              uint32_t w0, w1, w2;
+              split3_pair(odd ? got : x0, odd ? x1 : got, w0, w1, w2);
+              const int64_t o2 = (slab + (int64_t)col * n1 + mp) >> 1;
+              op[o2] = w0;
+              op[plane2 + o2] = w1;
+              op[2 * plane2 + o2] = w2;
             }
           }
+          continue;  // D2 already released
         }
         arrive(acc_empty);  // D2 of this tile has been read
       }
