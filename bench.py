@@ -80,11 +80,12 @@ def profiled_traffic(workload_name: str, kernel, profiles: str = None):
     """DRAM bytes per launch of the tensor-core mode-product kernel from the
     committed ncu summary, or None when the kernel source has changed since
     that capture or the capture is of another kernel than `kernel` (a
-    variant number of the per-direction kernel, or "fused" for the fused
-    two-mode kernel of 2D grids, summarised in tc_fused_<workload>.md)."""
+    variant number of the per-direction kernel; "fused" for the fused
+    two-mode kernel of 2D grids, or "fused+<variant>" for the two launches
+    of a 3D operator, summarised in tc_fused_<workload>.md)."""
     import hashlib
     import re
-    stem = "tc_fused" if kernel == "fused" else "tc_mode"
+    stem = "tc_fused" if str(kernel).startswith("fused") else "tc_mode"
     prof = os.path.join(profiles or os.path.join(ROOT, "profiles"), f"{stem}_{workload_name}.md")
     src = os.path.join(ROOT, "paper_2307_10684_gb300", "csrc", "tc.cu")
     try:
@@ -533,8 +534,11 @@ def run_single(args, p, nts: int, R, with_compare: bool, oracle):
     in_step = None
     if dom == "mode_product_tc":
         used = kernel if kernel >= 0 else (4 if npts >= 1000000 else 0)  # the plan default
-        if p.d == 2 and prec == wl.BF16X3 and os.environ.get("ADR_TC_FUSED", "1") != "0":
-            used = "fused"  # 2D operators run as one fused two-mode launch
+        if prec == wl.BF16X3 and os.environ.get("ADR_TC_FUSED", "1") != "0":
+            # 2D operators run as one fused two-mode launch; 3D operators as a
+            # fused launch and an x3 launch of kernel `used` (the summary then
+            # gives the mean DRAM bytes of the two per launch)
+            used = "fused" if p.d == 2 else f"fused+{used}"
         traffic = (profiled_traffic(PROFILE_KEY.get(p.name, p.name), used)
                    if p.scheme == wl.ETD2RKDS and int(getattr(p, "state", 0)) != wl.STATE_COMPENSATED
                    else None)

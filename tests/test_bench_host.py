@@ -55,6 +55,10 @@ def test_traffic_only_for_the_captured_source_and_kernel(tmp_path):
     (tmp_path / "tc_fused_fhn1024.md").write_text(
         f"source_sha256(tc.cu): {sha}\ncaptured_kernel: fused\ndram_bytes_per_launch: 123\n")
     assert bench.profiled_traffic("fhn1024", "fused", str(tmp_path)) == 123
+    (tmp_path / "tc_fused_bruss256.md").write_text(
+        f"source_sha256(tc.cu): {sha}\ncaptured_kernel: fused+0\ndram_bytes_per_launch: 456\n")
+    assert bench.profiled_traffic("bruss256", "fused+0", str(tmp_path)) == 456
+    assert bench.profiled_traffic("bruss256", "fused+4", str(tmp_path)) is None
 
 
 def test_in_step_roofline_arithmetic():
