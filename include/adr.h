@@ -270,9 +270,12 @@ adr_status adr_plan_matrix(adr_plan plan, int which, int component, int mu, doub
 
 /* Measurement aid (no counterpart in the paper): the duration of one
  * tensor-core mode-product launch as it runs inside a step.  The launches
- * of `reps` steps' Tucker operators (4 d per ETD2RKds step) are captured
- * back to back in one CUDA graph, with programmatic dependent launch
- * between them and no timing node in between, and the graph is replayed
+ * of `reps` steps' Tucker operators are captured back to back in one CUDA
+ * graph (per ETD2RKds step: 2 on 2D grids and 4 on 3D grids with BF16x3
+ * products, where the first two directions of an operator share one
+ * launch; 4 d with one launch per direction), with programmatic
+ * dependent launch between them and no timing node in between, and the
+ * graph is replayed
  * once to warm up and once between two CUDA events on the plan's stream.
  * *ms_per_launch = that replay's time / (reps x *launches_per_step).
  * u, v: device scratch state buffers of the plan's shape, 16-byte aligned;
@@ -329,8 +332,9 @@ adr_status adr_plan_stats(adr_plan plan, adr_stats* out);
  * Many independent solves (say hundreds of grids of different sizes)
  * advanced together.  When every plan is ADR_BF16X3 with the same d, one
  * step of the whole batch is a fixed set of grouped launches: one stencil
- * launch, one launch per mode product covering every solve's tiles (a
- * persistent tcgen05 kernel reading per-solve descriptors), one
+ * launch, one launch per mode-product pass covering every solve's tiles (a
+ * persistent tcgen05 kernel reading per-solve descriptors; the first two
+ * directions of an operator form one pass), one
  * reaction-difference launch; runs of 16 steps
  * replay a captured CUDA graph.  Other batches step their plans in turn.
  * The batch uses the plans' matrices and workspaces: while a batch steps, do
