@@ -137,20 +137,64 @@ __device__ __forceinline__ CoefDF coef_df(const TridiagT<float>& A, const Tridia
 // Round a double-float to FP32.
 __device__ __forceinline__ float df_round(dfloat x) { return __fadd_rn(x.h, x.l); }
 
-// D = G(u2, v2) - G(u0, v0) (the stage-2 reaction difference of Eq. 11),
-// both reactions and the difference in double-float, rounded once.
-__device__ __forceinline__ void react_diff_df(const ReactionT<float>& rx, float u0, float v0,
-                                              float u2, float v2, float& du, float& dv) {
-  ReactionT<dfloat> r;
-  r.model = rx.model;
-#pragma unroll
-  for (int i = 0; i < 16; ++i) r.p[i] = dfloat(rx.p[i], rx.plo[i]);
-  dfloat a0, b0, a2, b2;
-  react<dfloat>(r, dfloat(u0), dfloat(v0), a0, b0);
-  react<dfloat>(r, dfloat(u2), dfloat(v2), a2, b2);
-  const dfloat x = a2 - a0, y = b2 - b0;
-  du = __fadd_rn(x.h, x.l);
-  dv = __fadd_rn(y.h, y.l);
+// D = G(u2, v2) - G(u0, v0), the stage-2 reaction difference of Eq. 11, in
+// increment form: with du = u2 - u0 and dv = v2 - v0 (a single rounding,
+// relative to the increment), every polynomial difference is expanded by
+// d(AB) = dA B2 + A dB, e.g. d(u^2 v) = (u0 + u2) du v2 + u0^2 dv and
+// d(u^3) = (u2^2 + u2 u0 + u0^2) du.  The terms are of the size of D itself,
+// so the rounding is relative to D and not to the reactions, whose
+// difference cancels most of their digits when the step is small.
+template <typename T>
+__device__ __forceinline__ void react_diff(const ReactionT<T>& rx, T u0, T v0, T u2, T v2, T& du,
+                                           T& dv) {
+  const T eu = u2 - u0, ev = v2 - v0;
+  switch (rx.model) {
+    case ADR_SCHNAKENBERG: {
+      const T g = rx.p[0];
+      const T d = (u0 + u2) * eu * v2 + u0 * u0 * ev;  // d(u^2 v)
+      du = g * (d - eu);
+      dv = -g * d;
+    } break;
+    case ADR_FHN: {
+      const T e = rx.p[0], a1 = rx.p[1];
+      const T d3 = (u2 * u2 + u2 * u0 + u0 * u0) * eu;  // d(u^3)
+      du = eu - d3 - ev;
+      dv = e * (eu - a1 * ev);
+    } break;
+    case ADR_BRUSSELATOR: {
+      const T b = rx.p[1];
+      const T d = (u0 + u2) * eu * v2 + u0 * u0 * ev;
+      du = d - (b + (T)1) * eu;
+      dv = b * eu - d;
+    } break;
+    case ADR_FHN_RHO: {
+      const T rho = rx.p[0], a1 = rx.p[1], a2 = rx.p[2];
+      const T d3 = (u2 * u2 + u2 * u0 + u0 * u0) * eu;
+      du = rho * (eu - d3 - ev);
+      dv = rho * a1 * (eu - a2 * ev);
+    } break;
+    case ADR_DIB: {
+      const T rho = rx.p[0], a1u = rx.p[1], a2u = rx.p[2], a3u = rx.p[3];
+      const T a1v = rx.p[5], a2v = rx.p[6], a3v = rx.p[7], a4v = rx.p[8], a5v = rx.p[9];
+      const T one = (T)1;
+      // g^u: a1u (1 - v) u - a2u u^3 - a3u (v - a4u);  d((1 - v) u) = du - (v2 du + u0 dv)
+      const T d3 = (u2 * u2 + u2 * u0 + u0 * u0) * eu;
+      du = rho * (a1u * (eu - (v2 * eu + u0 * ev)) - a2u * d3 - a3u * ev);
+      // g^v: a1v P(u) Q(v) - a4v R(v) S(u) with P = 1 + a2v u, Q = w (1 - a3v w),
+      // w = 1 - v, R = v (1 + a3v v), S = 1 + a5v u
+      const T w0 = one - v0, w2 = one - v2;
+      const T q2 = w2 * (one - a3v * w2);
+      const T dq = -ev * (one - a3v * (w0 + w2));
+      const T r0 = v0 * (one + a3v * v0);
+      const T dr = ev * (one + a3v * (v0 + v2));
+      const T d1 = a2v * eu * q2 + (one + a2v * u0) * dq;
+      const T d2 = dr * (one + a5v * u2) + r0 * (a5v * eu);
+      dv = rho * (a1v * d1 - a4v * d2);
+    } break;
+    default:
+      du = (T)0;
+      dv = (T)0;
+  }
 }
 
 template <typename T>

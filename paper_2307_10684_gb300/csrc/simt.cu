@@ -32,11 +32,7 @@ __global__ void __launch_bounds__(256) rdiff_kernel(PointwiseArgsT<T> a, const T
                                                     T* __restrict__ dv) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.N;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    T g0u, g0v, g2u, g2v;
-    react<T>(a.rx, u[idx], v[idx], g0u, g0v);
-    react<T>(a.rx, u2[idx], v2[idx], g2u, g2v);
-    du[idx] = g2u - g0u;
-    dv[idx] = g2v - g0v;
+    react_diff<T>(a.rx, u[idx], v[idx], u2[idx], v2[idx], du[idx], dv[idx]);
   }
 }
 

@@ -904,12 +904,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
                 if (t == ch) xb = bv[t * XC + j];  // register-indexed select
               const float u0 = c == 0 ? xb : yb[j], v0 = c == 0 ? yb[j] : xb;
               const float u2 = c == 0 ? x2[j] : y2[j], v2 = c == 0 ? y2[j] : x2[j];
-              float g0u, g0v, g2u, g2v;
-              react<float>(rx, u0, v0, g0u, g0v);
-              react<float>(rx, u2, v2, g2u, g2v);
+              float du, dv;
+              react_diff<float>(rx, u0, v0, u2, v2, du, dv);
               const int64_t o = (int64_t)col * M + m;
               __nv_bfloat16 b0, b1, b2;
-              split3(c == 0 ? g2u - g0u : g2v - g0v, b0, b1, b2);
+              split3(c == 0 ? du : dv, b0, b1, b2);
               op[o] = b0;
               op[plane + o] = b1;
               op[2 * plane + o] = b2;
@@ -1046,15 +1045,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
               const float v2 = v0 + alpha * acc[1][j];
               of0[o] = u2;
               of1[o] = v2;
-              float g0u, g0v, g2u, g2v;
-              react<float>(rx, u0, v0, g0u, g0v);
-              react<float>(rx, u2, v2, g2u, g2v);
+              float du, dv;
+              react_diff<float>(rx, u0, v0, u2, v2, du, dv);
               __nv_bfloat16 b0, b1, b2;
-              split3(g2u - g0u, b0, b1, b2);
+              split3(du, b0, b1, b2);
               op0[o] = b0;
               op0[plane + o] = b1;
               op0[2 * plane + o] = b2;
-              split3(g2v - g0v, b0, b1, b2);
+              split3(dv, b0, b1, b2);
               op1[o] = b0;
               op1[plane + o] = b1;
               op1[2 * plane + o] = b2;
@@ -2427,7 +2425,7 @@ constexpr int kZB2 = 4;  // planes per iteration of the 2D stencil kernel
 
 // D^c = G^c(U2, V2) - G^c(U, V) written as BF16 pieces [3][N] (Eq. 11,
 // second stage).
-template <int F = kFmtBF16, bool DF = false>
+template <int F = kFmtBF16>
 __global__ void __launch_bounds__(kPwThreads) rdiff_pieces_kernel(const __grid_constant__ PwLaunch L) {
   FLAT_PROLOGUE
   const ReactionT<float> rx = sd.a.rx;
@@ -2449,15 +2447,9 @@ __global__ void __launch_bounds__(kPwThreads) rdiff_pieces_kernel(const __grid_c
     float du[4], dv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      if constexpr (DF) {
-        react_diff_df(rx, el(a0[k], j), el(a1[k], j), el(a2[k], j), el(a3[k], j), du[j], dv[j]);
-      } else {
-        float g0u, g0v, g2u, g2v;
-        react<float>(rx, el(a0[k], j), el(a1[k], j), g0u, g0v);
-        react<float>(rx, el(a2[k], j), el(a3[k], j), g2u, g2v);
-        du[j] = g2u - g0u;
-        dv[j] = g2v - g0v;
-      }
+      // the increment form (react_diff) in both modes: its rounding is
+      // relative to the difference itself
+      react_diff<float>(rx, el(a0[k], j), el(a1[k], j), el(a2[k], j), el(a3[k], j), du[j], dv[j]);
     }
     store_pieces_fmt<F>(sd.wu, N, 4 * g, du);
     store_pieces_fmt<F>(sd.wv, N, 4 * g, dv);
@@ -3578,10 +3570,8 @@ static cudaError_t group_step(adr_plan_s* ctl, const GroupStep& G) {
         e = timed_kernel(ctl, KC_RDIFF, N * 2.0 * 12.0, N * (16.0 + 12.0), [&] {
           const dim3 gr(G.flat_blocks), bl(kPwThreads);
           if (G.fmt == kFmtTF32)
-            return G.df ? launch_k(rdiff_pieces_kernel<kFmtTF32, true>, gr, bl, 0, st, G.flat)
-                        : launch_k(rdiff_pieces_kernel<kFmtTF32>, gr, bl, 0, st, G.flat);
-          return G.df ? launch_k(rdiff_pieces_kernel<kFmtBF16, true>, gr, bl, 0, st, G.flat)
-                      : launch_k(rdiff_pieces_kernel<>, gr, bl, 0, st, G.flat);
+            return launch_k(rdiff_pieces_kernel<kFmtTF32>, gr, bl, 0, st, G.flat);
+          return launch_k(rdiff_pieces_kernel<>, gr, bl, 0, st, G.flat);
         });
         break;
       case kOpLawsonPre:
