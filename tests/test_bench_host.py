@@ -84,6 +84,13 @@ def test_in_step_roofline_arithmetic():
     assert rf["algorithmic_bytes_per_launch"] == pytest.approx(24 * N + 16 * 1024 * 1024)
     assert rf["issued_tensor_frac"] == pytest.approx(0.5 * 6 * (8 * 1024 * N / 2e15) / 2e-5)
     q = wl.brusselator_256(precision=wl.BF16X3)  # 256^3, d = 3: HBM-bound
+    # fused 3D operators: a fused launch (two products) and an x3 launch per
+    # operator, 4 per step: 1.5 products and 16 + 8/2 B per point per launch
+    M3 = 256 ** 3
+    r3f = bench.mode_product_roofline(q, wl.BF16X3, 0.1, 4, peaks, "test", None)
+    assert r3f["mode_products_per_launch"] == pytest.approx(1.5)
+    assert r3f["algorithmic_flops_per_launch"] == pytest.approx(1.5 * 4 * 256 * M3)
+    assert r3f["algorithmic_bytes_per_launch"] == pytest.approx(20 * M3 + 1.5 * 8 * 256 * 256)
     r3 = bench.mode_product_roofline(q, wl.BF16X3, 0.1, 6, peaks, "test", None)
     assert r3["bound"] == "hbm" and r3["unit"] == "GB/s"
     assert r3["achieved"] == pytest.approx(((16 + 8 / 3) * 256 ** 3 + 8 * 256 * 256) / 1e-4 / 1e9)
